@@ -1,0 +1,677 @@
+/*
+ * swap_oracle.c -- plain FP64 CPU oracle for the associative bond-swap
+ * potential (Ciarella & Ellenbroek, "Associative bond swaps in molecular
+ * dynamics").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark use it.  It shares no code, header, table or helper with the
+ * CUDA library.
+ *
+ * What it computes (section "The swap potential"):
+ *   U = sum_{i<j} u2(r_ij) + sum_i sum_{j<k in R(i)} a_ij a_ik vh(r_ij) vh(r_ik)
+ *   - u2 for a reactive ("swap") type pair is the generalised Lennard-Jones
+ *     v(r) = 4 eps [(sigma/r)^(2n) - (sigma/r)^n] of Eq. 2b, r < r_cut;
+ *   - u2 for a "wca" type pair is the same form cut at its minimum
+ *     r_min = sigma 2^(1/n) and shifted up by eps (purely repulsive; the
+ *     paper's A-A and B-B interaction, section "Effect of swaps", n = 6);
+ *   - vh is the normalised two-body term of Eq. pot: 1 for r <= r_min,
+ *     -v(r)/eps beyond, 0 at and beyond r_cut;
+ *   - the three-body term is Eq. 3bp with centre i and the unordered pair
+ *     {j,k} of reactive partners of i; the prefactor lambda*eps of Eq. 3bp is
+ *     written a_ij a_ik with a = sqrt(lambda eps) so that it factorises when
+ *     the two pairs have different coefficients (reduces to lambda*eps for a
+ *     single reactive type pair).
+ *   - forces are -dU/dx by analytic differentiation of every pair and every
+ *     triplet term separately; the triplet loop is explicit, O(n_r^2) per
+ *     centre, exactly as Eq. 3bp is written (no per-centre partial sums);
+ *   - the virial is W_ab = -sum over pair vectors r_ij (= x_i - x_j) of
+ *     (r_ij)_a dU/d(r_ij)_b, which for the triplets is the content of Eq. p3.
+ *
+ * Optional "shifted" form of a swap pair (off by default, the paper's literal
+ * form is unshifted): v_s = v - v(r_cut) and vh_s = (v(r_cut) - v)/(eps +
+ * v(r_cut)) beyond r_min, continuous at r_cut and still equal to 1 at r_min.
+ *
+ * Decisions that turn a distance into an integer (is a pair inside its
+ * cut-off, inside the neighbour-list radius, inside the bond radius) can be
+ * taken in FP32 (fp32 = 1): the minimum-image displacement and
+ * d2 = (dx*dx + dy*dy) + dz*dz are evaluated in IEEE float, one rounding per
+ * operation, no contraction (build with -ffp-contract=off), and compared with
+ * the float of (cut*cut computed in double).  The values of the potential are
+ * always evaluated in FP64 from the double displacement.
+ *
+ * Integrators: velocity Verlet (NVE) and BAOAB Langevin (NVT), Leimkuhler &
+ * Matthews (2013).  The Langevin noise uses Philox4x32-10 (Salmon, Moraes,
+ * Dror & Shaw, SC'11) written here from its published definition, mapped to
+ * normals by the Box-Muller transform.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_KIND_NONE 0
+#define ORC_KIND_WCA 1
+#define ORC_KIND_SWAP 2
+
+typedef struct {
+    int kind;      /* ORC_KIND_* */
+    int n;         /* exponent n of Eq. 2b (integer >= 1) */
+    int shift;     /* swap pairs: 0 = literal Eq. 2b, 1 = shifted form */
+    int pad;
+    double eps;
+    double sigma;
+    double lambda3; /* lambda of Eq. 3bp */
+    double rcut;    /* swap pairs: r_cut of Eq. 2b; wca pairs: ignored (r_min) */
+    double rbond;   /* swap pairs: a reactive pair closer than this is a bond */
+} orc_pair;
+
+/* ---------------------------------------------------------------------- */
+/* Eq. 2b and its derivatives, plain pow().                                */
+
+static double lj_v(double r, double eps, double sigma, int n)
+{
+    double x = pow(sigma / r, (double)n);
+    return 4.0 * eps * (x * x - x);
+}
+
+/* dv/dr */
+static double lj_dv(double r, double eps, double sigma, int n)
+{
+    double x = pow(sigma / r, (double)n);
+    return 4.0 * eps * (-2.0 * n * x * x + n * x) / r;
+}
+
+/* d2v/dr2 */
+static double lj_d2v(double r, double eps, double sigma, int n)
+{
+    double x = pow(sigma / r, (double)n);
+    return 4.0 * eps * (2.0 * n * (2.0 * n + 1.0) * x * x - n * (n + 1.0) * x) / (r * r);
+}
+
+double orc_v2(double r, double eps, double sigma, int n) { return lj_v(r, eps, sigma, n); }
+double orc_dv2(double r, double eps, double sigma, int n) { return lj_dv(r, eps, sigma, n); }
+
+static double pair_rmin(const orc_pair *p) { return p->sigma * pow(2.0, 1.0 / p->n); }
+
+/* Two-body energy u2(r) and its first two derivatives for one pair type, for
+ * a pair already decided to be inside its cut-off (the decision is taken by
+ * the caller, in the decision precision; a WCA pair is inside for r < r_min,
+ * where u2 and du2/dr go to zero continuously). */
+static void pair_u2(const orc_pair *p, double r, double *u, double *du, double *d2u)
+{
+    *u = *du = *d2u = 0.0;
+    if (p->kind == ORC_KIND_WCA) {
+        *u = lj_v(r, p->eps, p->sigma, p->n) + p->eps;
+        *du = lj_dv(r, p->eps, p->sigma, p->n);
+        *d2u = lj_d2v(r, p->eps, p->sigma, p->n);
+    } else if (p->kind == ORC_KIND_SWAP) {
+        double vc = p->shift ? lj_v(p->rcut, p->eps, p->sigma, p->n) : 0.0;
+        *u = lj_v(r, p->eps, p->sigma, p->n) - vc;
+        *du = lj_dv(r, p->eps, p->sigma, p->n);
+        *d2u = lj_d2v(r, p->eps, p->sigma, p->n);
+    }
+}
+
+/* Eq. pot: the normalised two-body term vh(r) and its derivatives, for a
+ * swap pair already decided to be inside r_cut. */
+static void pair_vhat(const orc_pair *p, double r, double *vh, double *dvh, double *d2vh)
+{
+    *vh = *dvh = *d2vh = 0.0;
+    if (p->kind != ORC_KIND_SWAP)
+        return;
+    if (r <= pair_rmin(p)) {
+        *vh = 1.0;
+        return;
+    }
+    double vc = p->shift ? lj_v(p->rcut, p->eps, p->sigma, p->n) : 0.0;
+    double den = p->eps + vc;
+    *vh = (vc - lj_v(r, p->eps, p->sigma, p->n)) / den;
+    *dvh = -lj_dv(r, p->eps, p->sigma, p->n) / den;
+    *d2vh = -lj_d2v(r, p->eps, p->sigma, p->n) / den;
+}
+
+/* Eq. pot with its cut-off applied (vh = 0 for r >= r_cut). */
+double orc_vhat(const orc_pair *p, double r)
+{
+    double a, b, c;
+    if (p->kind != ORC_KIND_SWAP || r >= p->rcut)
+        return 0.0;
+    pair_vhat(p, r, &a, &b, &c);
+    return a;
+}
+
+/* Two-body energy with its cut-off applied. */
+double orc_u2(const orc_pair *p, double r)
+{
+    double a, b, c;
+    if (p->kind == ORC_KIND_WCA && r >= p->sigma * pow(2.0, 1.0 / p->n))
+        return 0.0;
+    if (p->kind == ORC_KIND_SWAP && r >= p->rcut)
+        return 0.0;
+    if (p->kind == ORC_KIND_NONE)
+        return 0.0;
+    pair_u2(p, r, &a, &b, &c);
+    return a;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Distance decisions.                                                     */
+
+static double wrap_d(double d, double L)
+{
+    if (d > 0.5 * L)
+        return d - L;
+    if (d < -0.5 * L)
+        return d + L;
+    return d;
+}
+
+static float wrap_f(float d, float L, float hL)
+{
+    if (d > hL)
+        return d - L;
+    if (d < -hL)
+        return d + L;
+    return d;
+}
+
+/* Squared minimum-image distance used for integer decisions. */
+static double decision_d2(const double *xi, const double *xj, const double *box, int fp32)
+{
+    if (fp32) {
+        float dx = (float)xj[0] - (float)xi[0];
+        float dy = (float)xj[1] - (float)xi[1];
+        float dz = (float)xj[2] - (float)xi[2];
+        float Lx = (float)box[0], Ly = (float)box[1], Lz = (float)box[2];
+        dx = wrap_f(dx, Lx, 0.5f * Lx);
+        dy = wrap_f(dy, Ly, 0.5f * Ly);
+        dz = wrap_f(dz, Lz, 0.5f * Lz);
+        float s = dx * dx;
+        float t = dy * dy;
+        s = s + t;
+        t = dz * dz;
+        s = s + t;
+        return (double)s;
+    }
+    double dx = wrap_d(xj[0] - xi[0], box[0]);
+    double dy = wrap_d(xj[1] - xi[1], box[1]);
+    double dz = wrap_d(xj[2] - xi[2], box[2]);
+    double s = dx * dx;
+    double t = dy * dy;
+    s = s + t;
+    t = dz * dz;
+    s = s + t;
+    return s;
+}
+
+/* The squared threshold a decision compares against, in the same precision. */
+static double decision_cut2(double cut, int fp32)
+{
+    double c2 = cut * cut;
+    return fp32 ? (double)(float)c2 : c2;
+}
+
+/* Interaction cut-off of a pair type (0 when the pair does not interact). */
+static double pair_rcut(const orc_pair *p)
+{
+    if (p->kind == ORC_KIND_WCA)
+        return pair_rmin(p);
+    if (p->kind == ORC_KIND_SWAP)
+        return p->rcut;
+    return 0.0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Candidate pairs from a plain linked-cell list (or all pairs for boxes   */
+/* too small for a 3x3x3 stencil).                                         */
+
+typedef struct {
+    int i, j;
+} ipair;
+
+typedef struct {
+    ipair *a;
+    long n, cap;
+} pairvec;
+
+static int pv_push(pairvec *v, int i, int j)
+{
+    if (v->n == v->cap) {
+        long nc = v->cap ? 2 * v->cap : 1024;
+        ipair *na = (ipair *)realloc(v->a, (size_t)nc * sizeof(ipair));
+        if (!na)
+            return -1;
+        v->a = na;
+        v->cap = nc;
+    }
+    v->a[v->n].i = i;
+    v->a[v->n].j = j;
+    v->n++;
+    return 0;
+}
+
+/* All unordered pairs i<j whose squared decision distance is below the
+ * pair type's cut2 (cut = pair cut-off + extra).  Returns 0 or -1 (memory). */
+static int find_pairs(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
+                      const double *box, int fp32, double extra, pairvec *out)
+{
+    double cmax = 0.0;
+    for (int t = 0; t < ntypes * ntypes; t++) {
+        double c = pair_rcut(&tab[t]);
+        if (c > 0.0 && c + extra > cmax)
+            cmax = c + extra;
+    }
+    out->n = 0;
+    if (cmax <= 0.0 || n < 2)
+        return 0;
+    int nc[3];
+    for (int d = 0; d < 3; d++) {
+        nc[d] = (int)floor(box[d] / cmax);
+        if (nc[d] < 1)
+            nc[d] = 1;
+    }
+    int brute = (nc[0] < 3 || nc[1] < 3 || nc[2] < 3);
+    if (brute) {
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++) {
+                const orc_pair *p = &tab[type[i] * ntypes + type[j]];
+                double c = pair_rcut(p);
+                if (c <= 0.0)
+                    continue;
+                if (decision_d2(&x[3 * i], &x[3 * j], box, fp32) < decision_cut2(c + extra, fp32))
+                    if (pv_push(out, i, j))
+                        return -1;
+            }
+        return 0;
+    }
+    long ncell = (long)nc[0] * nc[1] * nc[2];
+    int *head = (int *)malloc((size_t)ncell * sizeof(int));
+    int *next = (int *)malloc((size_t)n * sizeof(int));
+    int *cid = (int *)malloc((size_t)n * 3 * sizeof(int));
+    if (!head || !next || !cid) {
+        free(head);
+        free(next);
+        free(cid);
+        return -1;
+    }
+    for (long c = 0; c < ncell; c++)
+        head[c] = -1;
+    for (int i = 0; i < n; i++) {
+        int c3[3];
+        for (int d = 0; d < 3; d++) {
+            double s = x[3 * i + d] / box[d];
+            s -= floor(s);
+            int k = (int)(s * nc[d]);
+            if (k >= nc[d])
+                k = nc[d] - 1;
+            if (k < 0)
+                k = 0;
+            c3[d] = k;
+            cid[3 * i + d] = k;
+        }
+        long c = ((long)c3[2] * nc[1] + c3[1]) * nc[0] + c3[0];
+        next[i] = head[c];
+        head[c] = i;
+    }
+    for (int i = 0; i < n; i++) {
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int cx = (cid[3 * i] + dx + nc[0]) % nc[0];
+                    int cy = (cid[3 * i + 1] + dy + nc[1]) % nc[1];
+                    int cz = (cid[3 * i + 2] + dz + nc[2]) % nc[2];
+                    long c = ((long)cz * nc[1] + cy) * nc[0] + cx;
+                    for (int j = head[c]; j >= 0; j = next[j]) {
+                        if (j <= i)
+                            continue;
+                        const orc_pair *p = &tab[type[i] * ntypes + type[j]];
+                        double cut = pair_rcut(p);
+                        if (cut <= 0.0)
+                            continue;
+                        if (decision_d2(&x[3 * i], &x[3 * j], box, fp32) <
+                            decision_cut2(cut + extra, fp32))
+                            if (pv_push(out, i, j)) {
+                                free(head);
+                                free(next);
+                                free(cid);
+                                return -1;
+                            }
+                    }
+                }
+    }
+    free(head);
+    free(next);
+    free(cid);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Energy, forces, virial.                                                 */
+
+/* out[0] = U2, out[1] = U3, out[2..7] = W (xx, yy, zz, xy, xz, yz),
+ * out[8] = number of bonds.
+ * scales (may be NULL): [0] energy scale of U2, [1] of U3, [2] virial scale.
+ * fscale (may be NULL): per-particle force scale, the sum over every term
+ * acting on the particle of |term| + r |d term/dr| (first-order sensitivity
+ * of the term to a relative perturbation of its distances).
+ * force (may be NULL): 3n doubles. */
+int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
+               const double *box, int fp32, double *force, double *out, double *scales,
+               double *fscale)
+{
+    pairvec pv = {0, 0, 0};
+    if (find_pairs(n, x, type, ntypes, tab, box, fp32, 0.0, &pv))
+        return -1;
+    double U2 = 0, U3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
+    double sU2 = 0, sU3 = 0, sW = 0;
+    long nb = 0;
+    if (force)
+        memset(force, 0, (size_t)n * 3 * sizeof(double));
+    if (fscale)
+        memset(fscale, 0, (size_t)n * sizeof(double));
+
+    /* Per-centre lists of reactive partners (index into pv). */
+    int *rcount = (int *)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
+    if (!rcount) {
+        free(pv.a);
+        return -1;
+    }
+
+    for (long q = 0; q < pv.n; q++) {
+        int i = pv.a[q].i, j = pv.a[q].j;
+        const orc_pair *p = &tab[type[i] * ntypes + type[j]];
+        double d[3];
+        for (int c = 0; c < 3; c++)
+            d[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]); /* r_ij = x_i - x_j */
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double u, du, d2u;
+        pair_u2(p, r, &u, &du, &d2u);
+        U2 += u;
+        sU2 += fabs(u) + r * fabs(du);
+        /* F_i = -du/dr * d/r ; F_j = -F_i */
+        double g = -du / r;
+        if (force)
+            for (int c = 0; c < 3; c++) {
+                force[3 * i + c] += g * d[c];
+                force[3 * j + c] -= g * d[c];
+            }
+        W[0] += g * d[0] * d[0];
+        W[1] += g * d[1] * d[1];
+        W[2] += g * d[2] * d[2];
+        W[3] += g * d[0] * d[1];
+        W[4] += g * d[0] * d[2];
+        W[5] += g * d[1] * d[2];
+        sW += r * fabs(du) + r * r * fabs(d2u);
+        if (fscale) {
+            double s = fabs(du) + r * fabs(d2u);
+            fscale[i] += s;
+            fscale[j] += s;
+        }
+        if (p->kind == ORC_KIND_SWAP) {
+            rcount[i]++;
+            rcount[j]++;
+            if (decision_d2(&x[3 * i], &x[3 * j], box, fp32) < decision_cut2(p->rbond, fp32))
+                nb++;
+        }
+    }
+
+    /* CSR of reactive partners per centre. */
+    long *rstart = (long *)malloc((size_t)(n + 1) * sizeof(long));
+    long total = 0;
+    for (int i = 0; i < n; i++)
+        total += rcount[i];
+    int *rpart = (int *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int));
+    if (!rstart || !rpart) {
+        free(rstart);
+        free(rpart);
+        free(rcount);
+        free(pv.a);
+        return -1;
+    }
+    rstart[0] = 0;
+    for (int i = 0; i < n; i++)
+        rstart[i + 1] = rstart[i] + rcount[i];
+    for (int i = 0; i < n; i++)
+        rcount[i] = 0;
+    for (long q = 0; q < pv.n; q++) {
+        int i = pv.a[q].i, j = pv.a[q].j;
+        if (tab[type[i] * ntypes + type[j]].kind != ORC_KIND_SWAP)
+            continue;
+        rpart[rstart[i] + rcount[i]++] = j;
+        rpart[rstart[j] + rcount[j]++] = i;
+    }
+
+    /* Eq. 3bp: explicit loop over every centre i and unordered {j,k}. */
+    for (int i = 0; i < n; i++) {
+        for (long qa = rstart[i]; qa < rstart[i + 1]; qa++) {
+            for (long qb = qa + 1; qb < rstart[i + 1]; qb++) {
+                int j = rpart[qa], k = rpart[qb];
+                const orc_pair *pj = &tab[type[i] * ntypes + type[j]];
+                const orc_pair *pk = &tab[type[i] * ntypes + type[k]];
+                double dj[3], dk[3];
+                for (int c = 0; c < 3; c++) {
+                    dj[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]);
+                    dk[c] = wrap_d(x[3 * i + c] - x[3 * k + c], box[c]);
+                }
+                double rj = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+                double rk = sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
+                double hj, dhj, d2hj, hk, dhk, d2hk;
+                pair_vhat(pj, rj, &hj, &dhj, &d2hj);
+                pair_vhat(pk, rk, &hk, &dhk, &d2hk);
+                double aj = sqrt(pj->lambda3 * pj->eps);
+                double ak = sqrt(pk->lambda3 * pk->eps);
+                double pref = aj * ak;
+                double v3 = pref * hj * hk;
+                U3 += v3;
+                sU3 += pref * (fabs(hj * hk) + rj * fabs(dhj * hk) + rk * fabs(hj * dhk));
+                /* dU/drj = pref dhj hk ; dU/drk = pref hj dhk */
+                double dUj = pref * dhj * hk;
+                double dUk = pref * hj * dhk;
+                double gj = -dUj / rj; /* force on i from the (i,j) leg: gj * dj */
+                double gk = -dUk / rk;
+                if (force)
+                    for (int c = 0; c < 3; c++) {
+                        force[3 * i + c] += gj * dj[c] + gk * dk[c];
+                        force[3 * j + c] -= gj * dj[c];
+                        force[3 * k + c] -= gk * dk[c];
+                    }
+                W[0] += gj * dj[0] * dj[0] + gk * dk[0] * dk[0];
+                W[1] += gj * dj[1] * dj[1] + gk * dk[1] * dk[1];
+                W[2] += gj * dj[2] * dj[2] + gk * dk[2] * dk[2];
+                W[3] += gj * dj[0] * dj[1] + gk * dk[0] * dk[1];
+                W[4] += gj * dj[0] * dj[2] + gk * dk[0] * dk[2];
+                W[5] += gj * dj[1] * dj[2] + gk * dk[1] * dk[2];
+                double sj = pref * (fabs(dhj * hk) + rj * fabs(d2hj * hk) + rk * fabs(dhj * dhk));
+                double sk = pref * (fabs(hj * dhk) + rk * fabs(hj * d2hk) + rj * fabs(dhj * dhk));
+                sW += rj * sj + rk * sk;
+                if (fscale) {
+                    fscale[i] += sj + sk;
+                    fscale[j] += sj;
+                    fscale[k] += sk;
+                }
+            }
+        }
+    }
+
+    out[0] = U2;
+    out[1] = U3;
+    for (int c = 0; c < 6; c++)
+        out[2 + c] = W[c];
+    out[8] = (double)nb;
+    if (scales) {
+        scales[0] = sU2;
+        scales[1] = sU3;
+        scales[2] = sW;
+    }
+    free(rstart);
+    free(rpart);
+    free(rcount);
+    free(pv.a);
+    return 0;
+}
+
+/* Neighbour-list membership: for every particle i, the sorted indices j != i
+ * whose squared decision distance is below (r_cut(ti,tj) + skin)^2, for
+ * interacting type pairs only.  counts[i] = number of such j; nbr is n*maxn
+ * row-major.  Returns the largest count (rows longer than maxn are cut), or
+ * -1 on allocation failure. */
+int orc_nlist(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
+              const double *box, int fp32, double skin, int maxn, int *counts, int *nbr)
+{
+    pairvec pv = {0, 0, 0};
+    if (find_pairs(n, x, type, ntypes, tab, box, fp32, skin, &pv))
+        return -1;
+    for (int i = 0; i < n; i++)
+        counts[i] = 0;
+    for (long q = 0; q < pv.n; q++) {
+        int i = pv.a[q].i, j = pv.a[q].j;
+        if (counts[i] < maxn)
+            nbr[(long)i * maxn + counts[i]] = j;
+        counts[i]++;
+        if (counts[j] < maxn)
+            nbr[(long)j * maxn + counts[j]] = i;
+        counts[j]++;
+    }
+    int mx = 0;
+    for (int i = 0; i < n; i++) {
+        int c = counts[i] < maxn ? counts[i] : maxn;
+        int *row = &nbr[(long)i * maxn];
+        for (int a = 1; a < c; a++) { /* insertion sort */
+            int v = row[a], b = a - 1;
+            while (b >= 0 && row[b] > v) {
+                row[b + 1] = row[b];
+                b--;
+            }
+            row[b + 1] = v;
+        }
+        if (counts[i] > mx)
+            mx = counts[i];
+    }
+    free(pv.a);
+    return mx;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10 and Box-Muller normals.                                   */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* Three standard normals for (seed, step, tag, purpose): counter words are
+ * (tag, step low, step high, purpose), key words (seed low, seed high);
+ * u = (w + 0.5) 2^-32; z0, z1 from (u0, u1), z2 from (u2, u3). */
+void orc_normals3(uint64_t seed, uint64_t step, uint32_t tag, uint32_t purpose, double z[3])
+{
+    uint32_t ctr[4] = {tag, (uint32_t)step, (uint32_t)(step >> 32), purpose};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    const double two_pi = 6.283185307179586476925286766559;
+    double u0 = ((double)w[0] + 0.5) * 2.3283064365386962890625e-10;
+    double u1 = ((double)w[1] + 0.5) * 2.3283064365386962890625e-10;
+    double u2 = ((double)w[2] + 0.5) * 2.3283064365386962890625e-10;
+    double u3 = ((double)w[3] + 0.5) * 2.3283064365386962890625e-10;
+    double ra = sqrt(-2.0 * log(u0));
+    double rb = sqrt(-2.0 * log(u2));
+    z[0] = ra * cos(two_pi * u1);
+    z[1] = ra * sin(two_pi * u1);
+    z[2] = rb * cos(two_pi * u3);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Integrators.                                                            */
+
+/* Advance nsteps from step index step0.  BAOAB when gamma > 0 (NVT), else
+ * velocity Verlet (NVE).  x is kept wrapped into [0, L) with image counts in
+ * img (3n ints, may be NULL).  thermo (may be NULL) receives per step
+ * [U2, U3, K, W0..W5, n_bonds] (10 doubles) after the step.  Langevin step k
+ * (advancing state step0+k) draws its normals with step value step0+k and the
+ * particle's tag, purpose 1. */
+int orc_run(int n, double *x, double *v, int *img, const int *type, const double *mass,
+            const uint32_t *tag, int ntypes, const orc_pair *tab, const double *box, int fp32,
+            double dt, int nsteps, double kT, double gamma, uint64_t seed, uint64_t step0,
+            double *thermo)
+{
+    double *F = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
+    double out[9];
+    if (!F)
+        return -1;
+    if (orc_forces(n, x, type, ntypes, tab, box, fp32, F, out, NULL, NULL)) {
+        free(F);
+        return -1;
+    }
+    double c = exp(-gamma * dt);
+    for (int s = 0; s < nsteps; s++) {
+        for (int i = 0; i < n; i++) {
+            double im = 1.0 / mass[i];
+            for (int d = 0; d < 3; d++) {
+                v[3 * i + d] += 0.5 * dt * F[3 * i + d] * im; /* B */
+                x[3 * i + d] += 0.5 * dt * v[3 * i + d];      /* A */
+            }
+            if (gamma > 0.0) { /* O */
+                double z[3];
+                orc_normals3(seed, step0 + (uint64_t)s, tag[i], 1u, z);
+                double sd = sqrt((1.0 - c * c) * kT * im);
+                for (int d = 0; d < 3; d++)
+                    v[3 * i + d] = c * v[3 * i + d] + sd * z[d];
+            }
+            for (int d = 0; d < 3; d++) {
+                x[3 * i + d] += 0.5 * dt * v[3 * i + d]; /* A */
+                double L = box[d];
+                double k = floor(x[3 * i + d] / L);
+                if (k != 0.0) {
+                    x[3 * i + d] -= k * L;
+                    if (x[3 * i + d] >= L) /* rounding guard */
+                        x[3 * i + d] -= L, k += 1.0;
+                    if (x[3 * i + d] < 0.0)
+                        x[3 * i + d] += L, k -= 1.0;
+                    if (img)
+                        img[3 * i + d] += (int)k;
+                }
+            }
+        }
+        if (orc_forces(n, x, type, ntypes, tab, box, fp32, F, out, NULL, NULL)) {
+            free(F);
+            return -1;
+        }
+        double K = 0.0;
+        for (int i = 0; i < n; i++) {
+            double im = 1.0 / mass[i];
+            for (int d = 0; d < 3; d++) {
+                v[3 * i + d] += 0.5 * dt * F[3 * i + d] * im; /* B */
+                K += 0.5 * mass[i] * v[3 * i + d] * v[3 * i + d];
+            }
+        }
+        if (thermo) {
+            double *t = &thermo[(long)s * 10];
+            t[0] = out[0];
+            t[1] = out[1];
+            t[2] = K;
+            for (int q = 0; q < 6; q++)
+                t[3 + q] = out[2 + q];
+            t[9] = out[8];
+        }
+    }
+    free(F);
+    return 0;
+}

@@ -1,0 +1,148 @@
+"""Seeded synthetic inputs shared by the tests, the oracle legs and the benchmark.
+
+This module holds no arithmetic of the method: it only draws configurations.
+Every array it returns is exactly representable in float32 (positions,
+velocities, box lengths), so that an FP32 device path and an FP64 CPU path see
+bit-identical inputs.
+
+Recipe (the paper has no public dataset; these stand in for its workloads):
+
+* positions: random sequential addition, uniform in a periodic orthorhombic box,
+  with a minimum pair separation (0.9 sigma by default), drawn from numpy's
+  Philox bit generator in batches; a candidate is rejected if it is closer than
+  the minimum separation to any accepted particle or to an earlier candidate of
+  its batch;
+* types: alternate by tag (tag % n_types), A:B = 1:1 for two types;
+* velocities: Maxwell-Boltzmann at kT with the centre-of-mass velocity removed;
+* box: cubic, L = (N / density)^(1/3) rounded to float32.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+try:  # scipy is present on both the build host and the GPU host
+    from scipy.spatial import cKDTree
+except Exception:  # pragma: no cover - fallback for minimal environments
+    cKDTree = None
+
+
+def f32(a):
+    """Round to the nearest float32 and return as float64."""
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def cubic_box(n: int, density: float) -> np.ndarray:
+    L = float(np.float32((n / density) ** (1.0 / 3.0)))
+    return np.array([L, L, L])
+
+
+def _min_dist_brute(cand, pts, box):
+    if len(pts) == 0:
+        return np.full(len(cand), np.inf)
+    d = cand[:, None, :] - pts[None, :, :]
+    d -= box * np.round(d / box)
+    return np.sqrt((d * d).sum(-1)).min(axis=1)
+
+
+def rsa_positions(n: int, box, min_sep: float = 0.9, seed: int = 1, batch: int = 16384,
+                  max_tries: int = 10000) -> np.ndarray:
+    """n positions (n x 3, float32-representable) with pairwise separation >= min_sep."""
+    box = np.asarray(box, dtype=np.float64)
+    rng = np.random.Generator(np.random.Philox(seed))
+    pts = np.zeros((0, 3))
+    tries = 0
+    while len(pts) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("rsa_positions: could not place particles (density too high)")
+        m = min(batch, max(64, 2 * (n - len(pts))))
+        cand = f32(rng.random((m, 3)) * box)
+        cand[cand >= box] = 0.0
+        cand[cand < 2.0 ** -20] = 0.0
+        if cKDTree is not None:
+            if len(pts):
+                tree = cKDTree(pts, boxsize=box)
+                dmin, _ = tree.query(cand, k=1, distance_upper_bound=min_sep)
+                ok = ~(dmin < min_sep)
+            else:
+                ok = np.ones(m, dtype=bool)
+            cand = cand[ok]
+            if len(cand) > 1:
+                ct = cKDTree(cand, boxsize=box)
+                pairs = ct.query_pairs(min_sep, output_type="ndarray")
+                bad = np.zeros(len(cand), dtype=bool)
+                if len(pairs):
+                    bad[np.maximum(pairs[:, 0], pairs[:, 1])] = True
+                cand = cand[~bad]
+        else:
+            ok = _min_dist_brute(cand, pts, box) >= min_sep
+            cand = cand[ok]
+            keep = []
+            for i in range(len(cand)):
+                if all(np.linalg.norm((cand[i] - cand[j]) - box * np.round((cand[i] - cand[j]) / box))
+                       >= min_sep for j in keep):
+                    keep.append(i)
+            cand = cand[keep]
+        pts = np.concatenate([pts, cand[: n - len(pts)]], axis=0)
+    return pts
+
+
+def alternating_types(n: int, n_types: int = 2) -> np.ndarray:
+    return (np.arange(n) % n_types).astype(np.int32)
+
+
+def maxwell_velocities(n: int, kT: float, mass, seed: int = 2) -> np.ndarray:
+    """Maxwell-Boltzmann velocities (n x 3, float32-representable), zero total momentum."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    m = np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,))
+    v = rng.standard_normal((n, 3)) * np.sqrt(kT / m)[:, None]
+    if n > 0:
+        v -= (m[:, None] * v).sum(0) / m.sum()
+    return f32(v)
+
+
+def swap_pairs(eps=1.0, sigma=1.0, n=10, rcut=1.5, lambda3=1.0, shift=0, rbond=None,
+               wca_sigma=1.0, wca_eps=1.0, wca_n=6):
+    """Two-type table of the paper's binary mixture: A-B swap, A-A and B-B WCA.
+
+    Returned as {(ti, tj): params}; ``rbond`` defaults to the outer root of
+    v = -eps/2 (where the normalised term equals one half).
+    """
+    if rbond is None:
+        rbond = sigma * ((1.0 - np.sqrt(0.5)) / 2.0) ** (-1.0 / n)
+    sw = dict(kind=2, eps=eps, sigma=sigma, n=n, rcut=rcut, lambda3=lambda3, shift=shift,
+              rbond=rbond)
+    wca = dict(kind=1, eps=wca_eps, sigma=wca_sigma, n=wca_n)
+    return {(0, 1): sw, (0, 0): wca, (1, 1): wca}
+
+
+def workload(name: str = "mix100k", lambda3: float = 1.0, seed: int = 1, n: int | None = None,
+             density: float | None = None, shift: int = 0):
+    """Named synthetic workloads.
+
+    * ``mix2k``: 2,000 particles, A:B 1:1, density 0.2, NVE dt 0.001 from Maxwell
+      velocities at kT 0.1 (the small FP64 parity case);
+    * ``mix100k``: 100,000 particles, A:B 1:1, density 0.5, Langevin kT 0.05,
+      gamma 1, dt 0.001, skin 0.3 (the FP32 throughput case).
+    Both: A-B swap pair with eps = sigma = 1, n = 10, r_cut = 1.5; A-A and B-B
+    WCA with sigma = 1; minimum separation 0.9.
+    """
+    if name == "mix2k":
+        n = n or 2000
+        density = density or 0.2
+        kT, gamma, dt, skin = 0.1, 0.0, 0.001, 0.3
+    elif name == "mix100k":
+        n = n or 100_000
+        density = density or 0.5
+        kT, gamma, dt, skin = 0.05, 1.0, 0.001, 0.3
+    else:
+        raise ValueError(f"unknown workload {name!r}")
+    box = cubic_box(n, density)
+    x = rsa_positions(n, box, 0.9, seed=seed)
+    types = alternating_types(n, 2)
+    mass = np.ones(n)
+    v = maxwell_velocities(n, kT, mass, seed=seed + 1000)
+    return dict(name=name, n=n, density=density, box=box, x=x, v=v, types=types, mass=mass,
+                tags=np.arange(n, dtype=np.uint32), n_types=2,
+                pairs=swap_pairs(lambda3=lambda3, shift=shift), kT=kT, gamma=gamma, dt=dt,
+                skin=skin, seed=seed)
