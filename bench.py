@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: swap-potential particle-timesteps/s on one GB300 (FP32 path).
+
+Workload (synthetic, seeded; the paper has no public dataset): 100,000
+particles, A:B 1:1 alternating by tag, density 0.5, RSA positions with minimum
+separation 0.9, A-B swap pair (eps = sigma = 1, n = 10, r_cut = 1.5, lambda 1
+by default), A-A and B-B WCA (sigma = 1), BAOAB Langevin at kT = 0.05,
+gamma = 1, dt = 0.001, skin 0.3, list rebuilt on the device on displacement.
+One benchmark step = one launch of the persistent step kernel advancing
+``--md-steps`` (default 1,000) time steps with energy and virial every step;
+the inputs stay resident in HBM, and L2 is flushed (a 512 MB write) between
+timed launches.
+
+Each rank (torchrun, one GPU each) runs its own independent replica: weak
+scaling, no collective on the data path.  ``--impl reference`` times the FP64
+CPU oracle on the same workload (bounded samples) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "swap-potential particle-timesteps/s at 100k (FP32); % of HBM roofline"
+UNIT = "particle-timesteps/s"
+# swp_read_thermo copies the device control block (176 bytes) to the host.
+CTL_BYTES = 176
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lam", type=float, default=1.0)
+    ap.add_argument("--md-steps", type=int, default=1000)
+    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--bps", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(n, lam, rank):
+    from paper_1912_08569_gb300 import inputs
+
+    return inputs.workload("mix100k", lambda3=lam, n=n, seed=1 + rank)
+
+
+def _config(a, n, world):
+    return {"workload": f"mix{n // 1000}k: N={n}, A:B 1:1, density 0.5, n=10, r_cut=1.5, "
+                        f"lambda={a.lam:g}, BAOAB kT=0.05 gamma=1 dt=0.001, skin 0.3",
+            "n_particles": n, "md_steps_per_step": a.md_steps, "lambda": a.lam,
+            "replicas": world, "l2": "flushed (512 MB write) between timed launches",
+            "parallelism": f"replicas x{world}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [s.strip() for s in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+
+def _kernel_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1912_08569_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _profile_traffic(n, md_steps):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_run_traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("kernel_digest") != _kernel_digest():
+        return None
+    per_particle_step = d.get("dram_bytes_per_particle_step")
+    if per_particle_step is None:
+        return None
+    return per_particle_step * n * md_steps
+
+
+def algorithmic_bytes(n, md_steps, nn, nn_r, rebuilds):
+    """Bytes one launch must move (each array read or written once per pass
+    that needs it): per particle-step 16 (position, S pass) + 16 (position,
+    force pass) + 16 (new position) + 48 (fixed-point position read+write) +
+    32 (velocity read+write) + 16 (force) + 8 (S write+read) + 8 (row counts)
+    + 4 (nn + nn_r) (list indices); per particle and rebuild 120 (sort) +
+    4 nn (list write)."""
+    per_step = 160.0 + 4.0 * (nn + nn_r)
+    per_rebuild = 120.0 + 4.0 * nn
+    return n * (md_steps * per_step + rebuilds * per_rebuild)
+
+
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(wl, seconds, steps_cap=200):
+    """Times the FP64 oracle on the same workload for a bounded number of steps."""
+    import oracle
+
+    tab = oracle.pair_table(wl["n_types"], wl["pairs"])
+    t0 = time.perf_counter()
+    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True)
+    t_force = time.perf_counter() - t0
+    nsteps = int(max(2, min(steps_cap, seconds / max(t_force, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], wl["n_types"], tab, wl["box"],
+               wl["dt"], nsteps, kT=wl["kT"], gamma=wl["gamma"], seed=wl["seed"], fp32=True)
+    el = time.perf_counter() - t0
+    return wl["n"] * nsteps / el, nsteps, el
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    wl = _workload(a.n, a.lam, 0)
+    tab = oracle.pair_table(wl["n_types"], wl["pairs"])
+    t0 = time.perf_counter()
+    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True)
+    t_force = time.perf_counter() - t0
+    # each step: a bounded sample of the workload (~8 s of CPU work)
+    per = int(max(1, min(50, 8.0 / max(t_force, 1e-6))))
+    x, v = wl["x"], wl["v"]
+    times = []
+    for k in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        x, v, _, th = oracle.run(x, v, wl["types"], wl["mass"], wl["tags"], wl["n_types"], tab,
+                                 wl["box"], wl["dt"], per, kT=wl["kT"], gamma=wl["gamma"],
+                                 seed=wl["seed"], step0=k * per, fp32=True)
+        if k >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = wl["n"] * per / (ms / 1e3)
+    sample = f"N={wl['n']}, {per} NVT steps per step of the FP64 C oracle (1 thread)"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(a, wl["n"], 1),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1912_08569_gb300 import SwapSystem
+    from paper_1912_08569_gb300 import _abi as A
+    from paper_1912_08569_gb300.build import build
+
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    wl = _workload(a.n, a.lam, rank)
+    n = wl["n"]
+    s = SwapSystem(n, 2, wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"],
+                   lanes=a.lanes, blocks_per_sm=a.bps)
+    s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
+    s.compute_forces()
+    _, counts = s.nlist()
+    nn = float(counts[:, 1].mean())
+    nn_r = float(counts[:, 0].mean())
+    stream = s.stream
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    dt, kT, gamma = wl["dt"], wl["kT"], wl["gamma"]
+
+    # warm-up (grows the list if a rebuild overflows)
+    for _ in range(a.warmup):
+        s.run(a.md_steps, dt, kT, gamma, sync=True)
+    th0 = s.thermo()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    evs = []
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(a.md_steps, dt, kT, gamma, sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    s.sync()  # raises if the device reported an error during the timed launches
+    th1 = s.thermo()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = float(np.sum(launch_ms))
+    assert th1["step"] - th0["step"] == a.steps * a.md_steps, "timed launches did not complete"
+    rebuilds = (th1["n_rebuilds"] - th0["n_rebuilds"]) / a.steps
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    value = world * n * a.md_steps * a.steps / (total_ms / 1e3)
+
+    # roofline of the persistent step kernel (the only kernel in the timed region)
+    peak, peak_kind = _peaks()
+    b_alg = algorithmic_bytes(n, a.md_steps, nn, nn_r, rebuilds)
+    achieved = b_alg / (float(np.mean(launch_ms)) / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": _profile_traffic(n, a.md_steps),
+            "peak_kind": peak_kind, "alg_bytes_per_launch": b_alg,
+            "nn_mean": nn, "nn_reactive_mean": nn_r, "rebuilds_per_launch": rebuilds}
+
+    # end to end through the C-ABI with host buffers: pinned state in, run,
+    # thermo record out, every step
+    e2e = None
+    if not a.no_e2e:
+        xh = torch.from_numpy(np.ascontiguousarray(wl["x"])).pin_memory()
+        vh = torch.from_numpy(np.ascontiguousarray(wl["v"])).pin_memory()
+        th_ = torch.from_numpy(np.ascontiguousarray(wl["types"], dtype=np.int32)).pin_memory()
+        mh = torch.from_numpy(np.ascontiguousarray(wl["mass"])).pin_memory()
+        h2d = xh.numel() * 8 + vh.numel() * 8 + th_.numel() * 4 + mh.numel() * 8
+        ctx = s.ctx
+        times = []
+        for k in range(a.warmup + a.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A.swp_set_state(ctx, xh, vh, th_, mh, None, A.SWP_HOST)
+            A.swp_step_nvt(ctx, dt, kT, gamma, a.md_steps)
+            rec = A.swp_read_thermo(ctx)
+            el = time.perf_counter() - t0
+            if k >= a.warmup:
+                times.append(el)
+        tt = torch.tensor([float(np.sum(times))], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n * a.md_steps * a.steps / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": CTL_BYTES,
+               "last_U": float(rec.U2 + rec.U3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        v, steps_done, el = cpu_oracle_sample(wl, a.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"N={n}, {steps_done} BAOAB steps of the FP64 C oracle (explicit triplet "
+                         f"loop, cell list every step), {el:.1f} s, 1 thread"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": _config(a, n, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": a.steps, "clocks": clk, "wall_s_timed": t_wall,
+               "kernel_digest": _kernel_digest(),
+               "thermo_last": {"U2": th1["U2"], "U3": th1["U3"], "K": th1["K"],
+                               "n_bonds": th1["n_bonds"]}}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    s.close()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

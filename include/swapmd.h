@@ -1,0 +1,204 @@
+/*
+ * swapmd.h -- C-ABI of the GB300 (sm_103a) associative bond-swap MD library.
+ *
+ * The library evaluates, every time step, the two-body bonding potential of
+ * reactive type pairs, Eq. 2b of Ciarella & Ellenbroek ("Associative bond
+ * swaps in molecular dynamics"):
+ *     v(r) = 4 eps [(sigma/r)^(2n) - (sigma/r)^n],  r < r_cut,
+ * plus the three-body swap term of Eq. 3bp,
+ *     v3_ijk = lambda eps vh(r_ij) vh(r_ik)   (centre i, unordered {j, k}),
+ * with vh the normalised two-body term of Eq. pot (1 inside
+ * r_min = sigma 2^(1/n), -v/eps beyond), and repulsive WCA between like
+ * types (section "Effect of swaps").  It returns forces, the two- and
+ * three-body energies, the virial of Eq. p3 and the bond count, over a Verlet
+ * neighbour list built from a cell list, and advances the system with velocity
+ * Verlet (NVE) or BAOAB Langevin (NVT, the paper's "canonical Langevin
+ * dynamics", section "Self-assembly pitfalls").
+ *
+ * Conventions
+ *  - Every call returns an int status: SWP_OK (0) or a negative SWP_ERR_*.
+ *    No call throws.  swp_last_error() gives a message owned by the context,
+ *    valid until the next call on it.
+ *  - Calls that launch work are asynchronous on the stream given to
+ *    swp_bind_workspace().  Errors raised on the device (neighbour-row
+ *    overflow, a device wait past its time bound, non-finite forces) are
+ *    latched and reported by the next swp_sync() or swp_read_*() call.
+ *  - Particle arrays exchanged with the caller are in USER order: entry i
+ *    belongs to the particle given as entry i to swp_set_state() (its tag).
+ *    Internally particles are re-ordered by cell; nothing of that leaks out.
+ *  - Positions are 3 doubles per particle (x, y, z), row-major [n][3].
+ *  - `where` is SWP_HOST (pointer in host memory; pinned or pageable) or
+ *    SWP_DEVICE (pointer in device memory of the bound device).
+ *  - Ownership: the library allocates NO device memory.  The caller allocates
+ *    the workspace and the neighbour-list buffer (sizes from
+ *    swp_workspace_size() / swp_nlist_size()) and keeps them alive until
+ *    swp_destroy() or until they are re-bound.  The context object itself is
+ *    host memory owned by the library (swp_create / swp_destroy).
+ */
+#ifndef SWAPMD_H
+#define SWAPMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SWP_API __attribute__((visibility("default")))
+#else
+#define SWP_API
+#endif
+
+#define SWP_ABI_VERSION 1
+
+/* Status codes. */
+#define SWP_OK 0
+#define SWP_ERR_INVALID (-1)         /* bad argument; the context is unchanged */
+#define SWP_ERR_CUDA (-2)            /* a CUDA runtime call failed (no device, launch error) */
+#define SWP_ERR_NLIST_OVERFLOW (-3)  /* a neighbour row exceeded max_nn: grow it (see below) */
+#define SWP_ERR_TIMEOUT (-4)         /* a device-side wait ran past its bound; state lost */
+#define SWP_ERR_STATE (-5)           /* call out of order (nothing bound / no state set) */
+#define SWP_ERR_NONFINITE (-6)       /* a non-finite force was produced */
+
+/* Arithmetic precision of a context. */
+#define SWP_FP32 0 /* FP32 pair/three-body arithmetic, FP64 reductions, 64-bit fixed-point positions */
+#define SWP_FP64 1 /* FP64 everywhere (parity and validation) */
+
+/* Kinds of type pairs. */
+#define SWP_PAIR_NONE 0 /* no interaction */
+#define SWP_PAIR_WCA 1  /* Eq. 2b cut at r_min and shifted up by eps: purely repulsive */
+#define SWP_PAIR_SWAP 2 /* Eq. 2b two-body term plus the Eq. 3bp three-body term */
+
+#define SWP_HOST 0
+#define SWP_DEVICE 1
+
+typedef struct swp_ctx swp_ctx;
+
+/* Thermodynamic record of the last force evaluation (one time step). */
+typedef struct {
+    double U2;        /* two-body energy (sum of Eq. 2b / WCA over interacting pairs) */
+    double U3;        /* three-body energy (sum of Eq. 3bp over centres and partner pairs) */
+    double K;         /* kinetic energy sum 1/2 m v^2 at the same time */
+    double W[6];      /* virial sum over pairs r_ij (x) F_ij: xx, yy, zz, xy, xz, yz (Eq. p3 for
+                         the three-body part; pressure = (2K/3 + tr W / 3) / V) */
+    int64_t n_bonds;  /* reactive pairs closer than their bond radius */
+    int64_t step;     /* completed time steps of the state */
+    int64_t n_rebuilds;  /* neighbour-list builds since swp_set_state() */
+    int64_t steps_done;  /* steps completed by the last step call */
+    int32_t max_row;     /* longest neighbour row of the last build */
+    int32_t state;       /* 0: forces current; 1: forces stale; 2: inside a step (after overflow) */
+} swp_thermo;
+
+/* ABI version (SWP_ABI_VERSION); needs no device. */
+SWP_API int swp_abi_version(void);
+
+/* Create a context for n particles of n_types types (1..8) in a periodic
+ * orthorhombic box box[3] (> 0).  precision is SWP_FP32 or SWP_FP64; seed
+ * keys the Langevin noise.  In FP32 the box lengths are rounded to float32;
+ * in both the box is then rounded to the 2^-48 fixed-point grid.  Uses the
+ * current CUDA device.  n may be 0 (every call is then a no-op).  n < 2^27.
+ * Errors: SWP_ERR_INVALID for bad sizes, SWP_ERR_CUDA if no device. */
+SWP_API int swp_create(swp_ctx** out, int n, int n_types, const double box[3], int precision,
+               uint64_t seed);
+
+/* Set the coefficients of type pair (ti, tj) (symmetric), the per-type-pair
+ * table of the paper's pair_coeff.set(types, types, sigma, n, epsilon,
+ * lambda3) (section "The swap potential").  kind is SWP_PAIR_*; n_exp is the
+ * exponent n of Eq. 2b (1..128); rcut is r_cut of Eq. 2b (SWAP only; WCA is
+ * cut at r_min); lambda3 is lambda of Eq. 3bp (>= 0, SWAP only).  shift = 1
+ * selects the shifted form v - v(r_cut), vh = (v(r_cut) - v)/(eps + v(r_cut))
+ * (continuous at r_cut); 0 is the paper's literal form.  rbond is the bond
+ * radius (a reactive pair closer than it counts as a bond); <= 0 selects the
+ * distance where vh = 1/2.  All pairs default to SWP_PAIR_NONE.
+ * Errors: SWP_ERR_INVALID.  Marks the forces and the neighbour list stale. */
+SWP_API int swp_set_pair(swp_ctx* ctx, int ti, int tj, int kind, double eps, double sigma, int n_exp,
+                 double rcut, double lambda3, int shift, double rbond);
+
+/* Neighbour-list skin (>= 0; list radius of a pair = its cut-off + skin) and
+ * row length max_nn (>= 1).  Call before swp_nlist_size / swp_bind_nlist.
+ * The box must hold >= 3 cells of edge max(cut-off) + skin per dimension:
+ * SWP_ERR_INVALID otherwise. */
+SWP_API int swp_set_nlist(swp_ctx* ctx, double skin, int max_nn);
+
+/* Bytes of device workspace this context needs (state, cell list, staging). */
+SWP_API int swp_workspace_size(const swp_ctx* ctx, size_t* bytes);
+
+/* Bytes of the neighbour-list buffer for the current max_nn. */
+SWP_API int swp_nlist_size(const swp_ctx* ctx, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= the size above) and
+ * the CUDA stream (cudaStream_t, may be NULL) every later call enqueues on.
+ * Binding a workspace discards any state (call swp_set_state after). */
+SWP_API int swp_bind_workspace(swp_ctx* ctx, void* device_ptr, size_t bytes, void* cuda_stream);
+
+/* Bind the neighbour-list buffer.  May be re-bound with a larger max_nn after
+ * SWP_ERR_NLIST_OVERFLOW without losing the state; marks the list stale. */
+SWP_API int swp_bind_nlist(swp_ctx* ctx, void* device_ptr, size_t bytes);
+
+/* Set the state in user order: x [n][3] (any real numbers: wrapped into the
+ * box, the wraps added to img), v [n][3] (NULL: zero), type [n] (NULL: all 0),
+ * mass [n] (> 0; NULL: all 1), img [n][3] (NULL: zero).  All pointers are of
+ * kind `where`.  Resets the step counter to 0.  Forces become stale. */
+SWP_API int swp_set_state(swp_ctx* ctx, const double* x, const double* v, const int32_t* type,
+                  const double* mass, const int32_t* img, int where);
+
+/* Set the step counter (keys the Langevin noise: resuming a saved state with
+ * its step gives the same trajectory). */
+SWP_API int swp_set_step(swp_ctx* ctx, int64_t step);
+
+/* Rebuild the cell list and the neighbour list now (normally automatic). */
+SWP_API int swp_build_nlist(swp_ctx* ctx);
+
+/* Bring forces, energies, virial and bond count up to date for the current
+ * positions (no time advance, except that a step interrupted by an overflow
+ * is completed first). */
+SWP_API int swp_compute_forces(swp_ctx* ctx);
+
+/* Advance nsteps time steps of velocity Verlet (NVE), dt > 0. */
+SWP_API int swp_step_nve(swp_ctx* ctx, double dt, int nsteps);
+
+/* Advance nsteps time steps of BAOAB Langevin dynamics at temperature kT with
+ * friction gamma (> 0; gamma = 0 is velocity Verlet).  The noise of step s
+ * for particle with tag t is Philox4x32-10 with counter (t, s lo, s hi, 1)
+ * and key (seed lo, seed hi), Box-Muller normals.  The list is rebuilt on the
+ * device whenever the accumulated displacement bound exceeds skin/2.
+ * On SWP_ERR_NLIST_OVERFLOW (reported by the next sync), thermo.steps_done
+ * steps were completed and thermo.max_row gives the row length needed:
+ * re-bind a larger list and call again for the remaining steps. */
+SWP_API int swp_step_nvt(swp_ctx* ctx, double dt, double kT, double gamma, int nsteps);
+
+/* Wait for the stream and report latched device errors. */
+SWP_API int swp_sync(swp_ctx* ctx);
+
+/* Synchronising reads.  swp_read_thermo fills *out with the record of the
+ * last force evaluation.  swp_read_forces needs current forces (state 0):
+ * f [n][3].  swp_read_state: x [n][3] wrapped into [0, L), v [n][3], img
+ * [n][3]; any of them may be NULL.  Pointers of kind `where`. */
+SWP_API int swp_read_thermo(swp_ctx* ctx, swp_thermo* out);
+SWP_API int swp_read_forces(swp_ctx* ctx, double* f, int where);
+SWP_API int swp_read_state(swp_ctx* ctx, double* x, double* v, int32_t* img, int where);
+
+/* Neighbour rows in user order (device pointers only): rows [n][max_nn]
+ * holds the tags of each particle's list, reactive partners first;
+ * counts [n][2] = (reactive, total). */
+SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev);
+
+/* Launch shape of the step kernel: lanes per particle (1, 2, 4, 8, 16 or
+ * 32; default 4) and resident blocks per SM (0: as many as fit). */
+SWP_API int swp_set_launch(swp_ctx* ctx, int lanes, int blocks_per_sm);
+
+/* Bound, in nanoseconds, on every device-side wait (default 2 s). */
+SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);
+
+SWP_API const char* swp_last_error(const swp_ctx* ctx);
+
+/* Free the context (not the caller's device buffers). NULL is accepted. */
+SWP_API int swp_destroy(swp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWAPMD_H */

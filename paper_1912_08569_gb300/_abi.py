@@ -1,0 +1,252 @@
+"""ctypes binding of the C-ABI in ``include/swapmd.h``: argument marshalling only.
+
+Every function here has the name of the C entry point it calls and raises
+``SwpError`` on a negative status.  No arithmetic of the method happens in
+Python: every step of the path runs in the CUDA kernels of ``libswapmd.so``.
+The library must be built (``paper_1912_08569_gb300.build.build()``); loading
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswapmd.so")
+
+SWP_OK = 0
+SWP_ERR_INVALID = -1
+SWP_ERR_CUDA = -2
+SWP_ERR_NLIST_OVERFLOW = -3
+SWP_ERR_TIMEOUT = -4
+SWP_ERR_STATE = -5
+SWP_ERR_NONFINITE = -6
+
+SWP_FP32 = 0
+SWP_FP64 = 1
+SWP_PAIR_NONE = 0
+SWP_PAIR_WCA = 1
+SWP_PAIR_SWAP = 2
+SWP_HOST = 0
+SWP_DEVICE = 1
+
+ERROR_NAMES = {
+    SWP_ERR_INVALID: "SWP_ERR_INVALID",
+    SWP_ERR_CUDA: "SWP_ERR_CUDA",
+    SWP_ERR_NLIST_OVERFLOW: "SWP_ERR_NLIST_OVERFLOW",
+    SWP_ERR_TIMEOUT: "SWP_ERR_TIMEOUT",
+    SWP_ERR_STATE: "SWP_ERR_STATE",
+    SWP_ERR_NONFINITE: "SWP_ERR_NONFINITE",
+}
+
+# Every entry point declared in include/swapmd.h.
+EXPORTS = (
+    "swp_abi_version", "swp_create", "swp_set_pair", "swp_set_nlist", "swp_workspace_size",
+    "swp_nlist_size", "swp_bind_workspace", "swp_bind_nlist", "swp_set_state", "swp_set_step",
+    "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
+    "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch",
+    "swp_set_timeout", "swp_last_error", "swp_destroy",
+)
+
+
+class SwpError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        self.code = code
+        super().__init__(f"{where}: {ERROR_NAMES.get(code, code)}: {msg}")
+
+
+class swp_thermo(ctypes.Structure):
+    _fields_ = [
+        ("U2", ctypes.c_double),
+        ("U3", ctypes.c_double),
+        ("K", ctypes.c_double),
+        ("W", ctypes.c_double * 6),
+        ("n_bonds", ctypes.c_int64),
+        ("step", ctypes.c_int64),
+        ("n_rebuilds", ctypes.c_int64),
+        ("steps_done", ctypes.c_int64),
+        ("max_row", ctypes.c_int32),
+        ("state", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libswapmd.so (built in-tree); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library not built: {path} is missing; run paper_1912_08569_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "swp_abi_version": ([], c_int),
+        "swp_create": ([P(c_void_p), c_int, c_int, P(c_double), c_int, ctypes.c_uint64], c_int),
+        "swp_set_pair": ([c_void_p, c_int, c_int, c_int, c_double, c_double, c_int, c_double, c_double,
+                          c_int, c_double], c_int),
+        "swp_set_nlist": ([c_void_p, c_double, c_int], c_int),
+        "swp_workspace_size": ([c_void_p, P(c_size_t)], c_int),
+        "swp_nlist_size": ([c_void_p, P(c_size_t)], c_int),
+        "swp_bind_workspace": ([c_void_p, c_void_p, c_size_t, c_void_p], c_int),
+        "swp_bind_nlist": ([c_void_p, c_void_p, c_size_t], c_int),
+        "swp_set_state": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int], c_int),
+        "swp_set_step": ([c_void_p, ctypes.c_int64], c_int),
+        "swp_build_nlist": ([c_void_p], c_int),
+        "swp_compute_forces": ([c_void_p], c_int),
+        "swp_step_nve": ([c_void_p, c_double, c_int], c_int),
+        "swp_step_nvt": ([c_void_p, c_double, c_double, c_double, c_int], c_int),
+        "swp_sync": ([c_void_p], c_int),
+        "swp_read_thermo": ([c_void_p, P(swp_thermo)], c_int),
+        "swp_read_forces": ([c_void_p, c_void_p, c_int], c_int),
+        "swp_read_state": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int], c_int),
+        "swp_read_nlist": ([c_void_p, c_void_p, c_void_p], c_int),
+        "swp_set_launch": ([c_void_p, c_int, c_int], c_int),
+        "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
+        "swp_last_error": ([c_void_p], ctypes.c_char_p),
+        "swp_destroy": ([c_void_p], c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(ctx, rc: int, where: str):
+    if rc < 0:
+        msg = load_library().swp_last_error(ctx)
+        raise SwpError(rc, where, (msg or b"").decode(errors="replace"))
+    return rc
+
+
+def _ptr(a):
+    """Address of a numpy array / torch tensor (or None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def swp_abi_version() -> int:
+    return load_library().swp_abi_version()
+
+
+def swp_create(n: int, n_types: int, box, precision: int, seed: int):
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    rc = lib.swp_create(ctypes.byref(ctx), int(n), int(n_types), b, int(precision), int(seed))
+    if rc < 0:
+        raise SwpError(rc, "swp_create", "cannot create context (bad sizes or no CUDA device)")
+    return ctx
+
+
+def swp_set_pair(ctx, ti, tj, kind, eps=1.0, sigma=1.0, n_exp=6, rcut=0.0, lambda3=0.0, shift=0,
+                 rbond=0.0):
+    return _check(ctx, load_library().swp_set_pair(ctx, int(ti), int(tj), int(kind), float(eps),
+                                                   float(sigma), int(n_exp), float(rcut),
+                                                   float(lambda3), int(shift), float(rbond)),
+                  "swp_set_pair")
+
+
+def swp_set_nlist(ctx, skin: float, max_nn: int):
+    return _check(ctx, load_library().swp_set_nlist(ctx, float(skin), int(max_nn)), "swp_set_nlist")
+
+
+def swp_workspace_size(ctx) -> int:
+    v = ctypes.c_size_t()
+    _check(ctx, load_library().swp_workspace_size(ctx, ctypes.byref(v)), "swp_workspace_size")
+    return v.value
+
+
+def swp_nlist_size(ctx) -> int:
+    v = ctypes.c_size_t()
+    _check(ctx, load_library().swp_nlist_size(ctx, ctypes.byref(v)), "swp_nlist_size")
+    return v.value
+
+
+def swp_bind_workspace(ctx, dev_ptr: int, nbytes: int, stream: int):
+    return _check(ctx, load_library().swp_bind_workspace(ctx, ctypes.c_void_p(dev_ptr), nbytes,
+                                                         ctypes.c_void_p(stream)),
+                  "swp_bind_workspace")
+
+
+def swp_bind_nlist(ctx, dev_ptr: int, nbytes: int):
+    return _check(ctx, load_library().swp_bind_nlist(ctx, ctypes.c_void_p(dev_ptr), nbytes),
+                  "swp_bind_nlist")
+
+
+def swp_set_state(ctx, x, v=None, types=None, mass=None, img=None, where=SWP_HOST):
+    return _check(ctx, load_library().swp_set_state(ctx, _ptr(x), _ptr(v), _ptr(types), _ptr(mass),
+                                                    _ptr(img), int(where)), "swp_set_state")
+
+
+def swp_set_step(ctx, step: int):
+    return _check(ctx, load_library().swp_set_step(ctx, int(step)), "swp_set_step")
+
+
+def swp_build_nlist(ctx):
+    return _check(ctx, load_library().swp_build_nlist(ctx), "swp_build_nlist")
+
+
+def swp_compute_forces(ctx):
+    return _check(ctx, load_library().swp_compute_forces(ctx), "swp_compute_forces")
+
+
+def swp_step_nve(ctx, dt: float, nsteps: int):
+    return _check(ctx, load_library().swp_step_nve(ctx, float(dt), int(nsteps)), "swp_step_nve")
+
+
+def swp_step_nvt(ctx, dt: float, kT: float, gamma: float, nsteps: int):
+    return _check(ctx, load_library().swp_step_nvt(ctx, float(dt), float(kT), float(gamma), int(nsteps)),
+                  "swp_step_nvt")
+
+
+def swp_sync(ctx):
+    return _check(ctx, load_library().swp_sync(ctx), "swp_sync")
+
+
+def swp_read_thermo(ctx, check: bool = True) -> swp_thermo:
+    t = swp_thermo()
+    rc = load_library().swp_read_thermo(ctx, ctypes.byref(t))
+    if check:
+        _check(ctx, rc, "swp_read_thermo")
+    return t
+
+
+def swp_read_forces(ctx, out, where=SWP_HOST):
+    return _check(ctx, load_library().swp_read_forces(ctx, _ptr(out), int(where)), "swp_read_forces")
+
+
+def swp_read_state(ctx, x=None, v=None, img=None, where=SWP_HOST):
+    return _check(ctx, load_library().swp_read_state(ctx, _ptr(x), _ptr(v), _ptr(img), int(where)),
+                  "swp_read_state")
+
+
+def swp_read_nlist(ctx, rows_dev, counts_dev):
+    return _check(ctx, load_library().swp_read_nlist(ctx, _ptr(rows_dev), _ptr(counts_dev)),
+                  "swp_read_nlist")
+
+
+def swp_set_launch(ctx, lanes: int, blocks_per_sm: int = 0):
+    return _check(ctx, load_library().swp_set_launch(ctx, int(lanes), int(blocks_per_sm)),
+                  "swp_set_launch")
+
+
+def swp_set_timeout(ctx, ns: int):
+    return _check(ctx, load_library().swp_set_timeout(ctx, int(ns)), "swp_set_timeout")
+
+
+def swp_last_error(ctx) -> str:
+    return (load_library().swp_last_error(ctx) or b"").decode(errors="replace")
+
+
+def swp_destroy(ctx):
+    return load_library().swp_destroy(ctx)

@@ -1,0 +1,804 @@
+// Host side of the C-ABI declared in include/swapmd.h: validation, the
+// workspace layout, parameter tables, launches and the user-order exchange.
+// The library allocates no device memory; everything lives in the caller's
+// workspace and neighbour-list buffers.
+#include "swapmd.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "swp_internal.h"
+
+using namespace swp;
+
+namespace {
+
+struct PairHost {
+    int kind = KIND_NONE;
+    int n = 6;
+    int shift = 0;
+    double eps = 1.0, sigma = 1.0, lambda3 = 0.0, rcut = 0.0, rbond = 0.0;
+};
+
+__global__ void k_mark_stale(Ctl* ctl)
+{
+    if (ctl->state == 0) ctl->state = 1;
+    ctl->need_rebuild = 1;
+}
+
+__global__ void k_clear_status_bits(Ctl* ctl, int bits) { ctl->status &= ~bits; }
+
+}  // namespace
+
+struct swp_ctx {
+    int n = 0, ntypes = 1, precision = SWP_FP32;
+    double box[3] = {0, 0, 0};
+    uint64_t seed = 0;
+    double skin = 0.3;
+    int max_nn = 64;
+    PairHost pairs[kMaxTypes * kMaxTypes];
+    int nc[3] = {3, 3, 3};
+    int ncell = 27;
+    int device = 0, num_sms = 0;
+    int lanes = 4, bps_req = 0, grid = 0, max_blocks = 0;
+    long long timeout_ns = 2000000000LL;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* nl = nullptr;
+    size_t nl_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool ws_bound = false, nl_bound = false, state_set = false, table_dirty = true;
+    bool layout_dirty = true;
+    Dev<float> df;
+    Dev<double> dd;
+    Ctl hctl;
+    std::vector<int> cell_rank;
+    std::vector<unsigned char> table_host;
+    std::string err;
+};
+
+namespace {
+
+int fail(swp_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(swp_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, SWP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SWP_CUDA(c, call)                                          \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call);   \
+    } while (0)
+
+double pair_cut(const PairHost& p)
+{
+    if (p.kind == KIND_WCA) return p.sigma * std::pow(2.0, 1.0 / p.n);
+    if (p.kind == KIND_SWAP) return p.rcut;
+    return 0.0;
+}
+
+double lj(double r, double eps, double sigma, int n)
+{
+    double x = std::pow(sigma / r, (double)n);
+    return 4.0 * eps * (x * x - x);
+}
+
+double max_list_radius(const swp_ctx* c)
+{
+    double m = 0.0;
+    for (int t = 0; t < c->ntypes * c->ntypes; t++) {
+        double cut = pair_cut(c->pairs[t]);
+        if (cut > 0.0) m = std::max(m, cut + c->skin);
+    }
+    return m;
+}
+
+unsigned long long spread3(unsigned v)
+{
+    unsigned long long x = v & 0x3ff;
+    unsigned long long r = 0;
+    for (int b = 0; b < 10; b++) r |= ((x >> b) & 1ull) << (3 * b);
+    return r;
+}
+
+// Cell grid and its Morton order (cells that are close in space are close
+// in the sorted particle arrays, so neighbour gathers share cache lines).
+int derive_cells(swp_ctx* c)
+{
+    double rl = max_list_radius(c);
+    for (int d = 0; d < 3; d++) {
+        int k = rl > 0.0 ? (int)std::floor(c->box[d] / (rl * (1.0 + 1e-5))) : 3;
+        if (rl > 0.0 && k < 3)
+            return fail(c, SWP_ERR_INVALID,
+                        "box too small: each box length must hold 3 cells of edge max(cut-off) + skin");
+        c->nc[d] = std::max(3, std::min(k, 1024));
+    }
+    long long nce = (long long)c->nc[0] * c->nc[1] * c->nc[2];
+    if (nce > (1LL << 30)) return fail(c, SWP_ERR_INVALID, "too many cells");
+    c->ncell = (int)nce;
+    std::vector<std::pair<unsigned long long, int>> code(c->ncell);
+    for (int z = 0; z < c->nc[2]; z++)
+        for (int y = 0; y < c->nc[1]; y++)
+            for (int x = 0; x < c->nc[0]; x++) {
+                int lin = (z * c->nc[1] + y) * c->nc[0] + x;
+                code[lin] = {spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), lin};
+            }
+    std::sort(code.begin(), code.end());
+    c->cell_rank.assign(c->ncell, 0);
+    for (int r = 0; r < c->ncell; r++) c->cell_rank[code[r].second] = r;
+    return SWP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves the workspace; with base == nullptr only measures it.
+template <typename Real>
+size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
+{
+    typedef typename Dev<Real>::R4 R4;
+    const size_t n = (size_t)std::max(c->n, 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return base ? base + o : nullptr;
+    };
+    Ctl* ctl = (Ctl*)take(sizeof(Ctl));
+    PairP<Real>* table = (PairP<Real>*)take(sizeof(PairP<Real>) * kMaxTypes * kMaxTypes);
+    R4* pos0 = (R4*)take(sizeof(R4) * n);
+    R4* pos1 = (R4*)take(sizeof(R4) * n);
+    long long* xq0 = (long long*)take(sizeof(long long) * 3 * n);
+    long long* xq1 = (long long*)take(sizeof(long long) * 3 * n);
+    int* img0 = (int*)take(sizeof(int) * 3 * n);
+    int* img1 = (int*)take(sizeof(int) * 3 * n);
+    R4* vel0 = (R4*)take(sizeof(R4) * n);
+    R4* vel1 = (R4*)take(sizeof(R4) * n);
+    R4* force = (R4*)take(sizeof(R4) * n);
+    Real* S = (Real*)take(sizeof(Real) * n);
+    int2* ncnt = (int2*)take(sizeof(int2) * n);
+    int* cell_rank = (int*)take(sizeof(int) * c->ncell);
+    int* cell_cnt = (int*)take(sizeof(int) * c->ncell);
+    int* cell_start = (int*)take(sizeof(int) * (c->ncell + 1));
+    int* cell_fill = (int*)take(sizeof(int) * (c->ncell + n));
+    int* perm = (int*)take(sizeof(int) * n);
+    double* partials = (double*)take(sizeof(double) * 2 * c->max_blocks * kNQ);
+    double* io = (double*)take(sizeof(double) * 7 * n);
+    int* io_int = (int*)take(sizeof(int) * 4 * n);
+    if (d) {
+        d->n = c->n;
+        d->ntypes = c->ntypes;
+        d->max_nn = c->max_nn;
+        d->ncell = c->ncell;
+        for (int k = 0; k < 3; k++) {
+            d->nc[k] = c->nc[k];
+            long long q = (long long)std::llround(c->box[k] * kFix);
+            d->Lq[k] = q;
+            double L = (double)q * kInvFix;
+            d->L[k] = (Real)L;
+            d->hL[k] = (Real)(0.5 * (double)(Real)L);
+            d->inv_cw[k] = (Real)(c->nc[k] / L);
+        }
+        d->pos[0] = pos0;
+        d->pos[1] = pos1;
+        d->xq[0] = xq0;
+        d->xq[1] = xq1;
+        d->img[0] = img0;
+        d->img[1] = img1;
+        d->vel[0] = vel0;
+        d->vel[1] = vel1;
+        d->force = force;
+        d->S = S;
+        d->nlist = (int*)c->nl;
+        d->ncnt = ncnt;
+        d->cell_rank = cell_rank;
+        d->cell_cnt = cell_cnt;
+        d->cell_start = cell_start;
+        d->cell_fill = cell_fill;
+        d->perm = perm;
+        d->partials = partials;
+        d->ctl = ctl;
+        d->io = io;
+        d->io_int = io_int;
+        d->table = table;
+    }
+    return off;
+}
+
+size_t workspace_bytes(swp_ctx* c)
+{
+    return c->precision == SWP_FP64 ? layout<double>(c, nullptr, nullptr)
+                                    : layout<float>(c, nullptr, nullptr);
+}
+
+template <typename Real>
+void build_table(swp_ctx* c)
+{
+    c->table_host.assign(sizeof(PairP<Real>) * kMaxTypes * kMaxTypes, 0);
+    PairP<Real>* t = (PairP<Real>*)c->table_host.data();
+    for (int k = 0; k < c->ntypes * c->ntypes; k++) {
+        const PairHost& p = c->pairs[k];
+        PairP<Real> e;
+        std::memset(&e, 0, sizeof(e));
+        e.kind = p.kind;
+        e.nhalf = p.n / 2;
+        e.odd = p.n & 1;
+        e.four_eps = (Real)(4.0 * p.eps);
+        e.n_real = (Real)p.n;
+        e.sig2 = (Real)(p.sigma * p.sigma);
+        const double rmin = p.sigma * std::pow(2.0, 1.0 / p.n);
+        e.rmin2 = (Real)(rmin * rmin);
+        e.rlist2 = (Real)(-1.0);
+        if (p.kind == KIND_WCA) {
+            e.rc2 = (Real)(rmin * rmin);
+            e.ushift = (Real)p.eps;
+            e.inv_epshat = (Real)(1.0 / p.eps);
+            e.rlist2 = (Real)((rmin + c->skin) * (rmin + c->skin));
+            e.rbond2 = (Real)(-1.0);
+        } else if (p.kind == KIND_SWAP) {
+            const double vc = p.shift ? lj(p.rcut, p.eps, p.sigma, p.n) : 0.0;
+            e.rc2 = (Real)(p.rcut * p.rcut);
+            e.a = (Real)std::sqrt(p.lambda3 * p.eps);
+            e.inv_epshat = (Real)(1.0 / (p.eps + vc));
+            e.vshift = (Real)vc;
+            e.ushift = (Real)(-vc);
+            e.rlist2 = (Real)((p.rcut + c->skin) * (p.rcut + c->skin));
+            double rb = p.rbond > 0.0 ? p.rbond
+                                      : p.sigma * std::pow((1.0 - std::sqrt(0.5)) / 2.0, -1.0 / p.n);
+            e.rbond2 = (Real)(rb * rb);
+        }
+        t[k] = e;
+    }
+}
+
+template <typename Real>
+Dev<Real>& dev(swp_ctx* c);
+template <>
+Dev<float>& dev<float>(swp_ctx* c) { return c->df; }
+template <>
+Dev<double>& dev<double>(swp_ctx* c) { return c->dd; }
+
+int refresh_layout(swp_ctx* c)
+{
+    if (!c->ws_bound) return fail(c, SWP_ERR_STATE, "no workspace bound");
+    if (c->precision == SWP_FP64) layout<double>(c, (char*)c->ws, &c->dd);
+    else layout<float>(c, (char*)c->ws, &c->df);
+    if (c->precision == SWP_FP64) c->dd.nlist = (int*)c->nl;
+    else c->df.nlist = (int*)c->nl;
+    return SWP_OK;
+}
+
+Ctl* dev_ctl(swp_ctx* c) { return c->precision == SWP_FP64 ? c->dd.ctl : c->df.ctl; }
+
+int upload_table(swp_ctx* c)
+{
+    if (!c->table_dirty) return SWP_OK;
+    void* dst;
+    if (c->precision == SWP_FP64) {
+        build_table<double>(c);
+        dst = (void*)c->dd.table;
+    } else {
+        build_table<float>(c);
+        dst = (void*)c->df.table;
+    }
+    SWP_CUDA(c, cudaMemcpyAsync(dst, c->table_host.data(), c->table_host.size(),
+                                cudaMemcpyHostToDevice, c->stream));
+    c->table_dirty = false;
+    return SWP_OK;
+}
+
+int ready(swp_ctx* c, bool need_state)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (!c->ws_bound) return fail(c, SWP_ERR_STATE, "no workspace bound");
+    if (!c->nl_bound && c->n > 0) return fail(c, SWP_ERR_STATE, "no neighbour-list buffer bound");
+    if (need_state && !c->state_set) return fail(c, SWP_ERR_STATE, "no state set");
+    return SWP_OK;
+}
+
+int map_status(swp_ctx* c)
+{
+    int s = c->hctl.status;
+    if (s & kStatusTimeout) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "a device-side wait timed out (phase %lld); set the state again",
+                      c->hctl.timeout_at);
+        return fail(c, SWP_ERR_TIMEOUT, buf);
+    }
+    if (s & kStatusNonfinite) return fail(c, SWP_ERR_NONFINITE, "non-finite force; set the state again");
+    if (s & kStatusOverflow) {
+        cudaError_t e = cudaSuccess;
+        k_clear_status_bits<<<1, 1, 0, c->stream>>>(dev_ctl(c), kStatusOverflow);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "clear status");
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "neighbour row of %d entries exceeds max_nn = %d",
+                      c->hctl.max_row, c->max_nn);
+        return fail(c, SWP_ERR_NLIST_OVERFLOW, buf);
+    }
+    return SWP_OK;
+}
+
+// Waits for the stream and refreshes the host copy of the control block.
+int sync_ctl(swp_ctx* c)
+{
+    if (c->n == 0 || !c->state_set) {
+        SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+        return SWP_OK;
+    }
+    SWP_CUDA(c, cudaMemcpyAsync(&c->hctl, dev_ctl(c), sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return map_status(c);
+}
+
+template <typename Real>
+int run(swp_ctx* c, RunArgs a)
+{
+    Dev<Real>& d = dev<Real>(c);
+    int rc = upload_table(c);
+    if (rc) return rc;
+    int bps = 0;
+    SWP_CUDA(c, run_occupancy<Real>(kBlock, c->lanes, &bps));
+    if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
+    if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
+    bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
+    c->grid = c->num_sms * bps;
+    a.max_blocks = c->max_blocks;
+    a.timeout_ns = c->timeout_ns;
+    double margin = 0.0;
+    if (c->precision == SWP_FP32) {
+        double Lm = std::max(c->box[0], std::max(c->box[1], c->box[2]));
+        margin = 8.0 * Lm * std::ldexp(1.0, -24);
+    }
+    a.skin_eff = c->skin - margin;
+    a.seed = c->seed;
+    SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
+    SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->lanes, c->stream));
+    return SWP_OK;
+}
+
+int run_any(swp_ctx* c, RunArgs a)
+{
+    return c->precision == SWP_FP64 ? run<double>(c, a) : run<float>(c, a);
+}
+
+int mark_stale(swp_ctx* c)
+{
+    if (!c->ws_bound || !c->state_set || c->n == 0) return SWP_OK;
+    k_mark_stale<<<1, 1, 0, c->stream>>>(dev_ctl(c));
+    SWP_CUDA(c, cudaGetLastError());
+    return SWP_OK;
+}
+
+cudaMemcpyKind kind_to_dev(int where)
+{
+    return where == SWP_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+cudaMemcpyKind kind_from_dev(int where)
+{
+    return where == SWP_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+int swp_abi_version(void) { return SWP_ABI_VERSION; }
+
+int swp_create(swp_ctx** out, int n, int n_types, const double box[3], int precision,
+               uint64_t seed)
+{
+    if (!out) return SWP_ERR_INVALID;
+    *out = nullptr;
+    if (n < 0 || n >= kMaxTag || n_types < 1 || n_types > kMaxTypes || !box) return SWP_ERR_INVALID;
+    if (precision != SWP_FP32 && precision != SWP_FP64) return SWP_ERR_INVALID;
+    for (int k = 0; k < 3; k++)
+        if (!(box[k] > 0.0) || !std::isfinite(box[k]) || box[k] > 30000.0) return SWP_ERR_INVALID;
+    swp_ctx* c = new swp_ctx();
+    c->n = n;
+    c->ntypes = n_types;
+    c->precision = precision;
+    c->seed = seed;
+    for (int k = 0; k < 3; k++)
+        c->box[k] = precision == SWP_FP32 ? (double)(float)box[k] : box[k];
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        cudaGetLastError();
+        return SWP_ERR_CUDA;
+    }
+    c->max_blocks = c->num_sms * (2048 / kBlock);
+    std::memset(&c->hctl, 0, sizeof(Ctl));
+    if (derive_cells(c) != SWP_OK) {
+        delete c;
+        return SWP_ERR_INVALID;
+    }
+    *out = c;
+    return SWP_OK;
+}
+
+int swp_set_pair(swp_ctx* c, int ti, int tj, int kind, double eps, double sigma, int n_exp,
+                 double rcut, double lambda3, int shift, double rbond)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (ti < 0 || tj < 0 || ti >= c->ntypes || tj >= c->ntypes)
+        return fail(c, SWP_ERR_INVALID, "type index out of range");
+    if (kind != KIND_NONE && kind != KIND_WCA && kind != KIND_SWAP)
+        return fail(c, SWP_ERR_INVALID, "unknown pair kind");
+    PairHost p;
+    p.kind = kind;
+    if (kind != KIND_NONE) {
+        if (!(eps > 0.0) || !(sigma > 0.0) || n_exp < 1 || n_exp > 128 || !std::isfinite(eps) ||
+            !std::isfinite(sigma))
+            return fail(c, SWP_ERR_INVALID, "need eps > 0, sigma > 0, 1 <= n <= 128");
+        p.eps = eps;
+        p.sigma = sigma;
+        p.n = n_exp;
+    }
+    if (kind == KIND_SWAP) {
+        if (!(rcut > 0.0) || !std::isfinite(rcut) || !(lambda3 >= 0.0) || !std::isfinite(lambda3))
+            return fail(c, SWP_ERR_INVALID, "need r_cut > 0 and lambda >= 0");
+        if (shift != 0 && shift != 1) return fail(c, SWP_ERR_INVALID, "shift must be 0 or 1");
+        if (shift && !(eps + lj(rcut, eps, sigma, n_exp) > 0.0))
+            return fail(c, SWP_ERR_INVALID, "shifted form needs eps + v(r_cut) > 0");
+        p.rcut = rcut;
+        p.lambda3 = lambda3;
+        p.shift = shift;
+        p.rbond = std::isfinite(rbond) ? rbond : 0.0;
+    }
+    PairHost old_a = c->pairs[ti * c->ntypes + tj], old_b = c->pairs[tj * c->ntypes + ti];
+    c->pairs[ti * c->ntypes + tj] = p;
+    c->pairs[tj * c->ntypes + ti] = p;
+    int rc = derive_cells(c);
+    if (rc) {
+        c->pairs[ti * c->ntypes + tj] = old_a;
+        c->pairs[tj * c->ntypes + ti] = old_b;
+        derive_cells(c);
+        return rc;
+    }
+    c->table_dirty = true;
+    if (c->ws_bound) {
+        size_t need = workspace_bytes(c);
+        if (need > c->ws_bytes) {
+            c->ws_bound = false;
+            c->state_set = false;
+            return fail(c, SWP_ERR_STATE, "cell grid grew: workspace too small, bind a larger one");
+        }
+        refresh_layout(c);
+        SWP_CUDA(c, cudaMemcpyAsync((void*)(c->precision == SWP_FP64 ? c->dd.cell_rank : c->df.cell_rank),
+                                    c->cell_rank.data(), sizeof(int) * c->ncell,
+                                    cudaMemcpyHostToDevice, c->stream));
+    }
+    return mark_stale(c);
+}
+
+int swp_set_nlist(swp_ctx* c, double skin, int max_nn)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (!(skin >= 0.0) || !std::isfinite(skin) || max_nn < 1 || max_nn > 4096)
+        return fail(c, SWP_ERR_INVALID, "need skin >= 0 and 1 <= max_nn <= 4096");
+    double old_skin = c->skin;
+    int old_nn = c->max_nn;
+    c->skin = skin;
+    c->max_nn = max_nn;
+    int rc = derive_cells(c);
+    if (rc) {
+        c->skin = old_skin;
+        c->max_nn = old_nn;
+        derive_cells(c);
+        return rc;
+    }
+    c->table_dirty = true;
+    if (max_nn != old_nn) c->nl_bound = false;
+    if (c->ws_bound) {
+        size_t need = workspace_bytes(c);
+        if (need > c->ws_bytes) {
+            c->ws_bound = false;
+            c->state_set = false;
+            return fail(c, SWP_ERR_STATE, "cell grid grew: workspace too small, bind a larger one");
+        }
+        refresh_layout(c);
+        SWP_CUDA(c, cudaMemcpyAsync((void*)(c->precision == SWP_FP64 ? c->dd.cell_rank : c->df.cell_rank),
+                                    c->cell_rank.data(), sizeof(int) * c->ncell,
+                                    cudaMemcpyHostToDevice, c->stream));
+    }
+    return mark_stale(c);
+}
+
+int swp_workspace_size(const swp_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return SWP_ERR_INVALID;
+    *bytes = workspace_bytes(const_cast<swp_ctx*>(c));
+    return SWP_OK;
+}
+
+int swp_nlist_size(const swp_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return SWP_ERR_INVALID;
+    *bytes = align256(sizeof(int) * (size_t)std::max(c->n, 1) * c->max_nn);
+    return SWP_OK;
+}
+
+int swp_bind_workspace(swp_ctx* c, void* ptr, size_t bytes, void* stream)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (!ptr || ((uintptr_t)ptr & 255)) return fail(c, SWP_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (bytes < workspace_bytes(c)) return fail(c, SWP_ERR_INVALID, "workspace too small");
+    c->ws = ptr;
+    c->ws_bytes = bytes;
+    c->stream = (cudaStream_t)stream;
+    c->ws_bound = true;
+    c->state_set = false;
+    c->table_dirty = true;
+    refresh_layout(c);
+    SWP_CUDA(c, cudaMemcpyAsync((void*)(c->precision == SWP_FP64 ? c->dd.cell_rank : c->df.cell_rank),
+                                c->cell_rank.data(), sizeof(int) * c->ncell, cudaMemcpyHostToDevice,
+                                c->stream));
+    return upload_table(c);
+}
+
+int swp_bind_nlist(swp_ctx* c, void* ptr, size_t bytes)
+{
+    if (!c) return SWP_ERR_INVALID;
+    size_t need = 0;
+    swp_nlist_size(c, &need);
+    if (!ptr || ((uintptr_t)ptr & 255)) return fail(c, SWP_ERR_INVALID, "list buffer must be 256-byte aligned");
+    if (bytes < need) return fail(c, SWP_ERR_INVALID, "neighbour-list buffer too small");
+    c->nl = ptr;
+    c->nl_bytes = bytes;
+    c->nl_bound = true;
+    if (c->ws_bound) refresh_layout(c);
+    return mark_stale(c);
+}
+
+int swp_set_state(swp_ctx* c, const double* x, const double* v, const int32_t* type,
+                  const double* mass, const int32_t* img, int where)
+{
+    int rc = ready(c, false);
+    if (rc) return rc;
+    if (where != SWP_HOST && where != SWP_DEVICE) return fail(c, SWP_ERR_INVALID, "bad where");
+    const size_t n = (size_t)c->n;
+    if (n > 0 && !x) return fail(c, SWP_ERR_INVALID, "positions required");
+    if (where == SWP_HOST && n > 0) {
+        for (size_t i = 0; i < 3 * n; i++)
+            if (!std::isfinite(x[i]) || (v && !std::isfinite(v[i])))
+                return fail(c, SWP_ERR_INVALID, "non-finite position or velocity");
+        if (type)
+            for (size_t i = 0; i < n; i++)
+                if (type[i] < 0 || type[i] >= c->ntypes) return fail(c, SWP_ERR_INVALID, "type out of range");
+        if (mass)
+            for (size_t i = 0; i < n; i++)
+                if (!(mass[i] > 0.0) || !std::isfinite(mass[i])) return fail(c, SWP_ERR_INVALID, "mass must be > 0");
+    }
+    rc = upload_table(c);
+    if (rc) return rc;
+    double* io;
+    int* io_int;
+    Ctl* ctl;
+    if (c->precision == SWP_FP64) {
+        io = c->dd.io;
+        io_int = c->dd.io_int;
+        ctl = c->dd.ctl;
+    } else {
+        io = c->df.io;
+        io_int = c->df.io_int;
+        ctl = c->df.ctl;
+    }
+    std::memset(&c->hctl, 0, sizeof(Ctl));
+    c->hctl.state = 1;
+    c->hctl.need_rebuild = 1;
+    SWP_CUDA(c, cudaMemcpyAsync(ctl, &c->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    if (n == 0) {
+        c->state_set = true;
+        return SWP_OK;
+    }
+    SWP_CUDA(c, cudaMemcpyAsync(io, x, sizeof(double) * 3 * n, kind_to_dev(where), c->stream));
+    if (v) SWP_CUDA(c, cudaMemcpyAsync(io + 3 * n, v, sizeof(double) * 3 * n, kind_to_dev(where), c->stream));
+    else SWP_CUDA(c, cudaMemsetAsync(io + 3 * n, 0, sizeof(double) * 3 * n, c->stream));
+    if (mass) SWP_CUDA(c, cudaMemcpyAsync(io + 6 * n, mass, sizeof(double) * n, kind_to_dev(where), c->stream));
+    else {
+        std::vector<double> ones(n, 1.0);
+        SWP_CUDA(c, cudaMemcpyAsync(io + 6 * n, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (type) SWP_CUDA(c, cudaMemcpyAsync(io_int, type, sizeof(int) * n, kind_to_dev(where), c->stream));
+    else SWP_CUDA(c, cudaMemsetAsync(io_int, 0, sizeof(int) * n, c->stream));
+    if (img) SWP_CUDA(c, cudaMemcpyAsync(io_int + n, img, sizeof(int) * 3 * n, kind_to_dev(where), c->stream));
+    else SWP_CUDA(c, cudaMemsetAsync(io_int + n, 0, sizeof(int) * 3 * n, c->stream));
+    if (c->precision == SWP_FP64) SWP_CUDA(c, launch_set_state<double>(c->dd, c->stream));
+    else SWP_CUDA(c, launch_set_state<float>(c->df, c->stream));
+    c->state_set = true;
+    return SWP_OK;
+}
+
+int swp_set_step(swp_ctx* c, int64_t step)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (step < 0) return fail(c, SWP_ERR_INVALID, "step must be >= 0");
+    if (c->n == 0) return SWP_OK;
+    static_assert(sizeof(long long) == sizeof(int64_t), "step width");
+    long long s = (long long)step;
+    SWP_CUDA(c, cudaMemcpyAsync(&dev_ctl(c)->step, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+    SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SWP_OK;
+}
+
+int swp_build_nlist(swp_ctx* c)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (c->n == 0) return SWP_OK;
+    RunArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.build_only = 1;
+    return run_any(c, a);
+}
+
+int swp_compute_forces(swp_ctx* c)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (c->n == 0) return SWP_OK;
+    RunArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nsteps = 0;
+    return run_any(c, a);
+}
+
+static int step_common(swp_ctx* c, double dt, double kT, double gamma, int nsteps)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !(gamma >= 0.0) || !(kT >= 0.0) ||
+        !std::isfinite(gamma) || !std::isfinite(kT))
+        return fail(c, SWP_ERR_INVALID, "need dt > 0, nsteps >= 0, gamma >= 0, kT >= 0");
+    if (c->n == 0 || nsteps == 0) return SWP_OK;
+    RunArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nsteps = nsteps;
+    a.dt = dt;
+    a.langevin = gamma > 0.0 ? 1 : 0;
+    a.c1 = std::exp(-gamma * dt);
+    a.c2 = std::sqrt((1.0 - a.c1 * a.c1) * kT);
+    return run_any(c, a);
+}
+
+int swp_step_nve(swp_ctx* c, double dt, int nsteps) { return step_common(c, dt, 0.0, 0.0, nsteps); }
+
+int swp_step_nvt(swp_ctx* c, double dt, double kT, double gamma, int nsteps)
+{
+    return step_common(c, dt, kT, gamma, nsteps);
+}
+
+int swp_sync(swp_ctx* c)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (!c->ws_bound) return SWP_OK;
+    return sync_ctl(c);
+}
+
+int swp_read_thermo(swp_ctx* c, swp_thermo* out)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (!out) return fail(c, SWP_ERR_INVALID, "null output");
+    rc = sync_ctl(c);
+    std::memset(out, 0, sizeof(*out));
+    const Ctl& h = c->hctl;
+    out->U2 = h.thermo[Q_U2];
+    out->U3 = h.thermo[Q_U3];
+    out->K = h.thermo[Q_K];
+    for (int k = 0; k < 6; k++) out->W[k] = h.thermo[Q_W0 + k];
+    out->n_bonds = (int64_t)std::llround(h.thermo[Q_BONDS]);
+    out->step = h.step;
+    out->n_rebuilds = h.n_rebuilds;
+    out->steps_done = h.steps_done;
+    out->max_row = h.max_row;
+    out->state = h.state;
+    return rc;
+}
+
+int swp_read_forces(swp_ctx* c, double* f, int where)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (c->n == 0) return SWP_OK;
+    if (!f) return fail(c, SWP_ERR_INVALID, "null output");
+    rc = sync_ctl(c);
+    if (rc) return rc;
+    if (c->hctl.state != 0) return fail(c, SWP_ERR_STATE, "forces are not current: call swp_compute_forces");
+    double* io;
+    if (c->precision == SWP_FP64) {
+        SWP_CUDA(c, launch_get_forces<double>(c->dd, c->hctl.pos_cur, c->stream));
+        io = c->dd.io;
+    } else {
+        SWP_CUDA(c, launch_get_forces<float>(c->df, c->hctl.pos_cur, c->stream));
+        io = c->df.io;
+    }
+    SWP_CUDA(c, cudaMemcpyAsync(f, io, sizeof(double) * 3 * c->n, kind_from_dev(where), c->stream));
+    SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SWP_OK;
+}
+
+int swp_read_state(swp_ctx* c, double* x, double* v, int32_t* img, int where)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (c->n == 0) return SWP_OK;
+    rc = sync_ctl(c);
+    if (rc && rc != SWP_ERR_NLIST_OVERFLOW) return rc;
+    const size_t n = (size_t)c->n;
+    double* io;
+    int* io_int;
+    if (c->precision == SWP_FP64) {
+        SWP_CUDA(c, launch_get_state<double>(c->dd, c->hctl.pos_cur, c->hctl.arr_cur, c->stream));
+        io = c->dd.io;
+        io_int = c->dd.io_int;
+    } else {
+        SWP_CUDA(c, launch_get_state<float>(c->df, c->hctl.pos_cur, c->hctl.arr_cur, c->stream));
+        io = c->df.io;
+        io_int = c->df.io_int;
+    }
+    if (x) SWP_CUDA(c, cudaMemcpyAsync(x, io, sizeof(double) * 3 * n, kind_from_dev(where), c->stream));
+    if (v) SWP_CUDA(c, cudaMemcpyAsync(v, io + 3 * n, sizeof(double) * 3 * n, kind_from_dev(where), c->stream));
+    if (img) SWP_CUDA(c, cudaMemcpyAsync(img, io_int + n, sizeof(int) * 3 * n, kind_from_dev(where), c->stream));
+    SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+int swp_read_nlist(swp_ctx* c, int32_t* rows_dev, int32_t* counts_dev)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (c->n == 0) return SWP_OK;
+    if (!rows_dev || !counts_dev) return fail(c, SWP_ERR_INVALID, "null output");
+    rc = sync_ctl(c);
+    if (rc) return rc;
+    if (c->hctl.need_rebuild) return fail(c, SWP_ERR_STATE, "neighbour list is stale: call swp_build_nlist");
+    if (c->precision == SWP_FP64) SWP_CUDA(c, launch_get_nlist<double>(c->dd, c->hctl.pos_cur, rows_dev, counts_dev, c->stream));
+    else SWP_CUDA(c, launch_get_nlist<float>(c->df, c->hctl.pos_cur, rows_dev, counts_dev, c->stream));
+    SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SWP_OK;
+}
+
+int swp_set_launch(swp_ctx* c, int lanes, int blocks_per_sm)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(c, SWP_ERR_INVALID, "lanes must be 1, 2, 4, 8, 16 or 32");
+    if (blocks_per_sm < 0) return fail(c, SWP_ERR_INVALID, "blocks_per_sm must be >= 0");
+    c->lanes = lanes;
+    c->bps_req = blocks_per_sm;
+    return SWP_OK;
+}
+
+int swp_set_timeout(swp_ctx* c, int64_t ns)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (ns < 1000) return fail(c, SWP_ERR_INVALID, "timeout must be >= 1000 ns");
+    c->timeout_ns = (long long)ns;
+    return SWP_OK;
+}
+
+const char* swp_last_error(const swp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int swp_destroy(swp_ctx* c)
+{
+    delete c;
+    return SWP_OK;
+}
+
+}  // extern "C"

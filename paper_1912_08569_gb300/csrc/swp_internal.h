@@ -1,0 +1,148 @@
+// Internal layout shared by the CUDA kernels and the host side of the C-ABI.
+// Not part of the public interface (that is include/swapmd.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swp {
+
+constexpr int kMaxTypes = 8;       // type-pair table is kMaxTypes^2 entries at most
+constexpr int kNQ = 12;            // per-block thermo partials: see Q_* below
+constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
+constexpr int kBlock = 512;        // threads per block of the step kernel
+constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays clear)
+
+// Thermo quantities, in the order of the per-block partials.
+enum { Q_U2 = 0, Q_U3 = 1, Q_K = 2, Q_W0 = 3, Q_BONDS = 9, Q_SPARE0 = 10, Q_SPARE1 = 11 };
+
+// Fixed-point position unit: positions are int64 multiples of 2^-48 sigma.
+constexpr double kFix = 281474976710656.0;          // 2^48
+constexpr double kInvFix = 3.5527136788005009e-15;  // 2^-48
+
+enum PairKind { KIND_NONE = 0, KIND_WCA = 1, KIND_SWAP = 2 };
+
+// One type-pair entry, precomputed on the host in double and stored in the
+// arithmetic precision of the run.
+template <typename Real>
+struct PairP {
+    int kind;   // PairKind
+    int nhalf;  // exponent n = 2*nhalf + odd
+    int odd;
+    int pad;
+    Real four_eps;    // 4 eps
+    Real n_real;      // n
+    Real sig2;        // sigma^2
+    Real rc2;         // squared interaction cut-off (decision threshold)
+    Real rmin2;       // squared r_min = (sigma 2^(1/n))^2
+    Real a;           // sqrt(lambda eps): triplet prefactor factor
+    Real inv_epshat;  // 1 / (eps + v(r_cut)) shifted, 1 / eps unshifted
+    Real vshift;      // v(r_cut) shifted, 0 unshifted (vh = (vshift - v) inv_epshat)
+    Real ushift;      // two-body energy offset: -vshift (swap), +eps (wca)
+    Real rlist2;      // squared neighbour-list radius (decision threshold), < 0: never
+    Real rbond2;      // squared bond radius (decision threshold)
+};
+
+// Device-side control block (one per context, in the workspace).
+struct Ctl {
+    unsigned long long barrier;  // grid-barrier arrival counter (zeroed before each launch)
+    int status;                  // latched SWP_* error bits (see kStatus*)
+    int state;                   // 0: full step, forces valid; 1: forces invalid; 2: mid-step
+    int pos_cur;                 // which pos buffer holds the current snapshot
+    int arr_cur;                 // which xq/img/vel buffer set is current
+    int need_rebuild;            // set by the host after set_state / parameter changes
+    int max_row;                 // longest neighbour row seen by the last build
+    unsigned int dmax2[2];       // per-step max squared displacement (float bits), by parity
+    double disp;                 // displacement bound accumulated since the last build
+    long long step;              // completed time steps
+    long long n_rebuilds;
+    long long steps_done;        // steps completed by the last run call
+    long long timeout_at;        // diagnostic: phase id where a wait gave up
+    double thermo[kNQ];          // last reduced thermo record
+};
+
+// Status bits latched on the device.
+constexpr int kStatusOverflow = 1;
+constexpr int kStatusTimeout = 2;
+constexpr int kStatusNonfinite = 4;
+constexpr int kStatusBadCell = 8;
+
+template <typename Real>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    typedef float4 type;
+};
+struct alignas(32) dbl4 {
+    double x, y, z, w;
+};
+template <>
+struct Vec4<double> {
+    typedef dbl4 type;
+};
+
+// Pointers and sizes of one context's device state (passed by value).
+template <typename Real>
+struct Dev {
+    typedef typename Vec4<Real>::type R4;
+    int n;
+    int ntypes;
+    int max_nn;
+    int ncell;
+    int nc[3];
+    Real L[3];
+    Real hL[3];
+    Real inv_cw[3];  // cells per unit length
+    long long Lq[3]; // box in fixed-point units
+    R4* pos[2];      // snapshot (x, y, z, packed tag/type bits), ping-pong
+    long long* xq[2];  // fixed-point positions, SoA [3][n], two sets (reorder)
+    int* img[2];       // image counts, SoA [3][n], two sets
+    R4* vel[2];        // (vx, vy, vz, 1/m), two sets
+    R4* force;         // (fx, fy, fz, 0)
+    Real* S;           // per-centre sum of a*vh over reactive partners
+    int* nlist;        // [n][max_nn], reactive partners first
+    int2* ncnt;        // (n_reactive, n_total) per row
+    const int* cell_rank;  // cell linear index -> position in the sorted cell order
+    int* cell_cnt;     // [ncell]
+    int* cell_start;   // [ncell + 1]
+    int* cell_fill;    // [ncell]
+    int* perm;         // [n] new slot -> old slot
+    double* partials;  // [2][max_blocks][kNQ]
+    Ctl* ctl;
+    double* io;        // host-exchange staging: [3n] x, [3n] v, [n] mass
+    int* io_int;       // staging: [n] types, [3n] images
+    const PairP<Real>* table;  // [ntypes * ntypes]
+};
+
+// What one launch of the step kernel does.
+struct RunArgs {
+    int nsteps;         // time steps to advance (0: only bring forces up to date)
+    int build_only;     // 1: rebuild the neighbour list and stop
+    int force_rebuild;  // 1: rebuild before the first force evaluation
+    int langevin;       // 1: BAOAB with the O step; 0: velocity Verlet
+    double dt;
+    double c1;          // exp(-gamma dt)
+    double c2;          // sqrt((1 - c1^2) kT)
+    double skin_eff;    // rebuild when 2 * displacement bound > skin_eff
+    unsigned long long seed;
+    long long timeout_ns;  // bound on every device-side wait
+    int max_blocks;     // partials stride
+};
+
+// Host-side launchers (defined once per precision).
+template <typename Real>
+cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, int lanes,
+                       cudaStream_t s);
+template <typename Real>
+cudaError_t run_occupancy(int block, int lanes, int* blocks_per_sm);
+template <typename Real>
+cudaError_t launch_set_state(const Dev<Real>& d, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_get_state(const Dev<Real>& d, int pc, int ac, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_get_forces(const Dev<Real>& d, int pc, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts, cudaStream_t s);
+
+}  // namespace swp

@@ -1,0 +1,182 @@
+"""``SwapSystem``: one simulation on one GPU through the C-ABI.
+
+PyTorch provides only device memory (the workspace and the neighbour-list
+buffer the library borrows) and the CUDA stream.  The neighbour-list length is
+grown and the interrupted call resumed when the device reports an overflow.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import _abi as A
+
+
+def _round_up(x: int, m: int) -> int:
+    return ((x + m - 1) // m) * m
+
+
+class SwapSystem:
+    """n particles of n_types types in a periodic box, with a type-pair table.
+
+    pairs: {(ti, tj): dict(kind=1|2, eps, sigma, n, rcut, lambda3, shift, rbond)}
+    (kind 1 = WCA, 2 = swap).  precision: "fp32" or "fp64".
+    """
+
+    def __init__(self, n, n_types, box, pairs, precision="fp32", seed=0, skin=0.3, max_nn=None,
+                 lanes=4, blocks_per_sm=0, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("SwapSystem needs a CUDA device (no CPU fallback)")
+        A.load_library()
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.n = int(n)
+        self.n_types = int(n_types)
+        self.box = np.asarray(box, dtype=np.float64)
+        self.precision = A.SWP_FP64 if precision in ("fp64", A.SWP_FP64) else A.SWP_FP32
+        self.ctx = A.swp_create(self.n, self.n_types, self.box, self.precision, seed)
+        self.skin = float(skin)
+        for (ti, tj), p in pairs.items():
+            A.swp_set_pair(self.ctx, ti, tj, p.get("kind", 0), p.get("eps", 1.0), p.get("sigma", 1.0),
+                           p.get("n", 6), p.get("rcut", 0.0), p.get("lambda3", 0.0),
+                           p.get("shift", 0), p.get("rbond", 0.0) or 0.0)
+        if max_nn is None:
+            rl = max((p.get("rcut", 0.0) if p.get("kind") == 2 else p.get("sigma", 1.0) * 2 ** (1 / p.get("n", 6)))
+                     for p in pairs.values()) + self.skin if pairs else 1.0
+            rho = self.n / float(np.prod(self.box))
+            expect = rho * 4.0 / 3.0 * math.pi * rl ** 3
+            max_nn = max(16, _round_up(int(2.0 * expect + 16), 8))
+        self.max_nn = int(max_nn)
+        A.swp_set_nlist(self.ctx, self.skin, self.max_nn)
+        A.swp_set_launch(self.ctx, lanes, blocks_per_sm)
+        ws = A.swp_workspace_size(self.ctx)
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        A.swp_bind_workspace(self.ctx, self.workspace.data_ptr(), ws, self.stream.cuda_stream)
+        self._bind_nlist()
+        self.grows = 0
+
+    # -- buffers ------------------------------------------------------------
+    def _bind_nlist(self):
+        nb = A.swp_nlist_size(self.ctx)
+        self.nlist_buf = self.torch.empty(nb, dtype=self.torch.uint8, device=self.device)
+        A.swp_bind_nlist(self.ctx, self.nlist_buf.data_ptr(), nb)
+
+    def _grow(self, needed: int):
+        self.max_nn = _round_up(int(needed * 1.25) + 8, 8)
+        A.swp_set_nlist(self.ctx, self.skin, self.max_nn)
+        self._bind_nlist()
+        self.grows += 1
+
+    def set_launch(self, lanes: int, blocks_per_sm: int = 0):
+        A.swp_set_launch(self.ctx, lanes, blocks_per_sm)
+
+    def set_timeout(self, ns: int):
+        A.swp_set_timeout(self.ctx, ns)
+
+    # -- state --------------------------------------------------------------
+    def set_state(self, x, v=None, types=None, mass=None, img=None):
+        """Host arrays (numpy) or device tensors (torch, cuda) in user order."""
+        if hasattr(x, "is_cuda") and x.is_cuda:
+            where = A.SWP_DEVICE
+            t = self.torch
+            cv = lambda a, dt: None if a is None else a.to(device=self.device, dtype=dt).contiguous()
+            self._keep = [cv(x, t.float64), cv(v, t.float64), cv(types, t.int32), cv(mass, t.float64),
+                          cv(img, t.int32)]
+        else:
+            where = A.SWP_HOST
+            cv = lambda a, dt: None if a is None else np.ascontiguousarray(a, dtype=dt)
+            self._keep = [cv(x, np.float64), cv(v, np.float64), cv(types, np.int32), cv(mass, np.float64),
+                          cv(img, np.int32)]
+        A.swp_set_state(self.ctx, *self._keep, where=where)
+
+    def set_step(self, step: int):
+        A.swp_set_step(self.ctx, step)
+
+    # -- work ---------------------------------------------------------------
+    def _retry_overflow(self, call):
+        for _ in range(8):
+            call()
+            try:
+                A.swp_sync(self.ctx)
+                return
+            except A.SwpError as e:
+                if e.code != A.SWP_ERR_NLIST_OVERFLOW:
+                    raise
+                th = A.swp_read_thermo(self.ctx, check=False)
+                self._grow(th.max_row)
+        raise RuntimeError("neighbour list kept overflowing")
+
+    def build_nlist(self):
+        self._retry_overflow(lambda: A.swp_build_nlist(self.ctx))
+
+    def compute_forces(self):
+        self._retry_overflow(lambda: A.swp_compute_forces(self.ctx))
+
+    def run(self, nsteps: int, dt: float, kT: float = 0.0, gamma: float = 0.0, sync: bool = True):
+        """Advance nsteps (BAOAB if gamma > 0, else velocity Verlet)."""
+        if not sync:
+            A.swp_step_nvt(self.ctx, dt, kT, gamma, nsteps)
+            return
+        remaining = [int(nsteps)]
+
+        def call():
+            A.swp_step_nvt(self.ctx, dt, kT, gamma, remaining[0])
+
+        for _ in range(16):
+            call()
+            try:
+                A.swp_sync(self.ctx)
+                return
+            except A.SwpError as e:
+                if e.code != A.SWP_ERR_NLIST_OVERFLOW:
+                    raise
+                th = A.swp_read_thermo(self.ctx, check=False)
+                remaining[0] -= int(th.steps_done)
+                self._grow(th.max_row)
+        raise RuntimeError("neighbour list kept overflowing")
+
+    def sync(self):
+        A.swp_sync(self.ctx)
+
+    # -- read-out -----------------------------------------------------------
+    def thermo(self) -> dict:
+        t = A.swp_read_thermo(self.ctx)
+        return dict(U2=t.U2, U3=t.U3, K=t.K, W=np.array(list(t.W)), n_bonds=int(t.n_bonds),
+                    step=int(t.step), n_rebuilds=int(t.n_rebuilds), steps_done=int(t.steps_done),
+                    max_row=int(t.max_row), state=int(t.state))
+
+    def forces(self) -> np.ndarray:
+        f = np.zeros((max(self.n, 1), 3))
+        A.swp_read_forces(self.ctx, f)
+        return f[: self.n]
+
+    def state(self):
+        x = np.zeros((max(self.n, 1), 3))
+        v = np.zeros((max(self.n, 1), 3))
+        img = np.zeros((max(self.n, 1), 3), dtype=np.int32)
+        A.swp_read_state(self.ctx, x, v, img)
+        return x[: self.n], v[: self.n], img[: self.n]
+
+    def nlist(self):
+        """(rows, counts): rows[i, :counts[i,1]] are the tags in i's list, reactive first."""
+        t = self.torch
+        rows = t.full((max(self.n, 1), self.max_nn), -1, dtype=t.int32, device=self.device)
+        counts = t.zeros((max(self.n, 1), 2), dtype=t.int32, device=self.device)
+        A.swp_read_nlist(self.ctx, rows, counts)
+        return rows.cpu().numpy()[: self.n], counts.cpu().numpy()[: self.n]
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            A.swp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

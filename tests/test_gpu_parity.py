@@ -1,0 +1,199 @@
+"""GPU path vs the FP64 oracle, element by element, through the C-ABI.
+
+Neighbour-list membership and bond counts bit-exact; forces, energies and
+virial within 1e-5 (FP32) / 1e-12 (FP64) of the oracle's error scales.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, assert_forces_match, assert_thermo_match, make_gpu, oracle_pairs
+from paper_1912_08569_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_08569_gb300.build import build
+
+    build()
+
+
+def _wl(name="mix2k", lam=1.0, n=None, density=None, seed=1, shift=0):
+    return inputs.workload(name, lambda3=lam, n=n, density=density, seed=seed, shift=shift)
+
+
+def _oracle(orc, wl, fp32):
+    return orc.forces(wl["x"], wl["types"], wl["n_types"], oracle_pairs(orc, wl), wl["box"], fp32=fp32)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("n,density", [(2000, 0.2), (3001, 0.5)])
+def test_nlist_membership_bitexact(orc, precision, n, density):
+    wl = _wl(n=n, density=density)
+    s = make_gpu(wl, precision)
+    s.build_nlist()
+    rows, counts = s.nlist()
+    fp32 = precision == "fp32"
+    ref = orc.nlist(wl["x"], wl["types"], 2, oracle_pairs(orc, wl), wl["box"], wl["skin"], fp32=fp32)
+    react = wl["types"][:, None] != wl["types"][None, :]  # A-B is the only swap pair
+    for i in range(n):
+        got = rows[i, : counts[i, 1]]
+        assert np.array_equal(np.sort(got), ref[i]), i
+        nr = counts[i, 0]
+        # reactive partners first, then the others
+        assert np.all(wl["types"][got[:nr]] != wl["types"][i])
+        assert np.all(wl["types"][got[nr:]] == wl["types"][i])
+    assert counts[:, 1].sum() == sum(len(r) for r in ref)
+    del react
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 5.0])
+def test_forces_config_small(orc, precision, lam):
+    wl = _wl("mix2k", lam=lam)
+    s = make_gpu(wl, precision)
+    s.compute_forces()
+    F = s.forces()
+    th = s.thermo()
+    ref = _oracle(orc, wl, precision == "fp32")
+    tol = TOL[precision]
+    assert_forces_match(F, ref, tol, f"{precision} lam={lam}")
+    assert_thermo_match(th, ref, tol, f"{precision} lam={lam}")
+    K = 0.5 * (wl["v"] ** 2).sum()
+    assert th["K"] == pytest.approx(K, rel=1e-6 if precision == "fp32" else 1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_forces_dense_ragged_all_lane_shapes(orc, precision, lanes):
+    # density 0.5, a size that is no multiple of any tile, every launch shape
+    wl = _wl("mix2k", lam=2.0, n=4099, density=0.5, seed=3)
+    s = make_gpu(wl, precision, lanes=lanes)
+    s.compute_forces()
+    ref = _oracle(orc, wl, precision == "fp32")
+    assert_forces_match(s.forces(), ref, TOL[precision], f"lanes={lanes}")
+    assert_thermo_match(s.thermo(), ref, TOL[precision], f"lanes={lanes}")
+
+
+def test_forces_full_size_100k(orc):
+    # the benchmark's workload at full size, every element against the oracle
+    wl = _wl("mix100k", lam=1.0)
+    s = make_gpu(wl, "fp32")
+    s.compute_forces()
+    ref = _oracle(orc, wl, True)
+    assert_forces_match(s.forces(), ref, TOL["fp32"], "100k")
+    assert_thermo_match(s.thermo(), ref, TOL["fp32"], "100k")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_shifted_form_and_noncubic_box(orc, precision):
+    n = 1500
+    box = inputs.f32(np.array([14.0, 11.5, 17.25]))
+    x = inputs.rsa_positions(n, box, 0.9, seed=4)
+    wl = dict(n=n, n_types=2, box=box, x=x, types=inputs.alternating_types(n),
+              v=inputs.maxwell_velocities(n, 0.1, 1.0, seed=5), mass=np.ones(n),
+              pairs=inputs.swap_pairs(lambda3=3.0, shift=1), skin=0.25, seed=1)
+    s = make_gpu(wl, precision)
+    s.compute_forces()
+    ref = _oracle(orc, wl, precision == "fp32")
+    assert_forces_match(s.forces(), ref, TOL[precision])
+    assert_thermo_match(s.thermo(), ref, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_three_types_mixed_coefficients(orc, precision):
+    # reading of mixed coefficients: prefactor sqrt(l_ij e_ij l_ik e_ik)
+    n = 2000
+    box = inputs.cubic_box(n, 0.35)
+    x = inputs.rsa_positions(n, box, 0.88, seed=8)
+    sw1 = dict(kind=2, eps=1.0, sigma=1.0, n=10, rcut=1.5, lambda3=1.5, rbond=1.2)
+    sw2 = dict(kind=2, eps=2.0, sigma=0.9, n=8, rcut=1.4, lambda3=0.7, rbond=1.1)
+    wca = dict(kind=1, eps=1.0, sigma=1.0, n=6)
+    pairs = {(0, 1): sw1, (0, 2): sw2, (1, 2): wca, (0, 0): wca, (1, 1): wca, (2, 2): wca}
+    wl = dict(n=n, n_types=3, box=box, x=x, types=(np.arange(n) % 3).astype(np.int32),
+              v=np.zeros((n, 3)), mass=np.ones(n), pairs=pairs, skin=0.3, seed=1)
+    s = make_gpu(wl, precision)
+    s.compute_forces()
+    ref = orc.forces(x, wl["types"], 3, orc.pair_table(3, pairs), box, fp32=precision == "fp32")
+    assert_forces_match(s.forces(), ref, TOL[precision])
+    assert_thermo_match(s.thermo(), ref, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_degenerate_systems(orc, precision):
+    box = np.array([12.0, 12.0, 12.0])
+    pairs = inputs.swap_pairs(lambda3=1.0)
+    # one particle, a bonded dimer, a triad in the flat-barrier regime, and
+    # a system with no reactive pairs at all
+    cases = [
+        (np.array([[1.0, 2.0, 3.0]]), np.array([0], dtype=np.int32)),
+        (np.array([[5.0, 5.0, 5.0], [6.0625, 5.0, 5.0]]), np.array([0, 1], dtype=np.int32)),
+        (np.array([[6.0, 6.0, 6.0], [7.0, 6.0, 6.0], [5.0, 6.75, 6.0]]), np.array([1, 0, 0], dtype=np.int32)),
+        (inputs.rsa_positions(40, box, 0.95, seed=2), np.zeros(40, dtype=np.int32)),
+        # particles straddling the periodic boundary
+        (np.array([[0.125, 6.0, 6.0], [11.5, 6.0, 6.0], [0.5, 11.75, 0.25]]), np.array([0, 1, 1], dtype=np.int32)),
+    ]
+    for x, ty in cases:
+        n = len(x)
+        wl = dict(n=n, n_types=2, box=box, x=x, types=ty, v=np.zeros((n, 3)), mass=np.ones(n),
+                  pairs=pairs, skin=0.3, seed=0)
+        s = make_gpu(wl, precision)
+        s.compute_forces()
+        ref = _oracle(orc, wl, precision == "fp32")
+        assert_forces_match(s.forces(), ref, TOL[precision], f"n={n}")
+        assert_thermo_match(s.thermo(), ref, TOL[precision], f"n={n}")
+        s.close()
+
+
+def test_empty_system():
+    from paper_1912_08569_gb300 import SwapSystem
+
+    s = SwapSystem(0, 2, [10.0, 10.0, 10.0], inputs.swap_pairs())
+    s.set_state(np.zeros((0, 3)))
+    s.compute_forces()
+    s.run(10, 0.001, 0.1, 1.0)
+    th = s.thermo()
+    assert th["U2"] == 0.0 and th["n_bonds"] == 0
+    assert s.forces().shape == (0, 3)
+
+
+def test_overflow_is_reported_and_recovered(orc):
+    from paper_1912_08569_gb300 import _abi as A
+
+    wl = _wl("mix2k", lam=1.0, n=2000, density=0.5)
+    s = make_gpu(wl, "fp32", max_nn=4)
+    # the raw call reports the overflow ...
+    A.swp_compute_forces(s.ctx)
+    with pytest.raises(A.SwpError) as e:
+        A.swp_sync(s.ctx)
+    assert e.value.code == A.SWP_ERR_NLIST_OVERFLOW
+    need = A.swp_read_thermo(s.ctx, check=False).max_row
+    assert need > 4
+    # ... and the wrapper grows the list and gets the right forces
+    s.compute_forces()
+    assert s.max_nn >= need
+    ref = _oracle(orc, wl, True)
+    assert_forces_match(s.forces(), ref, TOL["fp32"])
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_1912_08569_gb300 import _abi as A
+
+    with pytest.raises(A.SwpError):
+        A.swp_create(10, 9, [10, 10, 10], A.SWP_FP32, 0)
+    ctx = A.swp_create(10, 2, [10, 10, 10], A.SWP_FP32, 0)
+    with pytest.raises(A.SwpError):
+        A.swp_set_pair(ctx, 0, 1, A.SWP_PAIR_SWAP, eps=-1.0, sigma=1.0, n_exp=10, rcut=1.5, lambda3=1.0)
+    with pytest.raises(A.SwpError):
+        A.swp_set_pair(ctx, 0, 5, A.SWP_PAIR_WCA)
+    with pytest.raises(A.SwpError):  # box holds fewer than 3 cells of edge 4.0 + 0.3
+        A.swp_set_pair(ctx, 0, 1, A.SWP_PAIR_SWAP, eps=1.0, sigma=1.0, n_exp=10, rcut=4.0, lambda3=1.0)
+    with pytest.raises(A.SwpError):  # nothing bound yet
+        A.swp_compute_forces(ctx)
+    with pytest.raises(A.SwpError):
+        A.swp_set_launch(ctx, 3, 0)
+    A.swp_destroy(ctx)
