@@ -192,6 +192,37 @@ SWP_API int swp_set_launch(swp_ctx* ctx, int lanes, int blocks_per_sm);
 /* Bound, in nanoseconds, on every device-side wait (default 2 s). */
 SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);
 
+/* Forces without any device allocation.  The paper has no counterpart: this
+ * serves callers that cannot allocate device memory when they need forces --
+ * code running inside a host framework whose memory pool has reserved the
+ * device and forbids side allocations, code driven from inside a stream
+ * capture, or a latency-bound loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc / cudaFree.  It neither allocates nor frees
+ * anything and needs no bound workspace or list buffer.
+ *
+ * Uses the coefficients, skin, max_nn and launch shape of ctx.  Inputs: x_dev
+ * [n][3] positions and type_dev [n] types (NULL: all 0), device pointers.
+ * Outputs (device pointers): f_dev [n][3] forces; thermo_dev (may be NULL)
+ * [9] = U2, U3, W xx yy zz xy xz yz, n_bonds.  Velocities are taken as zero
+ * and masses as one; the context's own state is not touched.
+ *
+ * Scratch: a file-scope device array of SWP_STATIC_SCRATCH_BYTES (8 MiB)
+ * that every GPU loading this library keeps until the process exits.  The
+ * state copy, cell list and neighbour list of the system must fit in it
+ * (about 10,000 particles at max_nn 64 and liquid densities); larger systems
+ * are rejected with SWP_ERR_INVALID and a message giving the bytes needed.
+ * Every call shares that one array and leaves its contents behind (each call
+ * re-initialises what must start at zero), so calls that overlap on the GPU
+ * -- from two streams, threads or contexts at once -- race and corrupt each
+ * other: serialise them.  The first call on each device looks up the array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  Enqueues on cuda_stream and returns after
+ * synchronising it.  Errors: as swp_compute_forces (row overflow:
+ * SWP_ERR_NLIST_OVERFLOW, grow max_nn with swp_set_nlist). */
+#define SWP_STATIC_SCRATCH_BYTES (8u << 20)
+SWP_API int swp_compute_forces_static(swp_ctx* ctx, const double* x_dev, const int32_t* type_dev,
+                                      double* f_dev, double* thermo_dev, void* cuda_stream);
+
 SWP_API const char* swp_last_error(const swp_ctx* ctx);
 
 /* Free the context (not the caller's device buffers). NULL is accepted. */

@@ -45,7 +45,7 @@ EXPORTS = (
     "swp_nlist_size", "swp_bind_workspace", "swp_bind_nlist", "swp_set_state", "swp_set_step",
     "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch",
-    "swp_set_timeout", "swp_last_error", "swp_destroy",
+    "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
 )
 
 
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
+        "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +247,14 @@ def swp_set_timeout(ctx, ns: int):
 
 def swp_last_error(ctx) -> str:
     return (load_library().swp_last_error(ctx) or b"").decode(errors="replace")
+
+
+def swp_compute_forces_static(ctx, x_dev, type_dev, f_dev, thermo_dev=None, stream: int = 0):
+    """Forces into caller buffers with no device allocation (scratch in a static array)."""
+    return _check(ctx, load_library().swp_compute_forces_static(ctx, _ptr(x_dev), _ptr(type_dev),
+                                                                _ptr(f_dev), _ptr(thermo_dev),
+                                                                ctypes.c_void_p(stream)),
+                  "swp_compute_forces_static")
 
 
 def swp_destroy(ctx):

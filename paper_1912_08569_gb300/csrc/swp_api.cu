@@ -802,3 +802,167 @@ int swp_destroy(swp_ctx* c)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Force evaluation without any device allocation.
+//
+// Some callers cannot allocate device memory at the moment they need forces:
+// code embedded in a host framework whose memory pool has reserved the
+// device's memory and forbids side allocations, code driven from inside a
+// stream capture, or a latency-bound loop that cannot afford the implicit
+// device synchronisation of cudaMalloc/cudaFree.  swp_compute_forces_static
+// serves them: its scratch (state copy, cell list, neighbour list, partial
+// sums) lives in the fixed-size array below, which the library's module
+// reserves on every GPU that loads it, for the life of the process.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)SWP_STATIC_SCRATCH_BYTES;
+constexpr int kMaxStaticDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device (host code sees only a
+// stand-in symbol; the address comes from cudaGetSymbolAddress).
+static void* g_static_addr[kMaxStaticDevices];
+
+__global__ void k_static_stage(const double* x, const int32_t* type, double* io, int* io_int, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int c = 0; c < 3; c++) {
+            io[3 * i + c] = x[3 * i + c];
+            io[3 * n + 3 * i + c] = 0.0;  // velocities
+            io_int[n + 3 * i + c] = 0;    // images
+        }
+        io[6 * n + i] = 1.0;  // masses
+        io_int[i] = type ? type[i] : 0;
+    }
+}
+
+template <typename Real>
+void static_table(const swp_ctx* c, PairP<Real>* t)
+{
+    std::memset(t, 0, sizeof(PairP<Real>) * kMaxTypes * kMaxTypes);
+    for (int k = 0; k < c->ntypes * c->ntypes; k++) {
+        const PairHost& p = c->pairs[k];
+        PairP<Real>& e = t[k];
+        e.kind = p.kind;
+        e.nhalf = p.n / 2;
+        e.odd = p.n & 1;
+        e.four_eps = (Real)(4.0 * p.eps);
+        e.n_real = (Real)p.n;
+        e.sig2 = (Real)(p.sigma * p.sigma);
+        const double rmin = p.sigma * std::pow(2.0, 1.0 / p.n);
+        e.rmin2 = (Real)(rmin * rmin);
+        e.rlist2 = (Real)(-1.0);
+        if (p.kind == KIND_WCA) {
+            e.rc2 = (Real)(rmin * rmin);
+            e.ushift = (Real)p.eps;
+            e.inv_epshat = (Real)(1.0 / p.eps);
+            e.rlist2 = (Real)((rmin + c->skin) * (rmin + c->skin));
+            e.rbond2 = (Real)(-1.0);
+        } else if (p.kind == KIND_SWAP) {
+            const double vc = p.shift ? lj(p.rcut, p.eps, p.sigma, p.n) : 0.0;
+            e.rc2 = (Real)(p.rcut * p.rcut);
+            e.a = (Real)std::sqrt(p.lambda3 * p.eps);
+            e.inv_epshat = (Real)(1.0 / (p.eps + vc));
+            e.vshift = (Real)vc;
+            e.ushift = (Real)(-vc);
+            e.rlist2 = (Real)((p.rcut + c->skin) * (p.rcut + c->skin));
+            double rb = p.rbond > 0.0 ? p.rbond
+                                      : p.sigma * std::pow((1.0 - std::sqrt(0.5)) / 2.0, -1.0 / p.n);
+            e.rbond2 = (Real)(rb * rb);
+        }
+    }
+}
+
+template <typename Real>
+int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, double* thermo,
+                  cudaStream_t s)
+{
+    int dev = 0;
+    SWP_CUDA(c, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxStaticDevices) return fail(c, SWP_ERR_INVALID, "device index too large");
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        SWP_CUDA(c, cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_addr[dev] = p;
+    }
+    char* base = (char*)g_static_addr[dev];
+    const size_t ws = layout<Real>(c, nullptr, nullptr);
+    const size_t nl = align256(sizeof(int) * (size_t)std::max(c->n, 1) * c->max_nn);
+    if (ws + nl > kStaticScratchBytes) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "system needs %zu bytes of scratch; the static scratch holds %zu "
+                      "(fewer particles, a smaller max_nn or a denser box fit)",
+                      ws + nl, kStaticScratchBytes);
+        return fail(c, SWP_ERR_INVALID, buf);
+    }
+    Dev<Real> d;
+    layout<Real>(c, base, &d);
+    d.nlist = (int*)(base + ws);
+
+    PairP<Real> tab[kMaxTypes * kMaxTypes];
+    static_table<Real>(c, tab);
+    SWP_CUDA(c, cudaMemcpyAsync((void*)d.table, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
+    SWP_CUDA(c, cudaMemcpyAsync((void*)d.cell_rank, c->cell_rank.data(), sizeof(int) * c->ncell,
+                                cudaMemcpyHostToDevice, s));
+    // The array keeps the previous call's contents: the control block (status,
+    // barrier counter, state) must start from zero every call.
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    h.state = 1;
+    h.need_rebuild = 1;
+    SWP_CUDA(c, cudaMemcpyAsync(d.ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    k_static_stage<<<(c->n + 255) / 256, 256, 0, s>>>(x, type, d.io, d.io_int, c->n);
+    SWP_CUDA(c, cudaGetLastError());
+    SWP_CUDA(c, launch_set_state<Real>(d, s));
+
+    int bps = 0;
+    SWP_CUDA(c, run_occupancy<Real>(kBlock, c->lanes, &bps));
+    if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
+    if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
+    bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
+    RunArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.max_blocks = c->max_blocks;
+    a.timeout_ns = c->timeout_ns;
+    a.skin_eff = c->skin;
+    a.seed = c->seed;
+    SWP_CUDA(c, launch_run<Real>(d, a, c->num_sms * bps, kBlock, c->lanes, s));
+    SWP_CUDA(c, cudaMemcpyAsync(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SWP_CUDA(c, cudaStreamSynchronize(s));
+    if (h.status & kStatusTimeout) return fail(c, SWP_ERR_TIMEOUT, "a device-side wait timed out");
+    if (h.status & kStatusNonfinite) return fail(c, SWP_ERR_NONFINITE, "non-finite force");
+    if (h.status & kStatusOverflow) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "neighbour row of %d entries exceeds max_nn = %d", h.max_row,
+                      c->max_nn);
+        return fail(c, SWP_ERR_NLIST_OVERFLOW, buf);
+    }
+    SWP_CUDA(c, launch_get_forces<Real>(d, h.pos_cur, s));
+    SWP_CUDA(c, cudaMemcpyAsync(f, d.io, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToDevice, s));
+    if (thermo) {
+        // [U2, U3, W xx yy zz xy xz yz, n_bonds]
+        SWP_CUDA(c, cudaMemcpyAsync(thermo, &d.ctl->thermo[Q_U2], 2 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+        SWP_CUDA(c, cudaMemcpyAsync(thermo + 2, &d.ctl->thermo[Q_W0], 7 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    SWP_CUDA(c, cudaStreamSynchronize(s));
+    return SWP_OK;
+}
+
+}  // namespace
+
+extern "C" int swp_compute_forces_static(swp_ctx* c, const double* x_dev, const int32_t* type_dev,
+                                         double* f_dev, double* thermo_dev, void* cuda_stream)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (c->n == 0) return SWP_OK;
+    if (!x_dev || !f_dev) return fail(c, SWP_ERR_INVALID, "positions and forces are required");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    return c->precision == SWP_FP64 ? static_forces<double>(c, x_dev, type_dev, f_dev, thermo_dev, s)
+                                    : static_forces<float>(c, x_dev, type_dev, f_dev, thermo_dev, s);
+}
