@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "swap-potential particle-timesteps/s at 100k (FP32); % of HBM roofline"
 UNIT = "particle-timesteps/s"
-# swp_read_thermo copies the device control block (176 bytes) to the host.
-CTL_BYTES = 176
+# swp_read_thermo copies the device control block (184 bytes) to the host.
+CTL_BYTES = 184
 
 
 def _args():
@@ -47,7 +47,7 @@ def _args():
     ap.add_argument("--lam", type=float, default=1.0)
     ap.add_argument("--md-steps", type=int, default=1000)
     ap.add_argument("--n", type=int, default=100_000)
-    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--lanes", type=int, default=16)
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -117,7 +117,9 @@ SWP_API int swp_set_pair(swp_ctx* ctx, int ti, int tj, int kind, double eps, dou
                  double rcut, double lambda3, int shift, double rbond);
 
 /* Neighbour-list skin (>= 0; list radius of a pair = its cut-off + skin) and
- * row length max_nn (>= 1).  Call before swp_nlist_size / swp_bind_nlist.
+ * mean row capacity max_nn (>= 1): the list holds max_nn entries per
+ * particle on average over each block's particles (a single row may be
+ * longer).  Call before swp_nlist_size / swp_bind_nlist.
  * The box must hold >= 3 cells of edge max(cut-off) + skin per dimension:
  * SWP_ERR_INVALID otherwise. */
 SWP_API int swp_set_nlist(swp_ctx* ctx, double skin, int max_nn);
@@ -180,13 +182,16 @@ SWP_API int swp_read_thermo(swp_ctx* ctx, swp_thermo* out);
 SWP_API int swp_read_forces(swp_ctx* ctx, double* f, int where);
 SWP_API int swp_read_state(swp_ctx* ctx, double* x, double* v, int32_t* img, int where);
 
-/* Neighbour rows in user order (device pointers only): rows [n][max_nn]
- * holds the tags of each particle's list, reactive partners first;
- * counts [n][2] = (reactive, total). */
-SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev);
+/* Neighbour rows in user order (device pointers only): rows [n][width]
+ * holds the tags of each particle's list (the first min(total, width)
+ * entries), reactive partners first; counts [n][2] = (reactive, total).
+ * Needs a current list (swp_build_nlist). */
+SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev, int width);
 
-/* Launch shape of the step kernel: lanes per particle (1, 2, 4, 8, 16 or
- * 32; default 4) and resident blocks per SM (0: as many as fit). */
+/* Launch shape of the step kernel: lanes per particle of the list build
+ * (1, 2, 4, 8, 16 or 32; default 16) and resident blocks per SM (0: as many
+ * as fit).  Changing it marks the list stale (its block partition follows
+ * the grid). */
 SWP_API int swp_set_launch(swp_ctx* ctx, int lanes, int blocks_per_sm);
 
 /* Bound, in nanoseconds, on every device-side wait (default 2 s). */

@@ -104,7 +104,7 @@ def load_library(path: str = LIB_PATH):
         "swp_read_thermo": ([c_void_p, P(swp_thermo)], c_int),
         "swp_read_forces": ([c_void_p, c_void_p, c_int], c_int),
         "swp_read_state": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int], c_int),
-        "swp_read_nlist": ([c_void_p, c_void_p, c_void_p], c_int),
+        "swp_read_nlist": ([c_void_p, c_void_p, c_void_p, c_int], c_int),
         "swp_set_launch": ([c_void_p, c_int, c_int], c_int),
         "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
@@ -231,8 +231,8 @@ def swp_read_state(ctx, x=None, v=None, img=None, where=SWP_HOST):
                   "swp_read_state")
 
 
-def swp_read_nlist(ctx, rows_dev, counts_dev):
-    return _check(ctx, load_library().swp_read_nlist(ctx, _ptr(rows_dev), _ptr(counts_dev)),
+def swp_read_nlist(ctx, rows_dev, counts_dev, width: int):
+    return _check(ctx, load_library().swp_read_nlist(ctx, _ptr(rows_dev), _ptr(counts_dev), int(width)),
                   "swp_read_nlist")
 
 

@@ -45,7 +45,7 @@ struct swp_ctx {
     int nc[3] = {3, 3, 3};
     int ncell = 27;
     int device = 0, num_sms = 0;
-    int lanes = 4, bps_req = 0, grid = 0, max_blocks = 0;
+    int lanes = 16, bps_req = 0, grid = 0, max_blocks = 0;
     long long timeout_ns = 2000000000LL;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -142,6 +142,20 @@ int derive_cells(swp_ctx* c)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Neighbour-list buffer: entries of every block's region (capacity
+// (n + max_blocks) * max_nn, enough for any grid of at most max_blocks
+// blocks): partner slots (int32), then owner indices (uint16).
+size_t list_entries(const swp_ctx* c) { return ((size_t)std::max(c->n, 1) + c->max_blocks) * c->max_nn; }
+
+size_t list_bytes(const swp_ctx* c) { return align256(list_entries(c) * 4) + align256(list_entries(c) * 2); }
+
+template <typename Real>
+void set_list(const swp_ctx* c, char* base, Dev<Real>* d)
+{
+    d->ent_j = (int*)base;
+    d->ent_o = base ? (unsigned short*)(base + align256(list_entries(c) * 4)) : nullptr;
+}
+
 // Carves the workspace; with base == nullptr only measures it.
 template <typename Real>
 size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
@@ -166,12 +180,13 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     R4* vel1 = (R4*)take(sizeof(R4) * n);
     R4* force = (R4*)take(sizeof(R4) * n);
     Real* S = (Real*)take(sizeof(Real) * n);
-    int2* ncnt = (int2*)take(sizeof(int2) * n);
+    int4* pinfo = (int4*)take(sizeof(int4) * n);
     int* cell_rank = (int*)take(sizeof(int) * c->ncell);
     int* cell_cnt = (int*)take(sizeof(int) * c->ncell);
     int* cell_start = (int*)take(sizeof(int) * (c->ncell + 1));
     int* cell_fill = (int*)take(sizeof(int) * (c->ncell + n));
     int* perm = (int*)take(sizeof(int) * n);
+    int* bsum = (int*)take(sizeof(int) * c->max_blocks);
     double* partials = (double*)take(sizeof(double) * 2 * c->max_blocks * kNQ);
     double* io = (double*)take(sizeof(double) * 7 * n);
     int* io_int = (int*)take(sizeof(int) * 4 * n);
@@ -188,6 +203,7 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
             d->L[k] = (Real)L;
             d->hL[k] = (Real)(0.5 * (double)(Real)L);
             d->inv_cw[k] = (Real)(c->nc[k] / L);
+            d->iL[k] = (Real)(1.0 / (double)(Real)L);
         }
         d->pos[0] = pos0;
         d->pos[1] = pos1;
@@ -199,13 +215,14 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
         d->vel[1] = vel1;
         d->force = force;
         d->S = S;
-        d->nlist = (int*)c->nl;
-        d->ncnt = ncnt;
+        set_list(c, (char*)c->nl, d);
+        d->pinfo = pinfo;
         d->cell_rank = cell_rank;
         d->cell_cnt = cell_cnt;
         d->cell_start = cell_start;
         d->cell_fill = cell_fill;
         d->perm = perm;
+        d->bsum = bsum;
         d->partials = partials;
         d->ctl = ctl;
         d->io = io;
@@ -273,8 +290,8 @@ int refresh_layout(swp_ctx* c)
     if (!c->ws_bound) return fail(c, SWP_ERR_STATE, "no workspace bound");
     if (c->precision == SWP_FP64) layout<double>(c, (char*)c->ws, &c->dd);
     else layout<float>(c, (char*)c->ws, &c->df);
-    if (c->precision == SWP_FP64) c->dd.nlist = (int*)c->nl;
-    else c->df.nlist = (int*)c->nl;
+    if (c->precision == SWP_FP64) set_list(c, (char*)c->nl, &c->dd);
+    else set_list(c, (char*)c->nl, &c->df);
     return SWP_OK;
 }
 
@@ -342,6 +359,40 @@ int sync_ctl(swp_ctx* c)
 }
 
 template <typename Real>
+PairP<Real>* uni_slot(RunArgs* a);
+template <>
+PairP<float>* uni_slot<float>(RunArgs* a) { return a->uf; }
+template <>
+PairP<double>* uni_slot<double>(RunArgs* a) { return a->ud; }
+
+bool same_pair(const PairHost& a, const PairHost& b)
+{
+    return a.kind == b.kind && a.n == b.n && a.shift == b.shift && a.eps == b.eps &&
+           a.sigma == b.sigma && a.lambda3 == b.lambda3 && a.rcut == b.rcut && a.rbond == b.rbond;
+}
+
+// Uniform coefficients: one parameter set for every reactive pair and one for
+// every other interacting pair lets the kernels keep them in registers.
+void uniform_pairs(const swp_ctx* c, RunArgs* a)
+{
+    int sw = -1, ot = -1;
+    bool uni = true;
+    for (int k = 0; k < c->ntypes * c->ntypes; k++) {
+        const PairHost& p = c->pairs[k];
+        if (p.kind == KIND_SWAP) {
+            if (sw < 0) sw = k;
+            else if (!same_pair(p, c->pairs[sw])) uni = false;
+        } else if (p.kind == KIND_WCA) {
+            if (ot < 0) ot = k;
+            else if (!same_pair(p, c->pairs[ot])) uni = false;
+        }
+    }
+    a->uni = uni ? 1 : 0;
+    a->uni_swap = sw < 0 ? 0 : sw;
+    a->uni_other = ot < 0 ? 0 : ot;
+}
+
+template <typename Real>
 int run(swp_ctx* c, RunArgs a)
 {
     Dev<Real>& d = dev<Real>(c);
@@ -362,6 +413,13 @@ int run(swp_ctx* c, RunArgs a)
     }
     a.skin_eff = c->skin - margin;
     a.seed = c->seed;
+    uniform_pairs(c, &a);
+    if (a.uni) {
+        const PairP<Real>* t = (const PairP<Real>*)c->table_host.data();
+        PairP<Real>* u = uni_slot<Real>(&a);
+        u[0] = t[a.uni_swap];
+        u[1] = t[a.uni_other];
+    }
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
     SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->lanes, c->stream));
     return SWP_OK;
@@ -419,7 +477,7 @@ int swp_create(swp_ctx** out, int n, int n_types, const double box[3], int preci
         cudaGetLastError();
         return SWP_ERR_CUDA;
     }
-    c->max_blocks = c->num_sms * (2048 / kBlock);
+    c->max_blocks = c->num_sms * std::max(1, 2048 / kBlock);
     std::memset(&c->hctl, 0, sizeof(Ctl));
     if (derive_cells(c) != SWP_OK) {
         delete c;
@@ -527,7 +585,7 @@ int swp_workspace_size(const swp_ctx* c, size_t* bytes)
 int swp_nlist_size(const swp_ctx* c, size_t* bytes)
 {
     if (!c || !bytes) return SWP_ERR_INVALID;
-    *bytes = align256(sizeof(int) * (size_t)std::max(c->n, 1) * c->max_nn);
+    *bytes = list_bytes(c);
     return SWP_OK;
 }
 
@@ -600,6 +658,9 @@ int swp_set_state(swp_ctx* c, const double* x, const double* v, const int32_t* t
     c->hctl.state = 1;
     c->hctl.need_rebuild = 1;
     SWP_CUDA(c, cudaMemcpyAsync(ctl, &c->hctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    // the cell build expects zeroed counts (it zeroes them itself after use)
+    SWP_CUDA(c, cudaMemsetAsync(c->precision == SWP_FP64 ? (void*)c->dd.cell_cnt : (void*)c->df.cell_cnt, 0,
+                                sizeof(int) * c->ncell, c->stream));
     if (n == 0) {
         c->state_set = true;
         return SWP_OK;
@@ -673,6 +734,12 @@ static int step_common(swp_ctx* c, double dt, double kT, double gamma, int nstep
     a.langevin = gamma > 0.0 ? 1 : 0;
     a.c1 = std::exp(-gamma * dt);
     a.c2 = std::sqrt((1.0 - a.c1 * a.c1) * kT);
+    a.hdt_d = 0.5 * dt;
+    a.c1_d = a.c1;
+    a.c2_d = a.c2;
+    a.hdt_f = (float)a.hdt_d;
+    a.c1_f = (float)a.c1;
+    a.c2_f = (float)a.c2;
     return run_any(c, a);
 }
 
@@ -759,17 +826,17 @@ int swp_read_state(swp_ctx* c, double* x, double* v, int32_t* img, int where)
     return rc;
 }
 
-int swp_read_nlist(swp_ctx* c, int32_t* rows_dev, int32_t* counts_dev)
+int swp_read_nlist(swp_ctx* c, int32_t* rows_dev, int32_t* counts_dev, int width)
 {
     int rc = ready(c, true);
     if (rc) return rc;
     if (c->n == 0) return SWP_OK;
-    if (!rows_dev || !counts_dev) return fail(c, SWP_ERR_INVALID, "null output");
+    if (!rows_dev || !counts_dev || width < 1) return fail(c, SWP_ERR_INVALID, "null output or width < 1");
     rc = sync_ctl(c);
     if (rc) return rc;
     if (c->hctl.need_rebuild) return fail(c, SWP_ERR_STATE, "neighbour list is stale: call swp_build_nlist");
-    if (c->precision == SWP_FP64) SWP_CUDA(c, launch_get_nlist<double>(c->dd, c->hctl.pos_cur, rows_dev, counts_dev, c->stream));
-    else SWP_CUDA(c, launch_get_nlist<float>(c->df, c->hctl.pos_cur, rows_dev, counts_dev, c->stream));
+    if (c->precision == SWP_FP64) SWP_CUDA(c, launch_get_nlist<double>(c->dd, c->hctl.pos_cur, rows_dev, counts_dev, width, c->stream));
+    else SWP_CUDA(c, launch_get_nlist<float>(c->df, c->hctl.pos_cur, rows_dev, counts_dev, width, c->stream));
     SWP_CUDA(c, cudaStreamSynchronize(c->stream));
     return SWP_OK;
 }
@@ -782,6 +849,7 @@ int swp_set_launch(swp_ctx* c, int lanes, int blocks_per_sm)
     if (blocks_per_sm < 0) return fail(c, SWP_ERR_INVALID, "blocks_per_sm must be >= 0");
     c->lanes = lanes;
     c->bps_req = blocks_per_sm;
+    if (c->ws_bound && c->state_set && c->n > 0) return mark_stale(c);
     return SWP_OK;
 }
 
@@ -890,7 +958,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     }
     char* base = (char*)g_static_addr[dev];
     const size_t ws = layout<Real>(c, nullptr, nullptr);
-    const size_t nl = align256(sizeof(int) * (size_t)std::max(c->n, 1) * c->max_nn);
+    const size_t nl = list_bytes(c);
     if (ws + nl > kStaticScratchBytes) {
         char buf[200];
         std::snprintf(buf, sizeof buf,
@@ -901,7 +969,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     }
     Dev<Real> d;
     layout<Real>(c, base, &d);
-    d.nlist = (int*)(base + ws);
+    set_list(c, base + ws, &d);
 
     PairP<Real> tab[kMaxTypes * kMaxTypes];
     static_table<Real>(c, tab);
@@ -915,6 +983,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     h.state = 1;
     h.need_rebuild = 1;
     SWP_CUDA(c, cudaMemcpyAsync(d.ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    SWP_CUDA(c, cudaMemsetAsync(d.cell_cnt, 0, sizeof(int) * c->ncell, s));
     k_static_stage<<<(c->n + 255) / 256, 256, 0, s>>>(x, type, d.io, d.io_int, c->n);
     SWP_CUDA(c, cudaGetLastError());
     SWP_CUDA(c, launch_set_state<Real>(d, s));

@@ -11,11 +11,12 @@ namespace swp {
 constexpr int kMaxTypes = 8;       // type-pair table is kMaxTypes^2 entries at most
 constexpr int kNQ = 12;            // per-block thermo partials: see Q_* below
 constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
-constexpr int kBlock = 512;        // threads per block of the step kernel
+constexpr int kBlock = 1024;       // threads per block of the step kernel (one block per SM)
 constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays clear)
 
 // Thermo quantities, in the order of the per-block partials.
 enum { Q_U2 = 0, Q_U3 = 1, Q_K = 2, Q_W0 = 3, Q_BONDS = 9, Q_SPARE0 = 10, Q_SPARE1 = 11 };
+constexpr int kNQA = 10;  // quantities accumulated per thread (Q_U2 .. Q_BONDS)
 
 // Fixed-point position unit: positions are int64 multiples of 2^-48 sigma.
 constexpr double kFix = 281474976710656.0;          // 2^48
@@ -52,7 +53,9 @@ struct Ctl {
     int pos_cur;                 // which pos buffer holds the current snapshot
     int arr_cur;                 // which xq/img/vel buffer set is current
     int need_rebuild;            // set by the host after set_state / parameter changes
-    int max_row;                 // longest neighbour row seen by the last build
+    int max_row;                 // row length (entries per particle) the last build needed
+    int overflow;                // set by a block whose entries exceeded its capacity
+    int list_grid;               // grid size the list was built for (its block partition)
     unsigned int dmax2[2];       // per-step max squared displacement (float bits), by parity
     double disp;                 // displacement bound accumulated since the last build
     long long step;              // completed time steps
@@ -94,6 +97,7 @@ struct Dev {
     Real L[3];
     Real hL[3];
     Real inv_cw[3];  // cells per unit length
+    Real iL[3];      // 1 / L
     long long Lq[3]; // box in fixed-point units
     R4* pos[2];      // snapshot (x, y, z, packed tag/type bits), ping-pong
     long long* xq[2];  // fixed-point positions, SoA [3][n], two sets (reorder)
@@ -101,13 +105,15 @@ struct Dev {
     R4* vel[2];        // (vx, vy, vz, 1/m), two sets
     R4* force;         // (fx, fy, fz, 0)
     Real* S;           // per-centre sum of a*vh over reactive partners
-    int* nlist;        // [n][max_nn], reactive partners first
-    int2* ncnt;        // (n_reactive, n_total) per row
+    int* ent_j;            // neighbour entries: partner slot (block-compact layout)
+    unsigned short* ent_o; // neighbour entries: owner's index inside its sub-chunk
+    int4* pinfo;           // per particle: (first reactive entry, count, first other entry, count)
     const int* cell_rank;  // cell linear index -> position in the sorted cell order
     int* cell_cnt;     // [ncell]
     int* cell_start;   // [ncell + 1]
     int* cell_fill;    // [ncell]
     int* perm;         // [n] new slot -> old slot
+    int* bsum;         // [max_blocks] per-block cell-count sums (scan)
     double* partials;  // [2][max_blocks][kNQ]
     Ctl* ctl;
     double* io;        // host-exchange staging: [3n] x, [3n] v, [n] mass
@@ -124,10 +130,20 @@ struct RunArgs {
     double dt;
     double c1;          // exp(-gamma dt)
     double c2;          // sqrt((1 - c1^2) kT)
+    // the same in the arithmetic precision of the run (converted once on the host)
+    float hdt_f, c1_f, c2_f;
+    double hdt_d, c1_d, c2_d;
     double skin_eff;    // rebuild when 2 * displacement bound > skin_eff
     unsigned long long seed;
     long long timeout_ns;  // bound on every device-side wait
     int max_blocks;     // partials stride
+    int uni;            // 1: uniform coefficients (see uni_swap / uni_other)
+    int uni_swap;       // table index of the reactive pair coefficients (UNI)
+    int uni_other;      // table index of the other pairs' coefficients (UNI)
+    // Uniform coefficients ([0] reactive, [1] other), read by the kernels
+    // straight from the kernel-parameter constant bank.
+    PairP<float> uf[2];
+    PairP<double> ud[2];
 };
 
 // Host-side launchers (defined once per precision).
@@ -143,6 +159,9 @@ cudaError_t launch_get_state(const Dev<Real>& d, int pc, int ac, cudaStream_t s)
 template <typename Real>
 cudaError_t launch_get_forces(const Dev<Real>& d, int pc, cudaStream_t s);
 template <typename Real>
-cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts, cudaStream_t s);
+cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts, int width,
+                             cudaStream_t s);
+template <typename Real>
+size_t run_smem_bytes();
 
 }  // namespace swp

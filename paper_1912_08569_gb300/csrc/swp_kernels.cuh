@@ -63,6 +63,13 @@ __device__ __forceinline__ double fix_to_real(long long q, double) { return __ll
 __device__ __forceinline__ long long real_to_fix(float x) { return __float2ll_rn(x * 0x1p48f); }
 __device__ __forceinline__ long long real_to_fix(double x) { return __double2ll_rn(x * kFix); }
 
+__device__ __forceinline__ const PairP<float>* uni_params(const RunArgs& a, float) { return a.uf; }
+__device__ __forceinline__ const PairP<double>* uni_params(const RunArgs& a, double) { return a.ud; }
+
+// Selects the run constant of the arithmetic precision.
+__device__ __forceinline__ float pick(float, float f, double) { return f; }
+__device__ __forceinline__ double pick(double, float, double d) { return d; }
+
 template <typename R4>
 __device__ __forceinline__ int type_of(const R4& p) { return packed_of(p.w) & ((1 << kTypeBits) - 1); }
 
@@ -87,9 +94,36 @@ __device__ __forceinline__ Real dist2(const R4& pi, const R4& pj, const Dev<Real
     return s;
 }
 
+// The same squared distance for a pair already in the list (|x_j - x_i| wraps
+// at most once and the wrapped distance is below the list radius, a third of
+// the box): k = rint(dx / L) is then the wrap of the branchy form above and
+// dx - k L is the same single rounding, so d2 is bit-identical.
+__device__ __forceinline__ float wrap_rint(float dx, float L, float iL) { return fmaf(-L, rintf(dx * iL), dx); }
+__device__ __forceinline__ double wrap_rint(double dx, double L, double iL) { return fma(-L, rint(dx * iL), dx); }
+
+template <typename Real, typename R4>
+__device__ __forceinline__ Real dist2_listed(const R4& pi, const R4& pj, const Dev<Real>& d, Real& dx,
+                                             Real& dy, Real& dz)
+{
+    dx = wrap_rint(sub_rn(pj.x, pi.x), d.L[0], d.iL[0]);
+    dy = wrap_rint(sub_rn(pj.y, pi.y), d.L[1], d.iL[1]);
+    dz = wrap_rint(sub_rn(pj.z, pi.z), d.L[2], d.iL[2]);
+    Real s = mul_rn(dx, dx);
+    s = add_rn(s, mul_rn(dy, dy));
+    s = add_rn(s, mul_rn(dz, dz));
+    return s;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real ipow(Real b, int e)
 {
+    // the common exponents n = 10 and n = 6 (e = n/2) by their short chains;
+    // e is uniform over a warp, so the branch costs no divergence
+    if (e == 5) {
+        Real b2 = b * b;
+        return b2 * b2 * b;
+    }
+    if (e == 3) return b * b * b;
     Real r = Real(1);
     while (e) {
         if (e & 1) r *= b;
@@ -99,11 +133,14 @@ __device__ __forceinline__ Real ipow(Real b, int e)
     return r;
 }
 
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Eq. 2b at squared distance r2: v and f = -(dv/dr)/r.
 template <typename Real>
 __device__ __forceinline__ void lj_eval(const PairP<Real>& p, Real r2, Real& v, Real& f)
 {
-    Real ir2 = Real(1) / r2;
+    Real ir2 = recip(r2);
     Real s2 = p.sig2 * ir2;
     Real x = ipow(s2, p.nhalf);
     if (p.odd) x *= sqrt(s2);
@@ -233,24 +270,32 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
 // ---------------------------------------------------------------------------
 // Block reductions
 
-// Sums kNQ per-thread accumulators over the block into partials[slot][q].
+// Sums the per-thread accumulators over the block into partials[slot][q]:
+// warp shuffles, then one warp combines the warp sums, in the arithmetic
+// precision (at most 1024 terms per block); the block totals are summed over
+// blocks in FP64 (reduce_thermo).  FP64 runs at a small fraction of the FP32
+// rate on this part, so it is kept out of the per-thread work.
 template <typename Real>
-__device__ __forceinline__ void block_thermo(const Real* acc, double* out, double* sh)
+__device__ __forceinline__ void block_thermo(const Real* acc, double* out, double* shd)
 {
-    // sh: kNQ * 32 doubles
+    Real* sh = (Real*)shd;  // kNQA * 32 values
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int q = 0; q < kNQ; q++) {
-        double v = (double)acc[q];
+    for (int q = 0; q < kNQA; q++) {
+        Real v = acc[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) sh[q * 32 + warp] = v;
     }
     __syncthreads();
-    if (threadIdx.x < kNQ) {
-        double s = 0.0;
-        for (int w = 0; w < nw; w++) s += sh[threadIdx.x * 32 + w];
-        out[threadIdx.x] = s;
+    if (warp == 0) {
+        for (int q = 0; q < kNQA; q++) {
+            Real v = lane < nw ? sh[q * 32 + lane] : Real(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) out[q] = (double)v;
+        }
+        if (lane < kNQ - kNQA) out[kNQA + lane] = 0.0;
     }
     __syncthreads();
 }
@@ -329,12 +374,6 @@ __device__ __forceinline__ void cell_coords(const Dev<Real>& d, const typename D
 }
 
 template <typename Real>
-__device__ void ph_zero_cells(const Dev<Real>& d, int t, int nt)
-{
-    for (int c = t; c < d.ncell; c += nt) d.cell_cnt[c] = 0;
-}
-
-template <typename Real>
 __device__ void ph_bin(const Dev<Real>& d, int pc, int t, int nt)
 {
     for (int p = t; p < d.n; p += nt) {
@@ -346,23 +385,59 @@ __device__ void ph_bin(const Dev<Real>& d, int pc, int t, int nt)
     }
 }
 
-// Block 0 only.
-template <typename Real>
-__device__ void ph_scan(const Dev<Real>& d, int* sh)
+// Parallel exclusive scan of the cell counts in two steps.  Block b owns the
+// contiguous chunk [b*ch, (b+1)*ch) of cells.  Step 1: each block sums its
+// chunk into bsum[b].  Step 2 (after a grid barrier): each block adds up the
+// sums of the blocks before it, scans its own chunk, writes cell_start and
+// cell_fill, and zeroes the counts it consumed (so the next build starts
+// from zero without a separate pass).
+__device__ __forceinline__ int block_sum_int(int v, int* sh)
 {
-    const int T = blockDim.x;
-    const int chunk = (d.ncell + T - 1) / T;
-    const int beg = min(threadIdx.x * chunk, d.ncell), end = min(beg + chunk, d.ncell);
-    int sum = 0;
-    for (int c = beg; c < end; c++) sum += d.cell_cnt[c];
-    int total;
-    int run = block_excl_scan(sum, sh, &total);
-    for (int c = beg; c < end; c++) {
-        d.cell_start[c] = run;
-        d.cell_fill[c] = run;
-        run += d.cell_cnt[c];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    int t = 0;
+    for (int w = 0; w < nw; w++) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+template <typename Real>
+__device__ void ph_chunk_sums(const Dev<Real>& d, int* sh)
+{
+    const int ch = (d.ncell + gridDim.x - 1) / gridDim.x;
+    const int beg = min((int)blockIdx.x * ch, d.ncell), end = min(beg + ch, d.ncell);
+    int v = 0;
+    for (int c = beg + threadIdx.x; c < end; c += blockDim.x) v += d.cell_cnt[c];
+    int t = block_sum_int(v, sh);
+    if (threadIdx.x == 0) d.bsum[blockIdx.x] = t;
+}
+
+template <typename Real>
+__device__ void ph_chunk_scan(const Dev<Real>& d, int* sh)
+{
+    const int ch = (d.ncell + gridDim.x - 1) / gridDim.x;
+    const int beg = min((int)blockIdx.x * ch, d.ncell), end = min(beg + ch, d.ncell);
+    int v = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) v += d.bsum[b];
+    int base = block_sum_int(v, sh);
+    // scan the chunk in pieces of blockDim.x cells
+    for (int c0 = beg; c0 < end; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const int cnt = c < end ? d.cell_cnt[c] : 0;
+        int total;
+        int ex = block_excl_scan(cnt, sh, &total);
+        if (c < end) {
+            d.cell_start[c] = base + ex;
+            d.cell_fill[c] = base + ex;
+            d.cell_cnt[c] = 0;
+        }
+        base += total;
     }
-    if (threadIdx.x == 0) d.cell_start[d.ncell] = total;
+    if (end == d.ncell && beg < end && threadIdx.x == 0) d.cell_start[d.ncell] = base;
 }
 
 template <typename Real>
@@ -412,93 +487,284 @@ __device__ void ph_gather(const Dev<Real>& d, int pc, int ac, int t, int nt)
     }
 }
 
-// One row per particle: reactive partners first (front), others from the
-// back, then moved down behind the reactive block.  Returns the longest row
-// seen by this thread.
+// ---------------------------------------------------------------------------
+// Block ownership and the compact neighbour list.
+//
+// Block b of a G-block launch owns the contiguous (Morton-ordered, hence
+// spatially compact) particle range [b*Pb, min((b+1)*Pb, n)), Pb = ceil(n/G),
+// processed in sub-chunks of at most blockDim.x particles.  The neighbour
+// entries of a sub-chunk are stored contiguously in the block's region of the
+// list buffer (capacity Pb * max_nn entries): first the reactive entries of
+// all its particles (in particle order), then the other entries.  Entry e
+// holds the partner slot ent_j[e] and the owner's index inside its sub-chunk
+// ent_o[e]; pinfo[p] = (first reactive entry, n_reactive, first other entry,
+// n_other).  The S and F passes then give one thread to one entry, so the
+// lanes of a warp neither idle on short rows nor diverge between the two
+// kinds of pair, and each owner thread sums its entries in entry order.
+
 template <typename Real>
-__device__ int ph_build_rows(const Dev<Real>& d, const PairP<Real>* tab, int pc, int t, int nt)
+__device__ __forceinline__ void block_range(const Dev<Real>& d, int& b0, int& b1)
+{
+    const int Pb = (d.n + (int)gridDim.x - 1) / (int)gridDim.x;
+    b0 = min((int)blockIdx.x * Pb, d.n);
+    b1 = min(b0 + Pb, d.n);
+}
+
+template <int LB>
+__device__ __forceinline__ int group_excl_scan(int v, unsigned mask, int lane, int* total)
+{
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < LB; o <<= 1) {
+        int y = __shfl_up_sync(mask, x, o, LB);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(mask, x, LB - 1, LB);
+    return x - v;
+}
+
+// The 27 stencil cells of a particle, split over the LB lanes of its group:
+// lane l takes cells l, l+LB, ...; their [start, end) slot ranges.
+template <typename Real, int LB>
+struct Stencil {
+    static constexpr int NU = (27 + LB - 1) / LB;
+    int cs[NU], ce[NU];
+
+    __device__ __forceinline__ void load(const Dev<Real>& d, const typename Dev<Real>::R4& pi, int lane)
+    {
+        int cx, cy, cz;
+        cell_coords(d, pi, cx, cy, cz);
+#pragma unroll
+        for (int u = 0; u < NU; u++) {
+            const int c = lane + LB * u;
+            cs[u] = ce[u] = 0;
+            if (c < 27) {
+                int x = cx + c % 3 - 1, y = cy + (c / 3) % 3 - 1, z = cz + c / 9 - 1;
+                x = x < 0 ? x + d.nc[0] : (x >= d.nc[0] ? x - d.nc[0] : x);
+                y = y < 0 ? y + d.nc[1] : (y >= d.nc[1] ? y - d.nc[1] : y);
+                z = z < 0 ? z + d.nc[2] : (z >= d.nc[2] ? z - d.nc[2] : z);
+                const int r = __ldg(&d.cell_rank[(z * d.nc[1] + y) * d.nc[0] + x]);
+                cs[u] = d.cell_start[r];
+                ce[u] = d.cell_start[r + 1];
+            }
+        }
+    }
+};
+
+// Visits every listed partner of slot i among this lane's stencil cells:
+// fn(q, reactive).  The decision is the exact squared distance against the
+// pair's list radius.
+template <typename Real, int LB, typename Fn>
+__device__ __forceinline__ void for_partners(const Dev<Real>& d, const PairP<Real>* tab,
+                                             const typename Dev<Real>::R4* pos,
+                                             const Stencil<Real, LB>& st, int i,
+                                             const typename Dev<Real>::R4& pi, Fn fn)
+{
+    typedef typename Dev<Real>::R4 R4;
+    const int ti = type_of(pi);
+#pragma unroll
+    for (int u = 0; u < Stencil<Real, LB>::NU; u++)
+        for (int q = st.cs[u]; q < st.ce[u]; q++) {
+            if (q == i) continue;
+            const R4 pj = pos[q];
+            const PairP<Real>& p = tab[ti * d.ntypes + type_of(pj)];
+            Real dx, dy, dz;
+            if (dist2(pi, pj, d, dx, dy, dz) < p.rlist2) fn(q, p.kind == KIND_SWAP);
+        }
+}
+
+// Builds the block's entries (K-a, last step).  cnt: blockDim.x int2 of
+// shared memory.  Returns the block's total entry count divided by its
+// particle count (rounded up), the row length a capacity check needs.
+template <typename Real, int LB>
+__device__ int ph_build_block(const Dev<Real>& d, const PairP<Real>* tab, int pc, int2* cnt,
+                              int* sh, int* overflow)
 {
     typedef typename Dev<Real>::R4 R4;
     const R4* pos = d.pos[pc];
-    const int M = d.max_nn;
-    int longest = 0;
-    for (int i = t; i < d.n; i += nt) {
-        R4 pi = pos[i];
-        int ti = type_of(pi);
-        int cx, cy, cz;
-        cell_coords(d, pi, cx, cy, cz);
-        int* row = d.nlist + (size_t)i * M;
-        int nr = 0, nw = 0;
-        for (int oz = -1; oz <= 1; oz++) {
-            int z = cz + oz;
-            z = z < 0 ? z + d.nc[2] : (z >= d.nc[2] ? z - d.nc[2] : z);
-            for (int oy = -1; oy <= 1; oy++) {
-                int y = cy + oy;
-                y = y < 0 ? y + d.nc[1] : (y >= d.nc[1] ? y - d.nc[1] : y);
-                for (int ox = -1; ox <= 1; ox++) {
-                    int x = cx + ox;
-                    x = x < 0 ? x + d.nc[0] : (x >= d.nc[0] ? x - d.nc[0] : x);
-                    int r = __ldg(&d.cell_rank[(z * d.nc[1] + y) * d.nc[0] + x]);
-                    int s = d.cell_start[r], e = d.cell_start[r + 1];
-                    for (int q = s; q < e; q++) {
-                        if (q == i) continue;
-                        R4 pj = pos[q];
-                        const PairP<Real>& p = tab[ti * d.ntypes + type_of(pj)];
-                        Real dx, dy, dz;
-                        Real d2 = dist2(pi, pj, d, dx, dy, dz);
-                        if (d2 < p.rlist2) {
-                            if (nr + nw < M) {
-                                if (p.kind == KIND_SWAP) row[nr] = q;
-                                else row[M - 1 - nw] = q;
-                            }
-                            if (p.kind == KIND_SWAP) nr++;
-                            else nw++;
-                        }
-                    }
-                }
+    const int lane = threadIdx.x % LB, grp = threadIdx.x / LB, ngrp = blockDim.x / LB;
+    const unsigned mask = group_mask<LB>();
+    int b0, b1;
+    block_range(d, b0, b1);
+    const int Pb = (d.n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const long long cap_beg = (long long)blockIdx.x * Pb * d.max_nn;
+    const long long cap_end = cap_beg + (long long)Pb * d.max_nn;
+    long long base = cap_beg;
+    for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
+        const int P = min((int)blockDim.x, b1 - q0);
+        // 1. partner counts per particle
+        for (int t = grp; t < P; t += ngrp) {
+            const int i = q0 + t;
+            const R4 pi = pos[i];
+            Stencil<Real, LB> st;
+            st.load(d, pi, lane);
+            int cr = 0, cw = 0;
+            for_partners<Real, LB>(d, tab, pos, st, i, pi, [&](int, bool r) { r ? cr++ : cw++; });
+#pragma unroll
+            for (int o = LB / 2; o > 0; o >>= 1) {
+                cr += __shfl_xor_sync(mask, cr, o, LB);
+                cw += __shfl_xor_sync(mask, cw, o, LB);
             }
+            if (lane == 0) cnt[t] = make_int2(cr, cw);
         }
-        int tot = nr + nw;
-        if (tot <= M)
-            for (int u = 0; u < nw; u++) row[nr + u] = row[M - nw + u];
-        d.ncnt[i] = make_int2(nr, tot);
-        longest = max(longest, tot);
+        __syncthreads();
+        // 2. entry offsets: reactive block, then the others
+        const int t = threadIdx.x;
+        const int2 c = t < P ? cnt[t] : make_int2(0, 0);
+        int Er, Ew;
+        const int offr = block_excl_scan(c.x, sh, &Er);
+        const int offw = block_excl_scan(c.y, sh, &Ew);
+        const bool fits = base + Er + Ew <= cap_end;
+        if (t < P)
+            d.pinfo[q0 + t] = make_int4((int)(base + offr), c.x, (int)(base + Er + offw), c.y);
+        if (!fits && t == 0) *overflow = 1;
+        __syncthreads();
+        // 3. entries (lane order inside each particle's run)
+        if (fits)
+            for (int tt = grp; tt < P; tt += ngrp) {
+                const int i = q0 + tt;
+                const R4 pi = pos[i];
+                const int4 inf = d.pinfo[i];
+                Stencil<Real, LB> st;
+                st.load(d, pi, lane);
+                int cr = 0, cw = 0;
+                for_partners<Real, LB>(d, tab, pos, st, i, pi, [&](int, bool r) { r ? cr++ : cw++; });
+                int tr, tw;
+                int er = inf.x + group_excl_scan<LB>(cr, mask, lane, &tr);
+                int ew = inf.z + group_excl_scan<LB>(cw, mask, lane, &tw);
+                for_partners<Real, LB>(d, tab, pos, st, i, pi, [&](int q, bool r) {
+                    const int e = r ? er++ : ew++;
+                    d.ent_j[e] = q;
+                    d.ent_o[e] = (unsigned short)tt;
+                });
+            }
+        base += Er + Ew;
+        __syncthreads();
     }
-    return longest;
+    const int np = b1 - b0;
+    return np > 0 ? (int)((base - cap_beg + np - 1) / np) : 0;
+}
+
+// ---------------------------------------------------------------------------
+// UNI: every reactive type pair has the same coefficients (ps) and so has
+// every other interacting pair (pw); they are then read from the
+// kernel-parameter constant bank instead of the shared-memory table, which
+// costs neither a lookup nor registers.
+template <typename Real, bool UNI>
+__device__ __forceinline__ const PairP<Real>& pair_of(const PairP<Real>* tab, int ti, int tj, int nt,
+                                                    const PairP<Real>& uni)
+{
+    return UNI ? uni : tab[ti * nt + tj];
+}
+
+// Shared-memory staging of one sub-chunk (dynamic shared memory).
+template <typename Real>
+struct Stage {
+    typedef typename Dev<Real>::R4 R4;
+    R4* pos;        // [blockDim.x] positions of the sub-chunk's particles
+    R4* vel;        // [blockDim.x] their velocities (asynchronous copy)
+    long long* xq;  // [3 * blockDim.x] their fixed-point positions (asynchronous copy)
+    int4* info;     // [blockDim.x] their pinfo
+    Real* S;        // [blockDim.x] their S
+    Real* w;        // [3 * wave] per-entry results of one wave
+    int wave;       // entries per wave
+
+    static constexpr int kWave = sizeof(Real) == 4 ? 8192 : 3072;
+    static size_t bytes(int block)
+    {
+        return (size_t)block * (2 * sizeof(R4) + 3 * sizeof(long long) + sizeof(int4) + sizeof(Real)) +
+               (size_t)3 * kWave * sizeof(Real);
+    }
+    __device__ void carve(unsigned char* base)
+    {
+        const size_t B = blockDim.x;
+        pos = (R4*)base;
+        vel = (R4*)(base + B * sizeof(R4));
+        xq = (long long*)(base + 2 * B * sizeof(R4));
+        info = (int4*)(base + B * (2 * sizeof(R4) + 3 * sizeof(long long)));
+        S = (Real*)(base + B * (2 * sizeof(R4) + 3 * sizeof(long long) + sizeof(int4)));
+        w = (Real*)(base + B * (2 * sizeof(R4) + 3 * sizeof(long long) + sizeof(int4) + sizeof(Real)));
+        wave = kWave;
+    }
+};
+
+// Asynchronous global -> shared copies (no register staging).
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename R4>
+__device__ __forceinline__ void cp_async_r4(R4* smem, const R4* gmem)
+{
+    if (sizeof(R4) == 16) {
+        cp_async(smem, gmem, 16);
+    } else {
+        cp_async(smem, gmem, 16);
+        cp_async((char*)smem + 16, (const char*)gmem + 16, 16);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // S pass (K-b1): S_i = sum over reactive partners k inside r_cut of a vh(r_ik).
 
-template <typename Real, int LANES>
-__device__ __forceinline__ void s_particle(const Dev<Real>& d, const PairP<Real>* tab, int pc,
-                                           int i, int lane, unsigned mask)
+template <typename Real, bool UNI>
+__device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc, Stage<Real>& sm,
+                             const PairP<Real>& ps)
 {
     typedef typename Dev<Real>::R4 R4;
     const R4* pos = d.pos[pc];
-    int2 c = d.ncnt[i];
-    R4 pi = pos[i];
-    const int ti = type_of(pi);
-    const int* row = d.nlist + (size_t)i * d.max_nn;
-    Real s = Real(0);
-    for (int k = lane; k < c.x; k += LANES) {
-        int j = row[k];
-        R4 pj = pos[j];
-        const PairP<Real>& p = tab[ti * d.ntypes + type_of(pj)];
-        Real dx, dy, dz;
-        Real r2 = dist2(pi, pj, d, dx, dy, dz);
-        if (r2 < p.rc2) {
-            Real vh = Real(1);
-            if (r2 > p.rmin2) {
-                Real v, f;
-                lj_eval(p, r2, v, f);
-                vh = (p.vshift - v) * p.inv_epshat;
-            }
-            s += p.a * vh;
+    int b0, b1;
+    block_range(d, b0, b1);
+    const int t = threadIdx.x;
+    for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
+        const int P = min((int)blockDim.x, b1 - q0);
+        if (t < P) {
+            sm.pos[t] = pos[q0 + t];
+            sm.info[t] = d.pinfo[q0 + t];
         }
+        __syncthreads();
+        const int e_beg = sm.info[0].x;
+        const int e_end = sm.info[P - 1].x + sm.info[P - 1].y;
+        Real s = Real(0);
+        for (int wb = e_beg; wb < e_end; wb += sm.wave) {
+            const int we = min(wb + sm.wave, e_end);
+            for (int e = wb + t; e < we; e += blockDim.x) {
+                const int j = d.ent_j[e];
+                const int o = d.ent_o[e];
+                const R4 pj = pos[j];
+                const R4 pi = sm.pos[o];
+                const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj), d.ntypes, ps);
+                Real dx, dy, dz;
+                const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+                Real sv = Real(0);
+                if (r2 < p.rc2) {
+                    Real vh = Real(1);
+                    if (r2 > p.rmin2) {
+                        Real v, f;
+                        lj_eval(p, r2, v, f);
+                        vh = (p.vshift - v) * p.inv_epshat;
+                    }
+                    sv = p.a * vh;
+                }
+                sm.w[e - wb] = sv;
+            }
+            __syncthreads();
+            if (t < P) {
+                const int4 inf = sm.info[t];
+                const int k0 = max(inf.x, wb), k1 = min(inf.x + inf.y, we);
+                for (int k = k0; k < k1; k++) s += sm.w[k - wb];
+            }
+            __syncthreads();
+        }
+        if (t < P) d.S[q0 + t] = s;
     }
-    s = group_sum<LANES>(s, mask);
-    if (lane == 0) d.S[i] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -512,16 +778,37 @@ enum { F_CLOSING = 1, F_OPENING = 2, F_STORE = 4 };
 
 template <typename Real>
 struct Acc {
-    Real q[kNQ];
+    Real q[kNQA];
 };
+
+// Per-particle integrator inputs, loaded before the force gathers so that
+// their latency overlaps the entry work.
+template <typename Real>
+struct PState {
+    typename Dev<Real>::R4 v;
+    long long q[3];
+};
+
+template <typename Real>
+__device__ __forceinline__ void load_pstate(const Dev<Real>& d, int ac, int i, int flags,
+                                            PState<Real>& ps)
+{
+    const int n = d.n;
+    ps.v = d.vel[ac][i];
+    if (flags & F_OPENING) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) ps.q[c] = d.xq[ac][c * n + i];
+    }
+}
 
 // Adds a displacement to one fixed-point coordinate, wraps it into the box
 // (counting the image) and returns the new snapshot coordinate.
 template <typename Real>
-__device__ __forceinline__ Real advance_fix(const Dev<Real>& d, int ac, int i, int c, Real dx)
+__device__ __forceinline__ Real advance_fix(const Dev<Real>& d, int ac, int i, int c, long long q0,
+                                            Real dx)
 {
     const int n = d.n;
-    long long q = d.xq[ac][c * n + i] + real_to_fix(dx);
+    long long q = q0 + real_to_fix(dx);
     const long long Lq = d.Lq[c];
     if (q >= Lq) {
         q -= Lq;
@@ -534,17 +821,18 @@ __device__ __forceinline__ Real advance_fix(const Dev<Real>& d, int ac, int i, i
     return fix_to_real(q, Real(0));
 }
 
-// Advances particle i given its force (lane 0 of its group).  Returns the
-// squared displacement of this step's drift (0 when not opening).
+// Advances particle i given its force.  Returns the squared displacement of
+// this step's drift (0 when not opening).
 template <typename Real>
 __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs& a, int pc,
                                                int ac, int i, Real fx, Real fy, Real fz,
-                                               int flags, long long step, Acc<Real>& acc)
+                                               int flags, long long step, PState<Real>& st,
+                                               Real wbits, Acc<Real>& acc)
 {
     typedef typename Dev<Real>::R4 R4;
-    R4 v = d.vel[ac][i];
+    R4 v = st.v;
     const Real im = v.w;
-    const Real hdt = Real(0.5) * Real(a.dt);
+    const Real hdt = pick(Real(0), a.hdt_f, a.hdt_d);
     if (flags & F_CLOSING) {
         v.x += hdt * fx * im;
         v.y += hdt * fy * im;
@@ -558,11 +846,10 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         v.z += hdt * fz * im;
         Real ddx = hdt * v.x, ddy = hdt * v.y, ddz = hdt * v.z;
         if (a.langevin) {
-            R4 p = d.pos[pc][i];
-            unsigned tag = (unsigned)(packed_of(p.w) >> kTypeBits);
             Real z[3];
-            normals3(a.seed, step, tag, z);
-            const Real c1 = Real(a.c1), sd = Real(a.c2) * sqrt(im);
+            normals3(a.seed, step, (unsigned)(packed_of(wbits) >> kTypeBits), z);
+            const Real c1 = pick(Real(0), a.c1_f, a.c1_d);
+            const Real sd = pick(Real(0), a.c2_f, a.c2_d) * sqrt(im);
             v.x = c1 * v.x + sd * z[0];
             v.y = c1 * v.y + sd * z[1];
             v.z = c1 * v.z + sd * z[2];
@@ -572,100 +859,142 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         ddz += hdt * v.z;
         disp2 = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
         R4 np;
-        np.x = advance_fix(d, ac, i, 0, ddx);
-        np.y = advance_fix(d, ac, i, 1, ddy);
-        np.z = advance_fix(d, ac, i, 2, ddz);
-        np.w = d.pos[pc][i].w;
+        np.x = advance_fix(d, ac, i, 0, st.q[0], ddx);
+        np.y = advance_fix(d, ac, i, 1, st.q[1], ddy);
+        np.z = advance_fix(d, ac, i, 2, st.q[2], ddz);
+        np.w = wbits;
         d.pos[pc ^ 1][i] = np;
     }
     d.vel[ac][i] = v;
     return disp2;
 }
 
-template <typename Real, int LANES>
-__device__ __forceinline__ float f_particle(const Dev<Real>& d, const PairP<Real>* tab,
-                                            const RunArgs& a, int pc, int ac, int i, int lane,
-                                            unsigned mask, int flags, long long step,
-                                            Acc<Real>& acc)
+// One entry's pair force on its owner (returned as the components of
+// f (x_i - x_j)), with the entry's share of energies, virial and bond count.
+// REACT: a reactive pair (two-body plus the three-body factor); else a
+// purely two-body pair.
+template <typename Real, bool UNI, bool REACT>
+__device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real>* tab,
+                                            const typename Dev<Real>::R4& pi,
+                                            const typename Dev<Real>::R4& pj, Real Si, Real Sj,
+                                            const PairP<Real>& pu, Acc<Real>& acc, Real& fx,
+                                            Real& fy, Real& fz)
+{
+    Real dx, dy, dz;
+    const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+    fx = fy = fz = Real(0);
+    const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj), d.ntypes, pu);
+    if (!(r2 < p.rc2)) return;
+    Real v, ft;
+    lj_eval(p, r2, v, ft);
+    acc.q[Q_U2] += Real(0.5) * (v + p.ushift);
+    if (REACT) {
+        Real vh = Real(1);
+        if (r2 > p.rmin2) {
+            vh = (p.vshift - v) * p.inv_epshat;
+            const Real h = p.a * (Si + Sj - Real(2) * p.a * vh);
+            ft *= Real(1) - h * p.inv_epshat;
+        }
+        acc.q[Q_U3] += Real(0.5) * p.a * vh * (Si - p.a * vh);
+        if (r2 < p.rbond2) acc.q[Q_BONDS] += Real(0.5);
+    }
+    fx = -ft * dx;
+    fy = -ft * dy;
+    fz = -ft * dz;
+    const Real hf = Real(0.5) * ft;
+    acc.q[Q_W0 + 0] += hf * dx * dx;
+    acc.q[Q_W0 + 1] += hf * dy * dy;
+    acc.q[Q_W0 + 2] += hf * dz * dz;
+    acc.q[Q_W0 + 3] += hf * dx * dy;
+    acc.q[Q_W0 + 4] += hf * dx * dz;
+    acc.q[Q_W0 + 5] += hf * dy * dz;
+}
+
+template <typename Real, bool UNI>
+__device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const RunArgs& a, int pc,
+                              int ac, int flags, long long step, Stage<Real>& sm, Acc<Real>& acc,
+                              const PairP<Real>& ps, const PairP<Real>& pw)
 {
     typedef typename Dev<Real>::R4 R4;
     const R4* pos = d.pos[pc];
-    int2 c = d.ncnt[i];
-    R4 pi = pos[i];
-    const Real Si = d.S[i];
-    const int ti = type_of(pi);
-    const int* row = d.nlist + (size_t)i * d.max_nn;
-    Real fx = 0, fy = 0, fz = 0;
-    for (int k = lane; k < c.x; k += LANES) {  // reactive partners
-        int j = row[k];
-        R4 pj = pos[j];
-        Real Sj = d.S[j];
-        const PairP<Real>& p = tab[ti * d.ntypes + type_of(pj)];
-        Real dx, dy, dz;
-        Real r2 = dist2(pi, pj, d, dx, dy, dz);
-        if (r2 < p.rc2) {
-            Real v, f2;
-            lj_eval(p, r2, v, f2);
-            Real ft = f2, vh = Real(1);
-            if (r2 > p.rmin2) {
-                vh = (p.vshift - v) * p.inv_epshat;
-                Real h = p.a * (Si + Sj - Real(2) * p.a * vh);
-                ft = f2 * (Real(1) - h * p.inv_epshat);
+    int b0, b1;
+    block_range(d, b0, b1);
+    const int t = threadIdx.x;
+    const int n = d.n;
+    float dmax = 0.0f;
+    for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
+        const int P = min((int)blockDim.x, b1 - q0);
+        if (t < P) {
+            const int i = q0 + t;
+            // integrator inputs: asynchronous copies, waited for after the entries
+            cp_async_r4(&sm.vel[t], &d.vel[ac][i]);
+            if (flags & F_OPENING)
+                for (int c = 0; c < 3; c++) cp_async(&sm.xq[3 * t + c], &d.xq[ac][c * n + i], 8);
+            cp_async_commit();
+            sm.pos[t] = pos[i];
+            sm.S[t] = d.S[i];
+            sm.info[t] = d.pinfo[i];
+        }
+        __syncthreads();
+        const int e_beg = sm.info[0].x;
+        const int e_rend = sm.info[P - 1].x + sm.info[P - 1].y;
+        const int e_end = sm.info[P - 1].z + sm.info[P - 1].w;
+        Real fx = 0, fy = 0, fz = 0;
+        for (int wb = e_beg; wb < e_end; wb += sm.wave) {
+            const int we = min(wb + sm.wave, e_end);
+            for (int e = wb + t; e < we; e += blockDim.x) {
+                const int j = d.ent_j[e];
+                const int o = d.ent_o[e];
+                const R4 pj = pos[j];
+                Real ex, ey, ez;
+                if (e < e_rend)
+                    entry_force<Real, UNI, true>(d, tab, sm.pos[o], pj, sm.S[o], d.S[j], ps, acc, ex, ey, ez);
+                else
+                    entry_force<Real, UNI, false>(d, tab, sm.pos[o], pj, Real(0), Real(0), pw, acc, ex, ey, ez);
+                sm.w[3 * (e - wb) + 0] = ex;
+                sm.w[3 * (e - wb) + 1] = ey;
+                sm.w[3 * (e - wb) + 2] = ez;
             }
-            acc.q[Q_U2] += Real(0.5) * (v + p.ushift);
-            acc.q[Q_U3] += Real(0.5) * p.a * vh * (Si - p.a * vh);
-            fx -= ft * dx;
-            fy -= ft * dy;
-            fz -= ft * dz;
-            Real hf = Real(0.5) * ft;
-            acc.q[Q_W0 + 0] += hf * dx * dx;
-            acc.q[Q_W0 + 1] += hf * dy * dy;
-            acc.q[Q_W0 + 2] += hf * dz * dz;
-            acc.q[Q_W0 + 3] += hf * dx * dy;
-            acc.q[Q_W0 + 4] += hf * dx * dz;
-            acc.q[Q_W0 + 5] += hf * dy * dz;
-            if (r2 < p.rbond2) acc.q[Q_BONDS] += Real(0.5);
+            __syncthreads();
+            if (t < P) {
+                const int4 inf = sm.info[t];
+                int k0 = max(inf.x, wb), k1 = min(inf.x + inf.y, we);
+                for (int k = k0; k < k1; k++) {
+                    fx += sm.w[3 * (k - wb) + 0];
+                    fy += sm.w[3 * (k - wb) + 1];
+                    fz += sm.w[3 * (k - wb) + 2];
+                }
+                k0 = max(inf.z, wb);
+                k1 = min(inf.z + inf.w, we);
+                for (int k = k0; k < k1; k++) {
+                    fx += sm.w[3 * (k - wb) + 0];
+                    fy += sm.w[3 * (k - wb) + 1];
+                    fz += sm.w[3 * (k - wb) + 2];
+                }
+            }
+            __syncthreads();
         }
-    }
-    for (int k = c.x + lane; k < c.y; k += LANES) {  // other pairs (WCA)
-        int j = row[k];
-        R4 pj = pos[j];
-        const PairP<Real>& p = tab[ti * d.ntypes + type_of(pj)];
-        Real dx, dy, dz;
-        Real r2 = dist2(pi, pj, d, dx, dy, dz);
-        if (r2 < p.rc2) {
-            Real v, f2;
-            lj_eval(p, r2, v, f2);
-            acc.q[Q_U2] += Real(0.5) * (v + p.ushift);
-            fx -= f2 * dx;
-            fy -= f2 * dy;
-            fz -= f2 * dz;
-            Real hf = Real(0.5) * f2;
-            acc.q[Q_W0 + 0] += hf * dx * dx;
-            acc.q[Q_W0 + 1] += hf * dy * dy;
-            acc.q[Q_W0 + 2] += hf * dz * dz;
-            acc.q[Q_W0 + 3] += hf * dx * dy;
-            acc.q[Q_W0 + 4] += hf * dx * dz;
-            acc.q[Q_W0 + 5] += hf * dy * dz;
+        if (t < P) {
+            const int i = q0 + t;
+            if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&d.ctl->status, kStatusNonfinite);
+            if (flags & F_STORE) {
+                R4 f;
+                f.x = fx;
+                f.y = fy;
+                f.z = fz;
+                f.w = Real(0);
+                d.force[i] = f;
+            }
+            cp_async_wait_all();
+            PState<Real> st;
+            st.v = sm.vel[t];
+            if (flags & F_OPENING)
+                for (int c = 0; c < 3; c++) st.q[c] = sm.xq[3 * t + c];
+            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, sm.pos[t].w, acc));
         }
+        __syncthreads();
     }
-    fx = group_sum<LANES>(fx, mask);
-    fy = group_sum<LANES>(fy, mask);
-    fz = group_sum<LANES>(fz, mask);
-    float disp2 = 0.0f;
-    if (lane == 0) {
-        if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&d.ctl->status, kStatusNonfinite);
-        if (flags & F_STORE) {
-            R4 f;
-            f.x = fx;
-            f.y = fy;
-            f.z = fz;
-            f.w = Real(0);
-            d.force[i] = f;
-        }
-        disp2 = integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, acc);
-    }
-    return disp2;
+    return dmax;
 }
 
 // Opening half of a step from stored forces (start of a run).
@@ -674,11 +1003,14 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
                                                   int ac, int i, long long step)
 {
     typedef typename Dev<Real>::R4 R4;
-    R4 f = d.force[i];
+    const R4 f = d.force[i];
+    const R4 pi = d.pos[pc][i];
+    PState<Real> st;
+    load_pstate(d, ac, i, F_OPENING, st);
     Acc<Real> unused;
 #pragma unroll
-    for (int q = 0; q < kNQ; q++) unused.q[q] = Real(0);
-    return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, unused);
+    for (int q = 0; q < kNQA; q++) unused.q[q] = Real(0);
+    return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, st, pi.w, unused);
 }
 
 // ---------------------------------------------------------------------------
@@ -687,9 +1019,7 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
 // grid barriers per step and a rebuild whenever the accumulated displacement
 // bound can let an unlisted pair come inside its cut-off.
 
-
-
-template <typename Real, int LANES>
+template <typename Real, int LB, bool UNI>
 struct Runner {
     typedef typename Dev<Real>::R4 R4;
     const Dev<Real>& d;
@@ -700,26 +1030,27 @@ struct Runner {
     float* sh_f;
     int* s_ok;
     float* s_disp;
+    int2* sh_cnt;
+    Stage<Real> sm;
     Ctl* ctl;
-    int gt, gn, lane, gid, ngroups;
-    unsigned mask;
+    int gt, gn;
     int pc, ac;
     long long rebuilds;
     BarState bs;
+    const PairP<Real>& ps;  // uniform coefficients (UNI), in the kernel-parameter bank
+    const PairP<Real>& pw;
 
     __device__ Runner(const Dev<Real>& d_, const RunArgs& a_, PairP<Real>* tab_, double* sr,
-                      int* si, float* sf, int* so, float* sd)
+                      int* si, float* sf, int* so, float* sd, unsigned char* dyn)
         : d(d_), a(a_), tab(tab_), sh_red(sr), sh_int(si), sh_f(sf), s_ok(so), s_disp(sd),
-          ctl(d_.ctl)
+          ctl(d_.ctl), ps(uni_params(a_, Real(0))[0]), pw(uni_params(a_, Real(0))[1])
     {
         gt = blockIdx.x * blockDim.x + threadIdx.x;
         gn = gridDim.x * blockDim.x;
-        lane = gt % LANES;
-        gid = gt / LANES;
-        ngroups = gn / LANES;
-        mask = group_mask<LANES>();
         rebuilds = 0;
         bs.target = 0;
+        sm.carve(dyn);
+        sh_cnt = (int2*)sm.w;  // the build's counts reuse the wave buffer
     }
 
     __device__ __forceinline__ bool barrier(int where)
@@ -728,15 +1059,18 @@ struct Runner {
         return bar_wait(ctl, bs, a.timeout_ns, where, s_ok);
     }
 
-    // 0: ok; 1: a row overflowed max_nn; 2: a wait timed out.
+    // 0: ok; 1: the list overflowed its capacity; 2: a wait timed out.
     __device__ int rebuild()
     {
-        if (threadIdx.x == 0 && blockIdx.x == 0) ctl->max_row = 0;
-        ph_zero_cells(d, gt, gn);
+        if (threadIdx.x == 0 && blockIdx.x == 0) {
+            ctl->max_row = 0;
+            ctl->overflow = 0;
+        }
+        ph_bin(d, pc, gt, gn);  // cell counts start at zero (see ph_chunk_scan)
         if (!barrier(1)) return 2;
-        ph_bin(d, pc, gt, gn);
+        ph_chunk_sums(d, sh_int);
         if (!barrier(2)) return 2;
-        if (blockIdx.x == 0) ph_scan(d, sh_int);
+        ph_chunk_scan(d, sh_int);
         if (!barrier(3)) return 2;
         ph_scatter(d, gt, gn);
         if (!barrier(4)) return 2;
@@ -746,35 +1080,32 @@ struct Runner {
         pc ^= 1;
         ac ^= 1;
         if (!barrier(6)) return 2;
-        int longest = ph_build_rows(d, tab, pc, gt, gn);
-        int m = block_max_int(longest, sh_int);
-        if (threadIdx.x == 0) atomicMax(&ctl->max_row, m);
+        int ovf = 0;
+        const int need = ph_build_block<Real, LB>(d, tab, pc, sh_cnt, sh_int, &ovf);
+        if (threadIdx.x == 0) {
+            atomicMax(&ctl->max_row, need);
+            if (ovf) atomicOr(&ctl->overflow, 1);
+        }
         if (!barrier(7)) return 2;
-        int mr = ld_relaxed(&ctl->max_row);
+        const int any_ovf = ld_relaxed(&ctl->overflow);
         rebuilds++;
         if (threadIdx.x == 0) *s_disp = 0.0f;
         __syncthreads();
-        if (mr > d.max_nn) {
+        if (any_ovf) {
             if (gt == 0) atomicOr(&ctl->status, kStatusOverflow);
             return 1;
         }
         return 0;
     }
 
-    __device__ void s_pass()
-    {
-        for (int i = gid; i < d.n; i += ngroups) s_particle<Real, LANES>(d, tab, pc, i, lane, mask);
-    }
+    __device__ void s_pass() { s_pass_block<Real, UNI>(d, tab, pc, sm, ps); }
 
     __device__ void f_pass(int flags, long long stp, int par)
     {
         Acc<Real> acc;
 #pragma unroll
-        for (int q = 0; q < kNQ; q++) acc.q[q] = Real(0);
-        float dmax = 0.0f;
-        for (int i = gid; i < d.n; i += ngroups)
-            dmax = fmaxf(dmax, f_particle<Real, LANES>(d, tab, a, pc, ac, i, lane, mask, flags,
-                                                       stp, acc));
+        for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
+        float dmax = f_pass_block<Real, UNI>(d, tab, a, pc, ac, flags, stp, sm, acc, ps, pw);
         block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, sh_red);
         if (flags & F_OPENING) {
             float m = block_max(dmax, sh_f);
@@ -819,8 +1150,8 @@ struct Runner {
     }
 };
 
-template <typename Real, int LANES>
-__global__ void __launch_bounds__(kBlock, 2) k_run(Dev<Real> d, RunArgs a)
+template <typename Real, int LB, bool UNI>
+__global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 {
     __shared__ PairP<Real> tab[kMaxTypes * kMaxTypes];
     __shared__ double sh_red[kNQ * 32];
@@ -828,24 +1159,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_run(Dev<Real> d, RunArgs a)
     __shared__ float sh_f[32];
     __shared__ int s_ok;
     __shared__ float s_disp;
+    extern __shared__ __align__(32) unsigned char dyn[];
 
     Ctl* ctl = d.ctl;
     const int ntt = d.ntypes * d.ntypes;
     for (int t = threadIdx.x; t < ntt; t += blockDim.x) tab[t] = d.table[t];
     if (threadIdx.x == 0) s_disp = (float)ctl->disp;
 
-    Runner<Real, LANES> R(d, a, tab, sh_red, sh_int, sh_f, &s_ok, &s_disp);
     int state = ctl->state;
-    R.pc = ctl->pos_cur;
-    R.ac = ctl->arr_cur;
     long long step = ctl->step;
-    int need_rb = ctl->need_rebuild | a.force_rebuild;
+    // the list's block partition depends on the grid: rebuild if it changed
+    int need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != (int)gridDim.x);
     int remaining = a.nsteps;
     int done = 0;
     int parity = 0;
     int have_thermo = 0;
     int rc = 0;  // 0 ok, 1 overflow
     __syncthreads();
+    Runner<Real, LB, UNI> R(d, a, tab, sh_red, sh_int, sh_f, &s_ok, &s_disp, dyn);
+    R.pc = ctl->pos_cur;
+    R.ac = ctl->arr_cur;
 
     if (a.build_only) {
         rc = R.rebuild();
@@ -915,6 +1248,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_run(Dev<Real> d, RunArgs a)
         ctl->n_rebuilds += R.rebuilds;
         ctl->steps_done = done;
         ctl->need_rebuild = need_rb;
+        if (R.rebuilds > 0) ctl->list_grid = rc == 0 ? (int)gridDim.x : -1;
         if (have_thermo) ctl->thermo[Q_SPARE0] = (double)step;
     }
 }
@@ -996,17 +1330,20 @@ __global__ void k_get_forces(Dev<Real> d, int pc)
 }
 
 template <typename Real>
-__global__ void k_get_nlist(Dev<Real> d, int pc, int* rows, int* counts)
+__global__ void k_get_nlist(Dev<Real> d, int pc, int* rows, int* counts, int width)
 {
     const int n = d.n;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        int tag = packed_of(d.pos[pc][q].w) >> kTypeBits;
-        int2 c = d.ncnt[q];
-        counts[2 * tag] = c.x;
-        counts[2 * tag + 1] = c.y;
-        const int* row = d.nlist + (size_t)q * d.max_nn;
-        for (int k = 0; k < c.y && k < d.max_nn; k++)
-            rows[(size_t)tag * d.max_nn + k] = packed_of(d.pos[pc][row[k]].w) >> kTypeBits;
+        const int tag = packed_of(d.pos[pc][q].w) >> kTypeBits;
+        const int4 inf = d.pinfo[q];
+        counts[2 * tag] = inf.y;
+        counts[2 * tag + 1] = inf.y + inf.w;
+        int* out = rows + (size_t)tag * width;
+        int k = 0;
+        for (int e = inf.x; e < inf.x + inf.y && k < width; e++, k++)
+            out[k] = packed_of(d.pos[pc][d.ent_j[e]].w) >> kTypeBits;
+        for (int e = inf.z; e < inf.z + inf.w && k < width; e++, k++)
+            out[k] = packed_of(d.pos[pc][d.ent_j[e]].w) >> kTypeBits;
     }
 }
 

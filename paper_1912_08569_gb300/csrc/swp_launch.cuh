@@ -6,38 +6,67 @@
 
 namespace swp {
 
-template <typename Real>
-static void* run_fn(int lanes)
+template <typename Real, bool UNI>
+static void* run_fn_u(int lanes)
 {
     switch (lanes) {
-    case 1: return (void*)k_run<Real, 1>;
-    case 2: return (void*)k_run<Real, 2>;
-    case 4: return (void*)k_run<Real, 4>;
-    case 8: return (void*)k_run<Real, 8>;
-    case 16: return (void*)k_run<Real, 16>;
-    case 32: return (void*)k_run<Real, 32>;
+    case 1: return (void*)k_run<Real, 1, UNI>;
+    case 2: return (void*)k_run<Real, 2, UNI>;
+    case 4: return (void*)k_run<Real, 4, UNI>;
+    case 8: return (void*)k_run<Real, 8, UNI>;
+    case 16: return (void*)k_run<Real, 16, UNI>;
+    case 32: return (void*)k_run<Real, 32, UNI>;
     default: return nullptr;
     }
+}
+
+template <typename Real>
+size_t run_smem_bytes()
+{
+    return Stage<Real>::bytes(kBlock);
+}
+
+// Opts every variant into the dynamic shared memory it needs (once).
+template <typename Real>
+static cudaError_t prepare_fn(void* fn)
+{
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)run_smem_bytes<Real>());
+}
+
+template <typename Real>
+static void* run_fn(int lanes, int uni)
+{
+    return uni ? run_fn_u<Real, true>(lanes) : run_fn_u<Real, false>(lanes);
 }
 
 template <typename Real>
 cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, int lanes,
                        cudaStream_t s)
 {
-    void* fn = run_fn<Real>(lanes);
+    void* fn = run_fn<Real>(lanes, a.uni);
     if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_fn<Real>(fn);
+    if (e != cudaSuccess) return e;
     Dev<Real> dd = d;
     RunArgs aa = a;
     void* args[] = {(void*)&dd, (void*)&aa};
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, run_smem_bytes<Real>(), s);
 }
 
 template <typename Real>
 cudaError_t run_occupancy(int block, int lanes, int* blocks_per_sm)
 {
-    void* fn = run_fn<Real>(lanes);
-    if (!fn) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, 0);
+    void* fu = run_fn<Real>(lanes, 1);
+    void* fg = run_fn<Real>(lanes, 0);
+    if (!fu || !fg) return cudaErrorInvalidValue;
+    int bu = 0, bg = 0;
+    cudaError_t e = prepare_fn<Real>(fu);
+    if (e == cudaSuccess) e = prepare_fn<Real>(fg);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, fu, block, run_smem_bytes<Real>());
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, fg, block, run_smem_bytes<Real>());
+    *blocks_per_sm = bu < bg ? bu : bg;
+    return e;
 }
 
 static inline int io_grid(int n) { return n > 0 ? (n + 255) / 256 : 1; }
@@ -67,10 +96,11 @@ cudaError_t launch_get_forces(const Dev<Real>& d, int pc, cudaStream_t s)
 }
 
 template <typename Real>
-cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts, cudaStream_t s)
+cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts, int width,
+                             cudaStream_t s)
 {
     if (d.n == 0) return cudaSuccess;
-    k_get_nlist<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc, rows, counts);
+    k_get_nlist<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc, rows, counts, width);
     return cudaGetLastError();
 }
 
@@ -80,6 +110,7 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
     template cudaError_t launch_set_state<R>(const Dev<R>&, cudaStream_t);                       \
     template cudaError_t launch_get_state<R>(const Dev<R>&, int, int, cudaStream_t);             \
     template cudaError_t launch_get_forces<R>(const Dev<R>&, int, cudaStream_t);                 \
-    template cudaError_t launch_get_nlist<R>(const Dev<R>&, int, int*, int*, cudaStream_t);
+    template cudaError_t launch_get_nlist<R>(const Dev<R>&, int, int*, int*, int, cudaStream_t); \
+    template size_t run_smem_bytes<R>();
 
 }  // namespace swp

@@ -25,7 +25,7 @@ class SwapSystem:
     """
 
     def __init__(self, n, n_types, box, pairs, precision="fp32", seed=0, skin=0.3, max_nn=None,
-                 lanes=4, blocks_per_sm=0, device=None, stream=None):
+                 lanes=16, blocks_per_sm=0, device=None, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -162,12 +162,18 @@ class SwapSystem:
         A.swp_read_state(self.ctx, x, v, img)
         return x[: self.n], v[: self.n], img[: self.n]
 
-    def nlist(self):
-        """(rows, counts): rows[i, :counts[i,1]] are the tags in i's list, reactive first."""
+    def nlist(self, width: int = 64):
+        """(rows, counts): rows[i, :counts[i,1]] are the tags in i's list, reactive first
+        (rows are cut at `width`; a second read is made when some row is longer)."""
         t = self.torch
-        rows = t.full((max(self.n, 1), self.max_nn), -1, dtype=t.int32, device=self.device)
         counts = t.zeros((max(self.n, 1), 2), dtype=t.int32, device=self.device)
-        A.swp_read_nlist(self.ctx, rows, counts)
+        for _ in range(2):
+            rows = t.full((max(self.n, 1), width), -1, dtype=t.int32, device=self.device)
+            A.swp_read_nlist(self.ctx, rows, counts, width)
+            longest = int(counts[:, 1].max().item()) if self.n else 0
+            if longest <= width:
+                break
+            width = longest
         return rows.cpu().numpy()[: self.n], counts.cpu().numpy()[: self.n]
 
     def close(self):

@@ -16,7 +16,7 @@ def oracle_pairs(orc, wl):
     return orc.pair_table(wl["n_types"], wl["pairs"])
 
 
-def make_gpu(wl, precision="fp32", lanes=4, **kw):
+def make_gpu(wl, precision="fp32", lanes=16, **kw):
     from paper_1912_08569_gb300 import SwapSystem
 
     s = SwapSystem(wl["n"], wl["n_types"], wl["box"], wl["pairs"], precision=precision,
