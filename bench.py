@@ -47,7 +47,6 @@ def _args():
     ap.add_argument("--lam", type=float, default=1.0)
     ap.add_argument("--md-steps", type=int, default=1000)
     ap.add_argument("--n", type=int, default=100_000)
-    ap.add_argument("--lanes", type=int, default=16)
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,7 +261,7 @@ def run_ours(a):
     wl = _workload(a.n, a.lam, rank)
     n = wl["n"]
     s = SwapSystem(n, 2, wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"],
-                   lanes=a.lanes, blocks_per_sm=a.bps)
+                   blocks_per_sm=a.bps)
     s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
     s.compute_forces()
     _, counts = s.nlist()

@@ -188,11 +188,11 @@ SWP_API int swp_read_state(swp_ctx* ctx, double* x, double* v, int32_t* img, int
  * Needs a current list (swp_build_nlist). */
 SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev, int width);
 
-/* Launch shape of the step kernel: lanes per particle of the list build
- * (1, 2, 4, 8, 16 or 32; default 16) and resident blocks per SM (0: as many
- * as fit).  Changing it marks the list stale (its block partition follows
- * the grid). */
-SWP_API int swp_set_launch(swp_ctx* ctx, int lanes, int blocks_per_sm);
+/* Launch shape of the step kernel: resident blocks per SM (0: as many as
+ * fit; the kernel uses 1024-thread blocks and most of an SM's shared memory,
+ * so one fits).  Changing it marks the list stale (its block partition
+ * follows the grid). */
+SWP_API int swp_set_launch(swp_ctx* ctx, int blocks_per_sm);
 
 /* Bound, in nanoseconds, on every device-side wait (default 2 s). */
 SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);

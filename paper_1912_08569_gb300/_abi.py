@@ -105,7 +105,7 @@ def load_library(path: str = LIB_PATH):
         "swp_read_forces": ([c_void_p, c_void_p, c_int], c_int),
         "swp_read_state": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int], c_int),
         "swp_read_nlist": ([c_void_p, c_void_p, c_void_p, c_int], c_int),
-        "swp_set_launch": ([c_void_p, c_int, c_int], c_int),
+        "swp_set_launch": ([c_void_p, c_int], c_int),
         "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
@@ -236,9 +236,8 @@ def swp_read_nlist(ctx, rows_dev, counts_dev, width: int):
                   "swp_read_nlist")
 
 
-def swp_set_launch(ctx, lanes: int, blocks_per_sm: int = 0):
-    return _check(ctx, load_library().swp_set_launch(ctx, int(lanes), int(blocks_per_sm)),
-                  "swp_set_launch")
+def swp_set_launch(ctx, blocks_per_sm: int = 0):
+    return _check(ctx, load_library().swp_set_launch(ctx, int(blocks_per_sm)), "swp_set_launch")
 
 
 def swp_set_timeout(ctx, ns: int):

@@ -45,7 +45,7 @@ struct swp_ctx {
     int nc[3] = {3, 3, 3};
     int ncell = 27;
     int device = 0, num_sms = 0;
-    int lanes = 16, bps_req = 0, grid = 0, max_blocks = 0;
+    int bps_req = 0, grid = 0, max_blocks = 0;
     long long timeout_ns = 2000000000LL;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -135,8 +135,11 @@ int derive_cells(swp_ctx* c)
                 code[lin] = {spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), lin};
             }
     std::sort(code.begin(), code.end());
-    c->cell_rank.assign(c->ncell, 0);
-    for (int r = 0; r < c->ncell; r++) c->cell_rank[code[r].second] = r;
+    c->cell_rank.assign(2 * (size_t)c->ncell, 0);
+    for (int r = 0; r < c->ncell; r++) {
+        c->cell_rank[code[r].second] = r;
+        c->cell_rank[c->ncell + r] = code[r].second;
+    }
     return SWP_OK;
 }
 
@@ -144,16 +147,16 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Neighbour-list buffer: entries of every block's region (capacity
 // (n + max_blocks) * max_nn, enough for any grid of at most max_blocks
-// blocks): partner slots (int32), then owner indices (uint16).
+// blocks): partner slots, then owner indices (both int32).
 size_t list_entries(const swp_ctx* c) { return ((size_t)std::max(c->n, 1) + c->max_blocks) * c->max_nn; }
 
-size_t list_bytes(const swp_ctx* c) { return align256(list_entries(c) * 4) + align256(list_entries(c) * 2); }
+size_t list_bytes(const swp_ctx* c) { return 2 * align256(list_entries(c) * 4); }
 
 template <typename Real>
 void set_list(const swp_ctx* c, char* base, Dev<Real>* d)
 {
     d->ent_j = (int*)base;
-    d->ent_o = base ? (unsigned short*)(base + align256(list_entries(c) * 4)) : nullptr;
+    d->ent_o = base ? (int*)(base + align256(list_entries(c) * 4)) : nullptr;
 }
 
 // Carves the workspace; with base == nullptr only measures it.
@@ -181,7 +184,7 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     R4* force = (R4*)take(sizeof(R4) * n);
     Real* S = (Real*)take(sizeof(Real) * n);
     int4* pinfo = (int4*)take(sizeof(int4) * n);
-    int* cell_rank = (int*)take(sizeof(int) * c->ncell);
+    int* cell_rank = (int*)take(sizeof(int) * 2 * c->ncell);
     int* cell_cnt = (int*)take(sizeof(int) * c->ncell);
     int* cell_start = (int*)take(sizeof(int) * (c->ncell + 1));
     int* cell_fill = (int*)take(sizeof(int) * (c->ncell + n));
@@ -399,7 +402,7 @@ int run(swp_ctx* c, RunArgs a)
     int rc = upload_table(c);
     if (rc) return rc;
     int bps = 0;
-    SWP_CUDA(c, run_occupancy<Real>(kBlock, c->lanes, &bps));
+    SWP_CUDA(c, run_occupancy<Real>(kBlock, &bps));
     if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
     if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
     bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
@@ -421,7 +424,7 @@ int run(swp_ctx* c, RunArgs a)
         u[1] = t[a.uni_other];
     }
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
-    SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->lanes, c->stream));
+    SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
     return SWP_OK;
 }
 
@@ -536,7 +539,7 @@ int swp_set_pair(swp_ctx* c, int ti, int tj, int kind, double eps, double sigma,
         }
         refresh_layout(c);
         SWP_CUDA(c, cudaMemcpyAsync((void*)(c->precision == SWP_FP64 ? c->dd.cell_rank : c->df.cell_rank),
-                                    c->cell_rank.data(), sizeof(int) * c->ncell,
+                                    c->cell_rank.data(), sizeof(int) * 2 * c->ncell,
                                     cudaMemcpyHostToDevice, c->stream));
     }
     return mark_stale(c);
@@ -569,7 +572,7 @@ int swp_set_nlist(swp_ctx* c, double skin, int max_nn)
         }
         refresh_layout(c);
         SWP_CUDA(c, cudaMemcpyAsync((void*)(c->precision == SWP_FP64 ? c->dd.cell_rank : c->df.cell_rank),
-                                    c->cell_rank.data(), sizeof(int) * c->ncell,
+                                    c->cell_rank.data(), sizeof(int) * 2 * c->ncell,
                                     cudaMemcpyHostToDevice, c->stream));
     }
     return mark_stale(c);
@@ -602,7 +605,7 @@ int swp_bind_workspace(swp_ctx* c, void* ptr, size_t bytes, void* stream)
     c->table_dirty = true;
     refresh_layout(c);
     SWP_CUDA(c, cudaMemcpyAsync((void*)(c->precision == SWP_FP64 ? c->dd.cell_rank : c->df.cell_rank),
-                                c->cell_rank.data(), sizeof(int) * c->ncell, cudaMemcpyHostToDevice,
+                                c->cell_rank.data(), sizeof(int) * 2 * c->ncell, cudaMemcpyHostToDevice,
                                 c->stream));
     return upload_table(c);
 }
@@ -841,13 +844,10 @@ int swp_read_nlist(swp_ctx* c, int32_t* rows_dev, int32_t* counts_dev, int width
     return SWP_OK;
 }
 
-int swp_set_launch(swp_ctx* c, int lanes, int blocks_per_sm)
+int swp_set_launch(swp_ctx* c, int blocks_per_sm)
 {
     if (!c) return SWP_ERR_INVALID;
-    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
-        return fail(c, SWP_ERR_INVALID, "lanes must be 1, 2, 4, 8, 16 or 32");
     if (blocks_per_sm < 0) return fail(c, SWP_ERR_INVALID, "blocks_per_sm must be >= 0");
-    c->lanes = lanes;
     c->bps_req = blocks_per_sm;
     if (c->ws_bound && c->state_set && c->n > 0) return mark_stale(c);
     return SWP_OK;
@@ -974,7 +974,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     PairP<Real> tab[kMaxTypes * kMaxTypes];
     static_table<Real>(c, tab);
     SWP_CUDA(c, cudaMemcpyAsync((void*)d.table, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
-    SWP_CUDA(c, cudaMemcpyAsync((void*)d.cell_rank, c->cell_rank.data(), sizeof(int) * c->ncell,
+    SWP_CUDA(c, cudaMemcpyAsync((void*)d.cell_rank, c->cell_rank.data(), sizeof(int) * 2 * c->ncell,
                                 cudaMemcpyHostToDevice, s));
     // The array keeps the previous call's contents: the control block (status,
     // barrier counter, state) must start from zero every call.
@@ -989,7 +989,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     SWP_CUDA(c, launch_set_state<Real>(d, s));
 
     int bps = 0;
-    SWP_CUDA(c, run_occupancy<Real>(kBlock, c->lanes, &bps));
+    SWP_CUDA(c, run_occupancy<Real>(kBlock, &bps));
     if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
     if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
     bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
@@ -999,7 +999,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     a.timeout_ns = c->timeout_ns;
     a.skin_eff = c->skin;
     a.seed = c->seed;
-    SWP_CUDA(c, launch_run<Real>(d, a, c->num_sms * bps, kBlock, c->lanes, s));
+    SWP_CUDA(c, launch_run<Real>(d, a, c->num_sms * bps, kBlock, s));
     SWP_CUDA(c, cudaMemcpyAsync(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
     SWP_CUDA(c, cudaStreamSynchronize(s));
     if (h.status & kStatusTimeout) return fail(c, SWP_ERR_TIMEOUT, "a device-side wait timed out");

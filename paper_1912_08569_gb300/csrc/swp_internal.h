@@ -106,9 +106,10 @@ struct Dev {
     R4* force;         // (fx, fy, fz, 0)
     Real* S;           // per-centre sum of a*vh over reactive partners
     int* ent_j;            // neighbour entries: partner slot (block-compact layout)
-    unsigned short* ent_o; // neighbour entries: owner's index inside its sub-chunk
+    int* ent_o;            // neighbour entries: owner's index inside its sub-chunk
     int4* pinfo;           // per particle: (first reactive entry, count, first other entry, count)
-    const int* cell_rank;  // cell linear index -> position in the sorted cell order
+    const int* cell_rank;  // [2 * ncell]: cell linear index -> rank in the sorted cell order,
+                           // then rank -> linear index
     int* cell_cnt;     // [ncell]
     int* cell_start;   // [ncell + 1]
     int* cell_fill;    // [ncell]
@@ -148,10 +149,9 @@ struct RunArgs {
 
 // Host-side launchers (defined once per precision).
 template <typename Real>
-cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, int lanes,
-                       cudaStream_t s);
+cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, cudaStream_t s);
 template <typename Real>
-cudaError_t run_occupancy(int block, int lanes, int* blocks_per_sm);
+cudaError_t run_occupancy(int block, int* blocks_per_sm);
 template <typename Real>
 cudaError_t launch_set_state(const Dev<Real>& d, cudaStream_t s);
 template <typename Real>

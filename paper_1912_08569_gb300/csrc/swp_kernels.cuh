@@ -58,9 +58,27 @@ __device__ __forceinline__ int packed_of(double w) { return (int)__double_as_lon
 __device__ __forceinline__ float pack_w(int v, float) { return __int_as_float(v); }
 __device__ __forceinline__ double pack_w(int v, double) { return __longlong_as_double((long long)v); }
 
-__device__ __forceinline__ float fix_to_real(long long q, float) { return __ll2float_rn(q) * 0x1p-48f; }
+// Fixed point <-> arithmetic precision.  FP32: through 32-bit halves (the
+// 64-bit conversions are slow on this part).  q = hi 2^32 + lo with hi and lo
+// converted exactly whenever q carries at most 24 significant bits (every
+// float position does), so a float position round-trips exactly; otherwise
+// the result is within one float ulp.  The displacement x 2^48 is split at
+// 2^24: both halves are exact integers in float for |x| >= 2^-25.
+__device__ __forceinline__ float fix_to_real(long long q, float)
+{
+    const float hi = (float)(int)(q >> 32);
+    const float lo = __uint2float_rn((unsigned)(q & 0xffffffffll));
+    return fmaf(hi, 0x1p32f, lo) * 0x1p-48f;
+}
 __device__ __forceinline__ double fix_to_real(long long q, double) { return __ll2double_rn(q) * kInvFix; }
-__device__ __forceinline__ long long real_to_fix(float x) { return __float2ll_rn(x * 0x1p48f); }
+__device__ __forceinline__ long long real_to_fix(float x)
+{
+    const float y = x * 0x1p24f;
+    const float h = truncf(y);
+    const int hi = (int)h;
+    const int lo = __float2int_rn((y - h) * 0x1p24f);
+    return (long long)hi * 16777216ll + lo;
+}
 __device__ __forceinline__ long long real_to_fix(double x) { return __double2ll_rn(x * kFix); }
 
 __device__ __forceinline__ const PairP<float>* uni_params(const RunArgs& a, float) { return a.uf; }
@@ -228,16 +246,27 @@ struct BarState {
     unsigned long long target;  // valid in thread 0
 };
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Arrival: the block's writes are ordered before a release add on the
+// counter (after the block-wide __syncthreads, thread 0's release is
+// cumulative over them).  Generation g completes at count g * gridDim.x.
 __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned long long old = atomicAdd(&ctl->barrier, 1ull);
-        b.target = (old / gridDim.x + 1ull) * gridDim.x;
+        b.target += gridDim.x;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
     }
 }
 
+// Wait: relaxed polling, then one acquire fence (so the other blocks' writes
+// are visible to this block after the __syncthreads), bounded in time.
 __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long timeout_ns,
                                          int where, int* s_ok)
 {
@@ -245,7 +274,7 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
         int ok = 1;
         int spins = 0;
         long long t0 = 0;
-        while (ld_acquire(&ctl->barrier) < b.target) {
+        while (ld_relaxed_u64(&ctl->barrier) < b.target) {
             if (++spins < 64) continue;
             if (spins == 64) t0 = gtimer_ns();
             if (ld_relaxed(&ctl->status) & kStatusTimeout) {
@@ -258,9 +287,9 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
                 ok = 0;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         *s_ok = ok;
     }
     __syncthreads();
@@ -271,31 +300,35 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
 // Block reductions
 
 // Sums the per-thread accumulators over the block into partials[slot][q]:
-// warp shuffles, then one warp combines the warp sums, in the arithmetic
-// precision (at most 1024 terms per block); the block totals are summed over
-// blocks in FP64 (reduce_thermo).  FP64 runs at a small fraction of the FP32
-// rate on this part, so it is kept out of the per-thread work.
+// warp shuffles level by level over all quantities at once (independent
+// chains in flight together), then warp q combines the warp sums of
+// quantity q, in the arithmetic precision (at most 1024 terms per block);
+// the block totals are summed over blocks in FP64 (reduce_thermo).  FP64
+// runs at a small fraction of the FP32 rate on this part, so it is kept out
+// of the per-thread work.
 template <typename Real>
 __device__ __forceinline__ void block_thermo(const Real* acc, double* out, double* shd)
 {
     Real* sh = (Real*)shd;  // kNQA * 32 values
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    Real v[kNQA];
 #pragma unroll
-    for (int q = 0; q < kNQA; q++) {
-        Real v = acc[q];
+    for (int q = 0; q < kNQA; q++) v[q] = acc[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[q * 32 + warp] = v;
-    }
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < kNQA; q++) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < kNQA; q++) sh[q * 32 + warp] = v[q];
     __syncthreads();
-    if (warp == 0) {
-        for (int q = 0; q < kNQA; q++) {
-            Real v = lane < nw ? sh[q * 32 + lane] : Real(0);
+    if (warp < kNQA) {
+        Real x = lane < nw ? sh[warp * 32 + lane] : Real(0);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) out[q] = (double)v;
-        }
-        if (lane < kNQ - kNQA) out[kNQA + lane] = 0.0;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) out[warp] = (double)x;
+    } else if (warp == kNQA && lane < kNQ - kNQA) {
+        out[kNQA + lane] = 0.0;
     }
     __syncthreads();
 }
@@ -308,8 +341,11 @@ __device__ __forceinline__ float block_max(float v, float* sh)
     if (lane == 0) sh[warp] = v;
     __syncthreads();
     float m = 0.0f;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < nw; w++) m = fmaxf(m, sh[w]);
+    if (warp == 0) {
+        m = lane < nw ? sh[lane] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
     __syncthreads();
     return m;  // valid in thread 0
 }
@@ -510,80 +546,31 @@ __device__ __forceinline__ void block_range(const Dev<Real>& d, int& b0, int& b1
     b1 = min(b0 + Pb, d.n);
 }
 
-template <int LB>
-__device__ __forceinline__ int group_excl_scan(int v, unsigned mask, int lane, int* total)
+// Builds the block's entries (K-a, last step), one warp per cell: the warp
+// loads the 27 stencil ranges of its cell once, then tests its member
+// particles against the candidates 32 at a time with warp ballots.  A
+// counting sweep, a block scan that places every particle's runs (reactive
+// entries of the sub-chunk first, then the others), and a writing sweep;
+// candidates keep the stencil order, so the output is deterministic.
+// cnt: blockDim.x int2 of shared memory.  Returns the block's entry count
+// per particle (rounded up), the row length a capacity check needs.
+template <typename Real>
+__device__ __forceinline__ int rank_of(const Dev<Real>& d, const typename Dev<Real>::R4& p)
 {
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < LB; o <<= 1) {
-        int y = __shfl_up_sync(mask, x, o, LB);
-        if (lane >= o) x += y;
-    }
-    *total = __shfl_sync(mask, x, LB - 1, LB);
-    return x - v;
+    int cx, cy, cz;
+    cell_coords(d, p, cx, cy, cz);
+    return __ldg(&d.cell_rank[(cz * d.nc[1] + cy) * d.nc[0] + cx]);
 }
 
-// The 27 stencil cells of a particle, split over the LB lanes of its group:
-// lane l takes cells l, l+LB, ...; their [start, end) slot ranges.
-template <typename Real, int LB>
-struct Stencil {
-    static constexpr int NU = (27 + LB - 1) / LB;
-    int cs[NU], ce[NU];
-
-    __device__ __forceinline__ void load(const Dev<Real>& d, const typename Dev<Real>::R4& pi, int lane)
-    {
-        int cx, cy, cz;
-        cell_coords(d, pi, cx, cy, cz);
-#pragma unroll
-        for (int u = 0; u < NU; u++) {
-            const int c = lane + LB * u;
-            cs[u] = ce[u] = 0;
-            if (c < 27) {
-                int x = cx + c % 3 - 1, y = cy + (c / 3) % 3 - 1, z = cz + c / 9 - 1;
-                x = x < 0 ? x + d.nc[0] : (x >= d.nc[0] ? x - d.nc[0] : x);
-                y = y < 0 ? y + d.nc[1] : (y >= d.nc[1] ? y - d.nc[1] : y);
-                z = z < 0 ? z + d.nc[2] : (z >= d.nc[2] ? z - d.nc[2] : z);
-                const int r = __ldg(&d.cell_rank[(z * d.nc[1] + y) * d.nc[0] + x]);
-                cs[u] = d.cell_start[r];
-                ce[u] = d.cell_start[r + 1];
-            }
-        }
-    }
-};
-
-// Visits every listed partner of slot i among this lane's stencil cells:
-// fn(q, reactive).  The decision is the exact squared distance against the
-// pair's list radius.
-template <typename Real, int LB, typename Fn>
-__device__ __forceinline__ void for_partners(const Dev<Real>& d, const PairP<Real>* tab,
-                                             const typename Dev<Real>::R4* pos,
-                                             const Stencil<Real, LB>& st, int i,
-                                             const typename Dev<Real>::R4& pi, Fn fn)
-{
-    typedef typename Dev<Real>::R4 R4;
-    const int ti = type_of(pi);
-#pragma unroll
-    for (int u = 0; u < Stencil<Real, LB>::NU; u++)
-        for (int q = st.cs[u]; q < st.ce[u]; q++) {
-            if (q == i) continue;
-            const R4 pj = pos[q];
-            const PairP<Real>& p = tab[ti * d.ntypes + type_of(pj)];
-            Real dx, dy, dz;
-            if (dist2(pi, pj, d, dx, dy, dz) < p.rlist2) fn(q, p.kind == KIND_SWAP);
-        }
-}
-
-// Builds the block's entries (K-a, last step).  cnt: blockDim.x int2 of
-// shared memory.  Returns the block's total entry count divided by its
-// particle count (rounded up), the row length a capacity check needs.
-template <typename Real, int LB>
-__device__ int ph_build_block(const Dev<Real>& d, const PairP<Real>* tab, int pc, int2* cnt,
+template <typename Real>
+__device__ int ph_build_cells(const Dev<Real>& d, const PairP<Real>* tab, int pc, int2* cnt,
                               int* sh, int* overflow)
 {
     typedef typename Dev<Real>::R4 R4;
+    constexpr int NCH = 4;  // candidate chunks of 32 held at once
     const R4* pos = d.pos[pc];
-    const int lane = threadIdx.x % LB, grp = threadIdx.x / LB, ngrp = blockDim.x / LB;
-    const unsigned mask = group_mask<LB>();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     int b0, b1;
     block_range(d, b0, b1);
     const int Pb = (d.n + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -591,55 +578,120 @@ __device__ int ph_build_block(const Dev<Real>& d, const PairP<Real>* tab, int pc
     const long long cap_end = cap_beg + (long long)Pb * d.max_nn;
     long long base = cap_beg;
     for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
-        const int P = min((int)blockDim.x, b1 - q0);
-        // 1. partner counts per particle
-        for (int t = grp; t < P; t += ngrp) {
-            const int i = q0 + t;
-            const R4 pi = pos[i];
-            Stencil<Real, LB> st;
-            st.load(d, pi, lane);
-            int cr = 0, cw = 0;
-            for_partners<Real, LB>(d, tab, pos, st, i, pi, [&](int, bool r) { r ? cr++ : cw++; });
+        const int q1 = min(q0 + (int)blockDim.x, b1);
+        const int P = q1 - q0;
+        const int r_lo = rank_of(d, pos[q0]);
+        const int r_hi = rank_of(d, pos[q1 - 1]);
+        if ((int)threadIdx.x < P) cnt[threadIdx.x] = make_int2(0, 0);
+        __syncthreads();
+        bool fits = true;
+        for (int pass = 0; pass < 2; pass++) {
+            if (pass == 1) {
+                // place the runs: reactive entries of the sub-chunk, then the others
+                const int t = threadIdx.x;
+                const int2 c = t < P ? cnt[t] : make_int2(0, 0);
+                int Er, Ew;
+                const int offr = block_excl_scan(c.x, sh, &Er);
+                const int offw = block_excl_scan(c.y, sh, &Ew);
+                fits = base + Er + Ew <= cap_end;
+                if (t < P) {
+                    const int ro = (int)(base + offr), wo = (int)(base + Er + offw);
+                    d.pinfo[q0 + t] = make_int4(ro, c.x, wo, c.y);
+                    cnt[t] = make_int2(ro, wo);  // running write positions
+                }
+                if (!fits && t == 0) *overflow = 1;
+                base += Er + Ew;
+                __syncthreads();
+                if (!fits) break;
+            }
+            for (int r = r_lo + warp; r <= r_hi; r += nwarps) {
+                const int m0 = max(d.cell_start[r], q0), m1 = min(d.cell_start[r + 1], q1);
+                if (m0 >= m1) continue;
+                // the 27 stencil ranges (lane l < 27 holds range l)
+                const int lin = __ldg(&d.cell_rank[d.ncell + r]);
+                const int cx = lin % d.nc[0], cy = (lin / d.nc[0]) % d.nc[1], cz = lin / (d.nc[0] * d.nc[1]);
+                int s = 0, len = 0;
+                if (lane < 27) {
+                    int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+                    x = x < 0 ? x + d.nc[0] : (x >= d.nc[0] ? x - d.nc[0] : x);
+                    y = y < 0 ? y + d.nc[1] : (y >= d.nc[1] ? y - d.nc[1] : y);
+                    z = z < 0 ? z + d.nc[2] : (z >= d.nc[2] ? z - d.nc[2] : z);
+                    const int rr = __ldg(&d.cell_rank[(z * d.nc[1] + y) * d.nc[0] + x]);
+                    s = d.cell_start[rr];
+                    len = d.cell_start[rr + 1] - s;
+                }
+                int pre = len;  // inclusive prefix over the lanes
 #pragma unroll
-            for (int o = LB / 2; o > 0; o >>= 1) {
-                cr += __shfl_xor_sync(mask, cr, o, LB);
-                cw += __shfl_xor_sync(mask, cw, o, LB);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (lane >= o) pre += y;
+                }
+                const int C = __shfl_sync(0xffffffffu, pre, 31);
+                for (int g0 = 0; g0 < C; g0 += 32 * NCH) {
+                    // this group's candidates: slot and position per lane and chunk.
+                    // Candidate tc lies in the range idx = number of ranges that end
+                    // at or before it; every lane runs every shuffle (no divergence).
+                    int cq[NCH];
+                    R4 cp[NCH];
+                    int idx[NCH];
+#pragma unroll
+                    for (int k = 0; k < NCH; k++) idx[k] = 0;
+                    for (int l = 0; l < 27; l++) {
+                        const int pl = __shfl_sync(0xffffffffu, pre, l);
+#pragma unroll
+                        for (int k = 0; k < NCH; k++) idx[k] += (pl <= g0 + 32 * k + lane) ? 1 : 0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < NCH; k++) {
+                        const int tc = g0 + 32 * k + lane;
+                        const int rg = min(idx[k], 26);
+                        const int sl = __shfl_sync(0xffffffffu, s, rg);
+                        const int pb = __shfl_sync(0xffffffffu, pre - len, rg);
+                        cq[k] = tc < C ? sl + (tc - pb) : -1;
+                    }
+#pragma unroll
+                    for (int k = 0; k < NCH; k++)
+                        if (cq[k] >= 0) cp[k] = pos[cq[k]];
+                    for (int i = m0; i < m1; i++) {
+                        const R4 pi = pos[i];
+                        const int ti = type_of(pi);
+                        int2 run = cnt[i - q0];
+#pragma unroll
+                        for (int k = 0; k < NCH; k++) {
+                            bool react = false, other = false;
+                            if (cq[k] >= 0 && cq[k] != i) {
+                                const PairP<Real>& p = tab[ti * d.ntypes + type_of(cp[k])];
+                                Real dx, dy, dz;
+                                if (dist2(pi, cp[k], d, dx, dy, dz) < p.rlist2) {
+                                    react = p.kind == KIND_SWAP;
+                                    other = !react;
+                                }
+                            }
+                            const unsigned br = __ballot_sync(0xffffffffu, react);
+                            const unsigned bw = __ballot_sync(0xffffffffu, other);
+                            if (pass == 1) {
+                                if (react) {
+                                    const int e = run.x + __popc(br & lt);
+                                    d.ent_j[e] = cq[k];
+                                    d.ent_o[e] = i - q0;
+                                }
+                                if (other) {
+                                    const int e = run.y + __popc(bw & lt);
+                                    d.ent_j[e] = cq[k];
+                                    d.ent_o[e] = i - q0;
+                                }
+                            }
+                            run.x += __popc(br);
+                            run.y += __popc(bw);
+                        }
+                        __syncwarp();
+                        if (lane == 0) cnt[i - q0] = run;
+                        __syncwarp();
+                    }
+                }
             }
-            if (lane == 0) cnt[t] = make_int2(cr, cw);
+            __syncthreads();
         }
-        __syncthreads();
-        // 2. entry offsets: reactive block, then the others
-        const int t = threadIdx.x;
-        const int2 c = t < P ? cnt[t] : make_int2(0, 0);
-        int Er, Ew;
-        const int offr = block_excl_scan(c.x, sh, &Er);
-        const int offw = block_excl_scan(c.y, sh, &Ew);
-        const bool fits = base + Er + Ew <= cap_end;
-        if (t < P)
-            d.pinfo[q0 + t] = make_int4((int)(base + offr), c.x, (int)(base + Er + offw), c.y);
-        if (!fits && t == 0) *overflow = 1;
-        __syncthreads();
-        // 3. entries (lane order inside each particle's run)
-        if (fits)
-            for (int tt = grp; tt < P; tt += ngrp) {
-                const int i = q0 + tt;
-                const R4 pi = pos[i];
-                const int4 inf = d.pinfo[i];
-                Stencil<Real, LB> st;
-                st.load(d, pi, lane);
-                int cr = 0, cw = 0;
-                for_partners<Real, LB>(d, tab, pos, st, i, pi, [&](int, bool r) { r ? cr++ : cw++; });
-                int tr, tw;
-                int er = inf.x + group_excl_scan<LB>(cr, mask, lane, &tr);
-                int ew = inf.z + group_excl_scan<LB>(cw, mask, lane, &tw);
-                for_partners<Real, LB>(d, tab, pos, st, i, pi, [&](int q, bool r) {
-                    const int e = r ? er++ : ew++;
-                    d.ent_j[e] = q;
-                    d.ent_o[e] = (unsigned short)tt;
-                });
-            }
-        base += Er + Ew;
-        __syncthreads();
     }
     const int np = b1 - b0;
     return np > 0 ? (int)((base - cap_beg + np - 1) / np) : 0;
@@ -657,35 +709,33 @@ __device__ __forceinline__ const PairP<Real>& pair_of(const PairP<Real>* tab, in
     return UNI ? uni : tab[ti * nt + tj];
 }
 
-// Shared-memory staging of one sub-chunk (dynamic shared memory).
+// Shared-memory staging of one sub-chunk (dynamic shared memory): the
+// sub-chunk's own particles and the per-entry results of one wave.  The
+// regions sit at compile-time offsets from one namespace-scope extern
+// __shared__ array, so every access is a direct shared-memory access.
+extern __shared__ __align__(32) unsigned char g_dyn[];
+
 template <typename Real>
 struct Stage {
     typedef typename Dev<Real>::R4 R4;
-    R4* pos;        // [blockDim.x] positions of the sub-chunk's particles
-    R4* vel;        // [blockDim.x] their velocities (asynchronous copy)
-    long long* xq;  // [3 * blockDim.x] their fixed-point positions (asynchronous copy)
-    int4* info;     // [blockDim.x] their pinfo
-    Real* S;        // [blockDim.x] their S
-    Real* w;        // [3 * wave] per-entry results of one wave
-    int wave;       // entries per wave
-
     static constexpr int kWave = sizeof(Real) == 4 ? 8192 : 3072;
-    static size_t bytes(int block)
-    {
-        return (size_t)block * (2 * sizeof(R4) + 3 * sizeof(long long) + sizeof(int4) + sizeof(Real)) +
-               (size_t)3 * kWave * sizeof(Real);
-    }
-    __device__ void carve(unsigned char* base)
-    {
-        const size_t B = blockDim.x;
-        pos = (R4*)base;
-        vel = (R4*)(base + B * sizeof(R4));
-        xq = (long long*)(base + 2 * B * sizeof(R4));
-        info = (int4*)(base + B * (2 * sizeof(R4) + 3 * sizeof(long long)));
-        S = (Real*)(base + B * (2 * sizeof(R4) + 3 * sizeof(long long) + sizeof(int4)));
-        w = (Real*)(base + B * (2 * sizeof(R4) + 3 * sizeof(long long) + sizeof(int4) + sizeof(Real)));
-        wave = kWave;
-    }
+    static constexpr size_t B = kBlock;
+    static constexpr size_t O_POS = 0;                                  // [B] R4 positions
+    static constexpr size_t O_VEL = O_POS + B * sizeof(R4);             // [B] R4 velocities
+    static constexpr size_t O_XQ = O_VEL + B * sizeof(R4);              // [3B] fixed-point positions
+    static constexpr size_t O_INFO = O_XQ + 3 * B * sizeof(long long);  // [B] int4 pinfo
+    static constexpr size_t O_S = O_INFO + B * sizeof(int4);            // [B] S
+    static constexpr size_t O_W = O_S + B * sizeof(Real);               // [3 kWave] entry results
+    static constexpr size_t kBytes = O_W + (size_t)3 * kWave * sizeof(Real);
+    static size_t bytes(int) { return kBytes; }
+
+    static __device__ __forceinline__ R4* pos() { return (R4*)(g_dyn + O_POS); }
+    static __device__ __forceinline__ R4* vel() { return (R4*)(g_dyn + O_VEL); }
+    static __device__ __forceinline__ long long* xq() { return (long long*)(g_dyn + O_XQ); }
+    static __device__ __forceinline__ int4* info() { return (int4*)(g_dyn + O_INFO); }
+    static __device__ __forceinline__ Real* S() { return (Real*)(g_dyn + O_S); }
+    static __device__ __forceinline__ Real* w() { return (Real*)(g_dyn + O_W); }
+    static constexpr int wave = kWave;
 };
 
 // Asynchronous global -> shared copies (no register staging).
@@ -694,8 +744,10 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     if (bytes == 16)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-    else
+    else if (bytes == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -714,10 +766,13 @@ __device__ __forceinline__ void cp_async_r4(R4* smem, const R4* gmem)
 // ---------------------------------------------------------------------------
 // S pass (K-b1): S_i = sum over reactive partners k inside r_cut of a vh(r_ik).
 
+constexpr int kU = 1;  // entries per thread whose loads are in flight together
+
 template <typename Real, bool UNI>
-__device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc, Stage<Real>& sm,
+__device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
                              const PairP<Real>& ps)
 {
+    typedef Stage<Real> SM;
     typedef typename Dev<Real>::R4 R4;
     const R4* pos = d.pos[pc];
     int b0, b1;
@@ -726,40 +781,57 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
     for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
         const int P = min((int)blockDim.x, b1 - q0);
         if (t < P) {
-            sm.pos[t] = pos[q0 + t];
-            sm.info[t] = d.pinfo[q0 + t];
+            SM::pos()[t] = pos[q0 + t];
+            SM::info()[t] = d.pinfo[q0 + t];
         }
         __syncthreads();
-        const int e_beg = sm.info[0].x;
-        const int e_end = sm.info[P - 1].x + sm.info[P - 1].y;
+        const int e_beg = SM::info()[0].x;
+        const int e_end = SM::info()[P - 1].x + SM::info()[P - 1].y;
         Real s = Real(0);
-        for (int wb = e_beg; wb < e_end; wb += sm.wave) {
-            const int we = min(wb + sm.wave, e_end);
-            for (int e = wb + t; e < we; e += blockDim.x) {
-                const int j = d.ent_j[e];
-                const int o = d.ent_o[e];
-                const R4 pj = pos[j];
-                const R4 pi = sm.pos[o];
-                const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj), d.ntypes, ps);
-                Real dx, dy, dz;
-                const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
-                Real sv = Real(0);
-                if (r2 < p.rc2) {
-                    Real vh = Real(1);
-                    if (r2 > p.rmin2) {
-                        Real v, f;
-                        lj_eval(p, r2, v, f);
-                        vh = (p.vshift - v) * p.inv_epshat;
-                    }
-                    sv = p.a * vh;
+        for (int wb = e_beg; wb < e_end; wb += SM::wave) {
+            const int we = min(wb + SM::wave, e_end);
+            // batches of U entries per thread: their indices, then their gathers,
+            // are all in flight together
+            for (int e0 = wb + t; e0 < we; e0 += kU * (int)blockDim.x) {
+                int jj[kU], oo[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int e = e0 + u * (int)blockDim.x;
+                    jj[u] = e < we ? d.ent_j[e] : 0;
+                    oo[u] = e < we ? d.ent_o[e] : 0;
                 }
-                sm.w[e - wb] = sv;
+                R4 pj[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++)
+                    if (e0 + u * (int)blockDim.x < we) pj[u] = pos[jj[u]];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int e = e0 + u * (int)blockDim.x;
+                    if (e >= we) break;
+                    const R4 pi = SM::pos()[oo[u]];
+                    const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj[u]), d.ntypes, ps);
+                    Real dx, dy, dz;
+                    const Real r2 = dist2_listed(pi, pj[u], d, dx, dy, dz);
+                    Real sv = Real(0);
+                    if (r2 < p.rc2) {
+                        Real vh = Real(1);
+                        if (r2 > p.rmin2) {
+                            Real v, f;
+                            lj_eval(p, r2, v, f);
+                            vh = (p.vshift - v) * p.inv_epshat;
+                        }
+                        sv = p.a * vh;
+                    }
+                    SM::w()[e - wb] = sv;
+                }
             }
             __syncthreads();
             if (t < P) {
-                const int4 inf = sm.info[t];
+                const int4 inf = SM::info()[t];
                 const int k0 = max(inf.x, wb), k1 = min(inf.x + inf.y, we);
-                for (int k = k0; k < k1; k++) s += sm.w[k - wb];
+                int k = k0;
+                for (; k + 4 <= k1; k += 4) s += (SM::w()[k - wb] + SM::w()[k + 1 - wb]) + (SM::w()[k + 2 - wb] + SM::w()[k + 3 - wb]);
+                for (; k < k1; k++) s += SM::w()[k - wb];
             }
             __syncthreads();
         }
@@ -827,7 +899,7 @@ template <typename Real>
 __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs& a, int pc,
                                                int ac, int i, Real fx, Real fy, Real fz,
                                                int flags, long long step, PState<Real>& st,
-                                               Real wbits, Acc<Real>& acc)
+                                               Real wbits, Real& kin)
 {
     typedef typename Dev<Real>::R4 R4;
     R4 v = st.v;
@@ -838,7 +910,7 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         v.y += hdt * fy * im;
         v.z += hdt * fz * im;
     }
-    acc.q[Q_K] += Real(0.5) * (v.x * v.x + v.y * v.y + v.z * v.z) / im;
+    kin += Real(0.5) * (v.x * v.x + v.y * v.y + v.z * v.z) * recip(im);
     float disp2 = 0.0f;
     if (flags & F_OPENING) {
         v.x += hdt * fx * im;
@@ -910,11 +982,33 @@ __device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real
     acc.q[Q_W0 + 5] += hf * dy * dz;
 }
 
+// Adds the per-entry forces w[3(k - wb) + c] of entries [k0, k1) to f, four
+// at a time (a fixed order: the result does not depend on the launch).
+template <typename Real>
+__device__ __forceinline__ void sum_run(const Real* w, int wb, int k0, int k1, Real& fx, Real& fy,
+                                        Real& fz)
+{
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+        const Real* p = w + 3 * (k - wb);
+        fx += (p[0] + p[3]) + (p[6] + p[9]);
+        fy += (p[1] + p[4]) + (p[7] + p[10]);
+        fz += (p[2] + p[5]) + (p[8] + p[11]);
+    }
+    for (; k < k1; k++) {
+        const Real* p = w + 3 * (k - wb);
+        fx += p[0];
+        fy += p[1];
+        fz += p[2];
+    }
+}
+
 template <typename Real, bool UNI>
 __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const RunArgs& a, int pc,
-                              int ac, int flags, long long step, Stage<Real>& sm, Acc<Real>& acc,
+                              int ac, int flags, long long step, Acc<Real>& acc,
                               const PairP<Real>& ps, const PairP<Real>& pw)
 {
+    typedef Stage<Real> SM;
     typedef typename Dev<Real>::R4 R4;
     const R4* pos = d.pos[pc];
     int b0, b1;
@@ -927,53 +1021,67 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         if (t < P) {
             const int i = q0 + t;
             // integrator inputs: asynchronous copies, waited for after the entries
-            cp_async_r4(&sm.vel[t], &d.vel[ac][i]);
+            cp_async_r4(&SM::vel()[t], &d.vel[ac][i]);
             if (flags & F_OPENING)
-                for (int c = 0; c < 3; c++) cp_async(&sm.xq[3 * t + c], &d.xq[ac][c * n + i], 8);
+                for (int c = 0; c < 3; c++) cp_async(&SM::xq()[3 * t + c], &d.xq[ac][c * n + i], 8);
             cp_async_commit();
-            sm.pos[t] = pos[i];
-            sm.S[t] = d.S[i];
-            sm.info[t] = d.pinfo[i];
+            SM::pos()[t] = pos[i];
+            SM::S()[t] = d.S[i];
+            SM::info()[t] = d.pinfo[i];
         }
         __syncthreads();
-        const int e_beg = sm.info[0].x;
-        const int e_rend = sm.info[P - 1].x + sm.info[P - 1].y;
-        const int e_end = sm.info[P - 1].z + sm.info[P - 1].w;
+        const int e_beg = SM::info()[0].x;
+        const int e_rend = SM::info()[P - 1].x + SM::info()[P - 1].y;
+        const int e_end = SM::info()[P - 1].z + SM::info()[P - 1].w;
         Real fx = 0, fy = 0, fz = 0;
-        for (int wb = e_beg; wb < e_end; wb += sm.wave) {
-            const int we = min(wb + sm.wave, e_end);
-            for (int e = wb + t; e < we; e += blockDim.x) {
-                const int j = d.ent_j[e];
-                const int o = d.ent_o[e];
-                const R4 pj = pos[j];
-                Real ex, ey, ez;
-                if (e < e_rend)
-                    entry_force<Real, UNI, true>(d, tab, sm.pos[o], pj, sm.S[o], d.S[j], ps, acc, ex, ey, ez);
-                else
-                    entry_force<Real, UNI, false>(d, tab, sm.pos[o], pj, Real(0), Real(0), pw, acc, ex, ey, ez);
-                sm.w[3 * (e - wb) + 0] = ex;
-                sm.w[3 * (e - wb) + 1] = ey;
-                sm.w[3 * (e - wb) + 2] = ez;
+        for (int wb = e_beg; wb < e_end; wb += SM::wave) {
+            const int we = min(wb + SM::wave, e_end);
+            for (int e0 = wb + t; e0 < we; e0 += kU * (int)blockDim.x) {
+                int jj[kU], oo[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int e = e0 + u * (int)blockDim.x;
+                    jj[u] = e < we ? d.ent_j[e] : 0;
+                    oo[u] = e < we ? d.ent_o[e] : 0;
+                }
+                R4 pj[kU];
+                Real sj[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int e = e0 + u * (int)blockDim.x;
+                    if (e < we) pj[u] = pos[jj[u]];
+                    sj[u] = e < e_rend ? d.S[jj[u]] : Real(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const int e = e0 + u * (int)blockDim.x;
+                    if (e >= we) break;
+                    const int o = oo[u];
+                    Real ex, ey, ez;
+                    if (e < e_rend)
+                        entry_force<Real, UNI, true>(d, tab, SM::pos()[o], pj[u], SM::S()[o], sj[u], ps, acc, ex, ey, ez);
+                    else
+                        entry_force<Real, UNI, false>(d, tab, SM::pos()[o], pj[u], Real(0), Real(0), pw, acc, ex, ey, ez);
+                    SM::w()[3 * (e - wb) + 0] = ex;
+                    SM::w()[3 * (e - wb) + 1] = ey;
+                    SM::w()[3 * (e - wb) + 2] = ez;
+                }
             }
             __syncthreads();
             if (t < P) {
-                const int4 inf = sm.info[t];
-                int k0 = max(inf.x, wb), k1 = min(inf.x + inf.y, we);
-                for (int k = k0; k < k1; k++) {
-                    fx += sm.w[3 * (k - wb) + 0];
-                    fy += sm.w[3 * (k - wb) + 1];
-                    fz += sm.w[3 * (k - wb) + 2];
-                }
-                k0 = max(inf.z, wb);
-                k1 = min(inf.z + inf.w, we);
-                for (int k = k0; k < k1; k++) {
-                    fx += sm.w[3 * (k - wb) + 0];
-                    fy += sm.w[3 * (k - wb) + 1];
-                    fz += sm.w[3 * (k - wb) + 2];
-                }
+                const int4 inf = SM::info()[t];
+                sum_run(SM::w(), wb, max(inf.x, wb), min(inf.x + inf.y, we), fx, fy, fz);
+                sum_run(SM::w(), wb, max(inf.z, wb), min(inf.z + inf.w, we), fx, fy, fz);
             }
             __syncthreads();
         }
+        // FP32: park the thermo accumulators in the (now free) wave buffer while
+        // the integrator runs, so they do not hold registers at its peak
+        constexpr bool kPark = sizeof(Real) == 4;
+        if (kPark)
+#pragma unroll
+            for (int q = 0; q < kNQA; q++) SM::w()[q * blockDim.x + t] = acc.q[q];
+        Real kin = Real(0);
         if (t < P) {
             const int i = q0 + t;
             if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&d.ctl->status, kStatusNonfinite);
@@ -987,11 +1095,15 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             }
             cp_async_wait_all();
             PState<Real> st;
-            st.v = sm.vel[t];
+            st.v = SM::vel()[t];
             if (flags & F_OPENING)
-                for (int c = 0; c < 3; c++) st.q[c] = sm.xq[3 * t + c];
-            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, sm.pos[t].w, acc));
+                for (int c = 0; c < 3; c++) st.q[c] = SM::xq()[3 * t + c];
+            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, SM::pos()[t].w, kin));
         }
+        if (kPark)
+#pragma unroll
+            for (int q = 0; q < kNQA; q++) acc.q[q] = SM::w()[q * blockDim.x + t];
+        acc.q[Q_K] += kin;
         __syncthreads();
     }
     return dmax;
@@ -1007,9 +1119,7 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
     const R4 pi = d.pos[pc][i];
     PState<Real> st;
     load_pstate(d, ac, i, F_OPENING, st);
-    Acc<Real> unused;
-#pragma unroll
-    for (int q = 0; q < kNQA; q++) unused.q[q] = Real(0);
+    Real unused = Real(0);
     return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, st, pi.w, unused);
 }
 
@@ -1018,238 +1128,277 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
 // steps (or only rebuilds, or only brings the forces up to date), with two
 // grid barriers per step and a rebuild whenever the accumulated displacement
 // bound can let an unlisted pair come inside its cut-off.
+//
+// Block-wide state lives in shared memory at namespace scope (addressed
+// directly, not through pointers), so that nothing but the phase at hand
+// occupies registers: the kernel runs at the 64-register limit of a
+// 1024-thread block.
 
-template <typename Real, int LB, bool UNI>
-struct Runner {
-    typedef typename Dev<Real>::R4 R4;
-    const Dev<Real>& d;
-    const RunArgs& a;
-    PairP<Real>* tab;
-    double* sh_red;
-    int* sh_int;
-    float* sh_f;
-    int* s_ok;
-    float* s_disp;
-    int2* sh_cnt;
-    Stage<Real> sm;
-    Ctl* ctl;
-    int gt, gn;
-    int pc, ac;
+struct LoopState {
+    unsigned long long bar_target;  // barrier generation target (thread 0)
+    long long step;
     long long rebuilds;
-    BarState bs;
-    const PairP<Real>& ps;  // uniform coefficients (UNI), in the kernel-parameter bank
-    const PairP<Real>& pw;
-
-    __device__ Runner(const Dev<Real>& d_, const RunArgs& a_, PairP<Real>* tab_, double* sr,
-                      int* si, float* sf, int* so, float* sd, unsigned char* dyn)
-        : d(d_), a(a_), tab(tab_), sh_red(sr), sh_int(si), sh_f(sf), s_ok(so), s_disp(sd),
-          ctl(d_.ctl), ps(uni_params(a_, Real(0))[0]), pw(uni_params(a_, Real(0))[1])
-    {
-        gt = blockIdx.x * blockDim.x + threadIdx.x;
-        gn = gridDim.x * blockDim.x;
-        rebuilds = 0;
-        bs.target = 0;
-        sm.carve(dyn);
-        sh_cnt = (int2*)sm.w;  // the build's counts reuse the wave buffer
-    }
-
-    __device__ __forceinline__ bool barrier(int where)
-    {
-        bar_arrive(ctl, bs);
-        return bar_wait(ctl, bs, a.timeout_ns, where, s_ok);
-    }
-
-    // 0: ok; 1: the list overflowed its capacity; 2: a wait timed out.
-    __device__ int rebuild()
-    {
-        if (threadIdx.x == 0 && blockIdx.x == 0) {
-            ctl->max_row = 0;
-            ctl->overflow = 0;
-        }
-        ph_bin(d, pc, gt, gn);  // cell counts start at zero (see ph_chunk_scan)
-        if (!barrier(1)) return 2;
-        ph_chunk_sums(d, sh_int);
-        if (!barrier(2)) return 2;
-        ph_chunk_scan(d, sh_int);
-        if (!barrier(3)) return 2;
-        ph_scatter(d, gt, gn);
-        if (!barrier(4)) return 2;
-        ph_cell_sort(d, gt, gn);
-        if (!barrier(5)) return 2;
-        ph_gather(d, pc, ac, gt, gn);
-        pc ^= 1;
-        ac ^= 1;
-        if (!barrier(6)) return 2;
-        int ovf = 0;
-        const int need = ph_build_block<Real, LB>(d, tab, pc, sh_cnt, sh_int, &ovf);
-        if (threadIdx.x == 0) {
-            atomicMax(&ctl->max_row, need);
-            if (ovf) atomicOr(&ctl->overflow, 1);
-        }
-        if (!barrier(7)) return 2;
-        const int any_ovf = ld_relaxed(&ctl->overflow);
-        rebuilds++;
-        if (threadIdx.x == 0) *s_disp = 0.0f;
-        __syncthreads();
-        if (any_ovf) {
-            if (gt == 0) atomicOr(&ctl->status, kStatusOverflow);
-            return 1;
-        }
-        return 0;
-    }
-
-    __device__ void s_pass() { s_pass_block<Real, UNI>(d, tab, pc, sm, ps); }
-
-    __device__ void f_pass(int flags, long long stp, int par)
-    {
-        Acc<Real> acc;
-#pragma unroll
-        for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
-        float dmax = f_pass_block<Real, UNI>(d, tab, a, pc, ac, flags, stp, sm, acc, ps, pw);
-        block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, sh_red);
-        if (flags & F_OPENING) {
-            float m = block_max(dmax, sh_f);
-            if (threadIdx.x == 0 && m > 0.0f) atomicMax(&ctl->dmax2[stp & 1], __float_as_uint(m));
-        }
-    }
-
-    __device__ void open_pass(long long stp)
-    {
-        float dmax = 0.0f;
-        for (int i = gt; i < d.n; i += gn) dmax = fmaxf(dmax, open_from_stored(d, a, pc, ac, i, stp));
-        float m = block_max(dmax, sh_f);
-        if (threadIdx.x == 0 && m > 0.0f) atomicMax(&ctl->dmax2[stp & 1], __float_as_uint(m));
-    }
-
-    // Deterministic reduction of one force pass's block partials: block q
-    // sums quantity q over all blocks in a fixed order.
-    __device__ void reduce_thermo(int par)
-    {
-        if (blockIdx.x >= kNQ) return;
-        double s = 0.0;
-        const double* src = d.partials + (size_t)par * a.max_blocks * kNQ + blockIdx.x;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += src[(size_t)b * kNQ];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
-        if (lw == 0) sh_red[w] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++) t += sh_red[k];
-            ctl->thermo[blockIdx.x] = t;
-        }
-        __syncthreads();
-    }
-
-    __device__ void add_disp(long long stp)
-    {
-        if (threadIdx.x == 0)
-            *s_disp += sqrtf(__uint_as_float((unsigned)ld_relaxed((const int*)&ctl->dmax2[stp & 1])));
-        __syncthreads();
-    }
+    int state, pc, ac, need_rb, remaining, done, parity, have_thermo, rc, ok;
+    float disp;
 };
 
-template <typename Real, int LB, bool UNI>
+static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
+static __shared__ double s_red[kNQ * 32];
+static __shared__ int s_int[64];
+static __shared__ float s_f[32];
+static __shared__ LoopState s_ls;
+
+template <typename Real>
+__device__ __forceinline__ const PairP<Real>* stab() { return (const PairP<Real>*)s_tab_raw; }
+
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, long long timeout_ns, int where)
+{
+    BarState bs;
+    bs.target = s_ls.bar_target;
+    bar_arrive(ctl, bs);
+    if (threadIdx.x == 0) s_ls.bar_target = bs.target;
+    return bar_wait(ctl, bs, timeout_ns, where, &s_ls.ok);
+}
+
+// 0: ok; 1: the list overflowed its capacity; 2: a wait timed out.
+template <typename Real>
+__device__ int run_rebuild(const Dev<Real>& d, const RunArgs& a)
+{
+    Ctl* ctl = d.ctl;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gn = gridDim.x * blockDim.x;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctl->max_row = 0;
+        ctl->overflow = 0;
+    }
+    const int pc0 = s_ls.pc, ac0 = s_ls.ac;
+    ph_bin(d, pc0, gt, gn);  // cell counts start at zero (see ph_chunk_scan)
+    if (!grid_barrier(ctl, a.timeout_ns, 1)) return 2;
+    ph_chunk_sums(d, s_int);
+    if (!grid_barrier(ctl, a.timeout_ns, 2)) return 2;
+    ph_chunk_scan(d, s_int);
+    if (!grid_barrier(ctl, a.timeout_ns, 3)) return 2;
+    ph_scatter(d, gt, gn);
+    if (!grid_barrier(ctl, a.timeout_ns, 4)) return 2;
+    ph_cell_sort(d, gt, gn);
+    if (!grid_barrier(ctl, a.timeout_ns, 5)) return 2;
+    ph_gather(d, pc0, ac0, gt, gn);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ls.pc = pc0 ^ 1;
+        s_ls.ac = ac0 ^ 1;
+    }
+    if (!grid_barrier(ctl, a.timeout_ns, 6)) return 2;
+    int ovf = 0;
+    const int need = ph_build_cells<Real>(d, stab<Real>(), pc0 ^ 1, (int2*)Stage<Real>::w(), s_int, &ovf);
+    if (threadIdx.x == 0) {
+        atomicMax(&ctl->max_row, need);
+        if (ovf) atomicOr(&ctl->overflow, 1);
+    }
+    if (!grid_barrier(ctl, a.timeout_ns, 7)) return 2;
+    const int any_ovf = ld_relaxed(&ctl->overflow);
+    if (threadIdx.x == 0) {
+        s_ls.rebuilds++;
+        s_ls.disp = 0.0f;
+    }
+    __syncthreads();
+    if (any_ovf) {
+        if (gt == 0) atomicOr(&ctl->status, kStatusOverflow);
+        return 1;
+    }
+    return 0;
+}
+
+template <typename Real, bool UNI>
+__device__ __forceinline__ void run_s_pass(const Dev<Real>& d, const RunArgs& a)
+{
+    s_pass_block<Real, UNI>(d, stab<Real>(), s_ls.pc, uni_params(a, Real(0))[0]);
+}
+
+template <typename Real, bool UNI>
+__device__ void run_f_pass(const Dev<Real>& d, const RunArgs& a, int flags, long long stp, int par)
+{
+    Acc<Real> acc;
+#pragma unroll
+    for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
+    const float dmax = f_pass_block<Real, UNI>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
+                                               uni_params(a, Real(0))[0], uni_params(a, Real(0))[1]);
+    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, s_red);
+    if (flags & F_OPENING) {
+        const float m = block_max(dmax, s_f);
+        if (threadIdx.x == 0 && m > 0.0f) atomicMax(&d.ctl->dmax2[stp & 1], __float_as_uint(m));
+    }
+}
+
+template <typename Real>
+__device__ void run_open_pass(const Dev<Real>& d, const RunArgs& a, long long stp)
+{
+    float dmax = 0.0f;
+    const int pc = s_ls.pc, ac = s_ls.ac;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x)
+        dmax = fmaxf(dmax, open_from_stored(d, a, pc, ac, i, stp));
+    const float m = block_max(dmax, s_f);
+    if (threadIdx.x == 0 && m > 0.0f) atomicMax(&d.ctl->dmax2[stp & 1], __float_as_uint(m));
+}
+
+// Deterministic reduction of one force pass's block partials: block q sums
+// quantity q over all blocks in a fixed order.
+template <typename Real>
+__device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
+{
+    if (blockIdx.x >= kNQ) return;
+    const int G = gridDim.x, nwp = (G + 31) / 32;
+    const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < nwp) {
+        const double* src = d.partials + (size_t)par * a.max_blocks * kNQ + blockIdx.x;
+        const int b = threadIdx.x;
+        double v = b < G ? src[(size_t)b * kNQ] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lw == 0) s_red[w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < nwp; k++) t += s_red[k];
+        d.ctl->thermo[blockIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
+{
+    if (threadIdx.x == 0)
+        s_ls.disp += sqrtf(__uint_as_float((unsigned)ld_relaxed((const int*)&ctl->dmax2[stp & 1])));
+    __syncthreads();
+}
+
+template <typename Real, bool UNI>
 __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 {
-    __shared__ PairP<Real> tab[kMaxTypes * kMaxTypes];
-    __shared__ double sh_red[kNQ * 32];
-    __shared__ int sh_int[64];
-    __shared__ float sh_f[32];
-    __shared__ int s_ok;
-    __shared__ float s_disp;
-    extern __shared__ __align__(32) unsigned char dyn[];
-
     Ctl* ctl = d.ctl;
+    PairP<Real>* tab = (PairP<Real>*)s_tab_raw;
     const int ntt = d.ntypes * d.ntypes;
     for (int t = threadIdx.x; t < ntt; t += blockDim.x) tab[t] = d.table[t];
-    if (threadIdx.x == 0) s_disp = (float)ctl->disp;
-
-    int state = ctl->state;
-    long long step = ctl->step;
-    // the list's block partition depends on the grid: rebuild if it changed
-    int need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != (int)gridDim.x);
-    int remaining = a.nsteps;
-    int done = 0;
-    int parity = 0;
-    int have_thermo = 0;
-    int rc = 0;  // 0 ok, 1 overflow
+    if (threadIdx.x == 0) {
+        s_ls.bar_target = 0;
+        s_ls.step = ctl->step;
+        s_ls.rebuilds = 0;
+        s_ls.state = ctl->state;
+        s_ls.pc = ctl->pos_cur;
+        s_ls.ac = ctl->arr_cur;
+        // the list's block partition depends on the grid: rebuild if it changed
+        s_ls.need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != (int)gridDim.x);
+        s_ls.remaining = a.nsteps;
+        s_ls.done = 0;
+        s_ls.parity = 0;
+        s_ls.have_thermo = 0;
+        s_ls.rc = 0;
+        s_ls.disp = (float)ctl->disp;
+    }
     __syncthreads();
-    Runner<Real, LB, UNI> R(d, a, tab, sh_red, sh_int, sh_f, &s_ok, &s_disp, dyn);
-    R.pc = ctl->pos_cur;
-    R.ac = ctl->arr_cur;
+    const float skin_eff = (float)a.skin_eff;
 
     if (a.build_only) {
-        rc = R.rebuild();
+        const int rc = run_rebuild(d, a);
         if (rc == 2) return;
-        need_rb = rc;
+        if (threadIdx.x == 0) {
+            s_ls.need_rb = rc;
+            s_ls.rc = rc;
+        }
+        __syncthreads();
     } else {
-        if (state == 1) {
-            if (need_rb || 2.0f * s_disp > (float)a.skin_eff) {
-                rc = R.rebuild();
+        if (s_ls.state == 1) {
+            if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
+                const int rc = run_rebuild(d, a);
                 if (rc == 2) return;
-                need_rb = rc;
+                if (threadIdx.x == 0) {
+                    s_ls.need_rb = rc;
+                    s_ls.rc = rc;
+                }
+                __syncthreads();
             }
-            if (rc == 0) {
-                R.s_pass();
-                if (!R.barrier(10)) return;
-                parity = (int)(step & 1);
-                R.f_pass(F_STORE, step, parity);
-                have_thermo = 1;
-                state = 0;
-                if (!R.barrier(11)) return;
+            if (s_ls.rc == 0) {
+                run_s_pass<Real, UNI>(d, a);
+                if (!grid_barrier(ctl, a.timeout_ns, 10)) return;
+                const int par = (int)(s_ls.step & 1);
+                run_f_pass<Real, UNI>(d, a, F_STORE, s_ls.step, par);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    s_ls.parity = par;
+                    s_ls.have_thermo = 1;
+                    s_ls.state = 0;
+                }
+                if (!grid_barrier(ctl, a.timeout_ns, 11)) return;
             }
         }
-        if (rc == 0 && remaining > 0 && state == 0) {
-            if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dmax2[step & 1] = 0u;
-            if (!R.barrier(12)) return;
-            R.open_pass(step);
-            R.pc ^= 1;
-            state = 2;
-            if (!R.barrier(13)) return;
-            R.add_disp(step);
+        if (s_ls.rc == 0 && s_ls.remaining > 0 && s_ls.state == 0) {
+            const long long stp = s_ls.step;
+            if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dmax2[stp & 1] = 0u;
+            if (!grid_barrier(ctl, a.timeout_ns, 12)) return;
+            run_open_pass(d, a, stp);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_ls.pc ^= 1;
+                s_ls.state = 2;
+            }
+            if (!grid_barrier(ctl, a.timeout_ns, 13)) return;
+            add_disp(ctl, stp);
         }
-        while (rc == 0 && state == 2) {
-            if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dmax2[(step + 1) & 1] = 0u;
-            if (need_rb || 2.0f * s_disp > (float)a.skin_eff) {
-                rc = R.rebuild();
+        while (s_ls.rc == 0 && s_ls.state == 2) {
+            const long long stp = s_ls.step;
+            if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dmax2[(stp + 1) & 1] = 0u;
+            if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
+                const int rc = run_rebuild(d, a);
                 if (rc == 2) return;
-                need_rb = rc;
+                if (threadIdx.x == 0) {
+                    s_ls.need_rb = rc;
+                    s_ls.rc = rc;
+                }
+                __syncthreads();
                 if (rc) break;
             }
-            R.s_pass();
-            bar_arrive(ctl, R.bs);
-            if (have_thermo) R.reduce_thermo(parity);  // previous pass, overlapped with the wait
-            if (!bar_wait(ctl, R.bs, a.timeout_ns, 20, &s_ok)) return;
-            const bool more = remaining > 1;
-            parity = (int)((step + 1) & 1);
-            R.f_pass(F_CLOSING | (more ? F_OPENING : F_STORE), step + 1, parity);
-            have_thermo = 1;
-            step++;
-            remaining--;
-            done++;
-            if (!R.barrier(21)) return;
+            run_s_pass<Real, UNI>(d, a);
+            {
+                BarState bs;
+                bs.target = s_ls.bar_target;
+                bar_arrive(ctl, bs);
+                if (threadIdx.x == 0) s_ls.bar_target = bs.target;
+                if (s_ls.have_thermo) run_reduce_thermo(d, a, s_ls.parity);  // overlapped with the wait
+                if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return;
+            }
+            const bool more = s_ls.remaining > 1;
+            const int par = (int)((stp + 1) & 1);
+            run_f_pass<Real, UNI>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, par);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_ls.parity = par;
+                s_ls.have_thermo = 1;
+                s_ls.step = stp + 1;
+                s_ls.remaining--;
+                s_ls.done++;
+            }
+            if (!grid_barrier(ctl, a.timeout_ns, 21)) return;
             if (more) {
-                R.pc ^= 1;
-                R.add_disp(step);
+                if (threadIdx.x == 0) s_ls.pc ^= 1;
+                add_disp(ctl, stp + 1);
             } else {
-                state = 0;
+                if (threadIdx.x == 0) s_ls.state = 0;
+                __syncthreads();
             }
         }
     }
-    if (have_thermo) R.reduce_thermo(parity);
+    if (s_ls.have_thermo) run_reduce_thermo(d, a, s_ls.parity);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->state = state;
-        ctl->pos_cur = R.pc;
-        ctl->arr_cur = R.ac;
-        ctl->step = step;
-        ctl->disp = s_disp;
-        ctl->n_rebuilds += R.rebuilds;
-        ctl->steps_done = done;
-        ctl->need_rebuild = need_rb;
-        if (R.rebuilds > 0) ctl->list_grid = rc == 0 ? (int)gridDim.x : -1;
-        if (have_thermo) ctl->thermo[Q_SPARE0] = (double)step;
+        ctl->state = s_ls.state;
+        ctl->pos_cur = s_ls.pc;
+        ctl->arr_cur = s_ls.ac;
+        ctl->step = s_ls.step;
+        ctl->disp = s_ls.disp;
+        ctl->n_rebuilds += s_ls.rebuilds;
+        ctl->steps_done = s_ls.done;
+        ctl->need_rebuild = s_ls.need_rb;
+        if (s_ls.rebuilds > 0) ctl->list_grid = s_ls.rc == 0 ? (int)gridDim.x : -1;
+        if (s_ls.have_thermo) ctl->thermo[Q_SPARE0] = (double)s_ls.step;
     }
 }
 

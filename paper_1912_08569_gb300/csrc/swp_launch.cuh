@@ -6,24 +6,16 @@
 
 namespace swp {
 
-template <typename Real, bool UNI>
-static void* run_fn_u(int lanes)
+template <typename Real>
+static void* run_fn(int uni)
 {
-    switch (lanes) {
-    case 1: return (void*)k_run<Real, 1, UNI>;
-    case 2: return (void*)k_run<Real, 2, UNI>;
-    case 4: return (void*)k_run<Real, 4, UNI>;
-    case 8: return (void*)k_run<Real, 8, UNI>;
-    case 16: return (void*)k_run<Real, 16, UNI>;
-    case 32: return (void*)k_run<Real, 32, UNI>;
-    default: return nullptr;
-    }
+    return uni ? (void*)k_run<Real, true> : (void*)k_run<Real, false>;
 }
 
 template <typename Real>
 size_t run_smem_bytes()
 {
-    return Stage<Real>::bytes(kBlock);
+    return Stage<Real>::kBytes;
 }
 
 // Opts every variant into the dynamic shared memory it needs (once).
@@ -35,17 +27,9 @@ static cudaError_t prepare_fn(void* fn)
 }
 
 template <typename Real>
-static void* run_fn(int lanes, int uni)
+cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, cudaStream_t s)
 {
-    return uni ? run_fn_u<Real, true>(lanes) : run_fn_u<Real, false>(lanes);
-}
-
-template <typename Real>
-cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, int lanes,
-                       cudaStream_t s)
-{
-    void* fn = run_fn<Real>(lanes, a.uni);
-    if (!fn) return cudaErrorInvalidValue;
+    void* fn = run_fn<Real>(a.uni);
     cudaError_t e = prepare_fn<Real>(fn);
     if (e != cudaSuccess) return e;
     Dev<Real> dd = d;
@@ -55,11 +39,10 @@ cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block
 }
 
 template <typename Real>
-cudaError_t run_occupancy(int block, int lanes, int* blocks_per_sm)
+cudaError_t run_occupancy(int block, int* blocks_per_sm)
 {
-    void* fu = run_fn<Real>(lanes, 1);
-    void* fg = run_fn<Real>(lanes, 0);
-    if (!fu || !fg) return cudaErrorInvalidValue;
+    void* fu = run_fn<Real>(1);
+    void* fg = run_fn<Real>(0);
     int bu = 0, bg = 0;
     cudaError_t e = prepare_fn<Real>(fu);
     if (e == cudaSuccess) e = prepare_fn<Real>(fg);
@@ -105,8 +88,8 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
 }
 
 #define SWP_INSTANTIATE(R)                                                                       \
-    template cudaError_t launch_run<R>(const Dev<R>&, const RunArgs&, int, int, int, cudaStream_t); \
-    template cudaError_t run_occupancy<R>(int, int, int*);                                       \
+    template cudaError_t launch_run<R>(const Dev<R>&, const RunArgs&, int, int, cudaStream_t);   \
+    template cudaError_t run_occupancy<R>(int, int*);                                            \
     template cudaError_t launch_set_state<R>(const Dev<R>&, cudaStream_t);                       \
     template cudaError_t launch_get_state<R>(const Dev<R>&, int, int, cudaStream_t);             \
     template cudaError_t launch_get_forces<R>(const Dev<R>&, int, cudaStream_t);                 \

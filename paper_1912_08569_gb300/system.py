@@ -25,7 +25,7 @@ class SwapSystem:
     """
 
     def __init__(self, n, n_types, box, pairs, precision="fp32", seed=0, skin=0.3, max_nn=None,
-                 lanes=16, blocks_per_sm=0, device=None, stream=None):
+                 blocks_per_sm=0, device=None, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -53,7 +53,7 @@ class SwapSystem:
             max_nn = max(16, _round_up(int(2.0 * expect + 16), 8))
         self.max_nn = int(max_nn)
         A.swp_set_nlist(self.ctx, self.skin, self.max_nn)
-        A.swp_set_launch(self.ctx, lanes, blocks_per_sm)
+        A.swp_set_launch(self.ctx, blocks_per_sm)
         ws = A.swp_workspace_size(self.ctx)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
         A.swp_bind_workspace(self.ctx, self.workspace.data_ptr(), ws, self.stream.cuda_stream)
@@ -73,7 +73,7 @@ class SwapSystem:
         self.grows += 1
 
     def set_launch(self, lanes: int, blocks_per_sm: int = 0):
-        A.swp_set_launch(self.ctx, lanes, blocks_per_sm)
+        A.swp_set_launch(self.ctx, blocks_per_sm)
 
     def set_timeout(self, ns: int):
         A.swp_set_timeout(self.ctx, ns)

@@ -16,11 +16,11 @@ def oracle_pairs(orc, wl):
     return orc.pair_table(wl["n_types"], wl["pairs"])
 
 
-def make_gpu(wl, precision="fp32", lanes=16, **kw):
+def make_gpu(wl, precision="fp32", **kw):
     from paper_1912_08569_gb300 import SwapSystem
 
     s = SwapSystem(wl["n"], wl["n_types"], wl["box"], wl["pairs"], precision=precision,
-                   seed=wl.get("seed", 0), skin=wl.get("skin", 0.3), lanes=lanes, **kw)
+                   seed=wl.get("seed", 0), skin=wl.get("skin", 0.3), **kw)
     s.set_state(wl["x"], wl.get("v"), wl["types"], wl.get("mass"))
     return s
 
