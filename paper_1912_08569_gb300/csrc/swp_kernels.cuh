@@ -151,7 +151,15 @@ __device__ __forceinline__ Real ipow(Real b, int e)
     return r;
 }
 
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// FP32: the hardware reciprocal approximation (PTX rcp.approx, relative error
+// below 2^-22): it feeds only the values of the potential and forces, never a
+// decision, and its error is far inside the FP32 force tolerance.
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Eq. 2b at squared distance r2: v and f = -(dv/dr)/r.
@@ -256,10 +264,19 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 // Arrival: the block's writes are ordered before a release add on the
 // counter (after the block-wide __syncthreads, thread 0's release is
 // cumulative over them).  Generation g completes at count g * gridDim.x.
-__device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b)
+// With pub_dst set, thread 0 first folds the block's shared maximum *pub_src
+// into the global maximum *pub_dst (and clears it), so the other blocks see
+// it after their wait.
+__device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_dst = nullptr,
+                                           unsigned* pub_src = nullptr)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (pub_dst) {
+            const unsigned m = *pub_src;
+            if (m) atomicMax(pub_dst, m);
+            *pub_src = 0u;
+        }
         b.target += gridDim.x;
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
     }
@@ -331,23 +348,6 @@ __device__ __forceinline__ void block_thermo(const Real* acc, double* out, doubl
         out[kNQA + lane] = 0.0;
     }
     __syncthreads();
-}
-
-__device__ __forceinline__ float block_max(float v, float* sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    float m = 0.0f;
-    if (warp == 0) {
-        m = lane < nw ? sh[lane] : 0.0f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    __syncthreads();
-    return m;  // valid in thread 0
 }
 
 __device__ __forceinline__ int block_max_int(int v, int* sh)
@@ -725,8 +725,8 @@ struct Stage {
     static constexpr size_t O_XQ = O_VEL + B * sizeof(R4);              // [3B] fixed-point positions
     static constexpr size_t O_INFO = O_XQ + 3 * B * sizeof(long long);  // [B] int4 pinfo
     static constexpr size_t O_S = O_INFO + B * sizeof(int4);            // [B] S
-    static constexpr size_t O_W = O_S + B * sizeof(Real);               // [3 kWave] entry results
-    static constexpr size_t kBytes = O_W + (size_t)3 * kWave * sizeof(Real);
+    static constexpr size_t O_W = O_S + B * sizeof(Real);               // [kWave] R4 entry results
+    static constexpr size_t kBytes = O_W + (size_t)kWave * sizeof(R4);
     static size_t bytes(int) { return kBytes; }
 
     static __device__ __forceinline__ R4* pos() { return (R4*)(g_dyn + O_POS); }
@@ -735,6 +735,7 @@ struct Stage {
     static __device__ __forceinline__ int4* info() { return (int4*)(g_dyn + O_INFO); }
     static __device__ __forceinline__ Real* S() { return (Real*)(g_dyn + O_S); }
     static __device__ __forceinline__ Real* w() { return (Real*)(g_dyn + O_W); }
+    static __device__ __forceinline__ R4* w4() { return (R4*)(g_dyn + O_W); }
     static constexpr int wave = kWave;
 };
 
@@ -982,24 +983,18 @@ __device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real
     acc.q[Q_W0 + 5] += hf * dy * dz;
 }
 
-// Adds the per-entry forces w[3(k - wb) + c] of entries [k0, k1) to f, four
-// at a time (a fixed order: the result does not depend on the launch).
-template <typename Real>
-__device__ __forceinline__ void sum_run(const Real* w, int wb, int k0, int k1, Real& fx, Real& fy,
+// Adds the per-entry forces w[k - wb] (one vector load each) of entries
+// [k0, k1) to f in entry order (the result does not depend on the launch).
+template <typename Real, typename R4>
+__device__ __forceinline__ void sum_run(const R4* w, int wb, int k0, int k1, Real& fx, Real& fy,
                                         Real& fz)
 {
-    int k = k0;
-    for (; k + 4 <= k1; k += 4) {
-        const Real* p = w + 3 * (k - wb);
-        fx += (p[0] + p[3]) + (p[6] + p[9]);
-        fy += (p[1] + p[4]) + (p[7] + p[10]);
-        fz += (p[2] + p[5]) + (p[8] + p[11]);
-    }
-    for (; k < k1; k++) {
-        const Real* p = w + 3 * (k - wb);
-        fx += p[0];
-        fy += p[1];
-        fz += p[2];
+#pragma unroll 2
+    for (int k = k0; k < k1; k++) {
+        const R4 p = w[k - wb];
+        fx += p.x;
+        fy += p.y;
+        fz += p.z;
     }
 }
 
@@ -1062,16 +1057,19 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
                         entry_force<Real, UNI, true>(d, tab, SM::pos()[o], pj[u], SM::S()[o], sj[u], ps, acc, ex, ey, ez);
                     else
                         entry_force<Real, UNI, false>(d, tab, SM::pos()[o], pj[u], Real(0), Real(0), pw, acc, ex, ey, ez);
-                    SM::w()[3 * (e - wb) + 0] = ex;
-                    SM::w()[3 * (e - wb) + 1] = ey;
-                    SM::w()[3 * (e - wb) + 2] = ez;
+                    R4 r;
+                    r.x = ex;
+                    r.y = ey;
+                    r.z = ez;
+                    r.w = Real(0);
+                    SM::w4()[e - wb] = r;
                 }
             }
             __syncthreads();
             if (t < P) {
                 const int4 inf = SM::info()[t];
-                sum_run(SM::w(), wb, max(inf.x, wb), min(inf.x + inf.y, we), fx, fy, fz);
-                sum_run(SM::w(), wb, max(inf.z, wb), min(inf.z + inf.w, we), fx, fy, fz);
+                sum_run(SM::w4(), wb, max(inf.x, wb), min(inf.x + inf.y, we), fx, fy, fz);
+                sum_run(SM::w4(), wb, max(inf.z, wb), min(inf.z + inf.w, we), fx, fy, fz);
             }
             __syncthreads();
         }
@@ -1140,22 +1138,23 @@ struct LoopState {
     long long rebuilds;
     int state, pc, ac, need_rb, remaining, done, parity, have_thermo, rc, ok;
     float disp;
+    unsigned dmax_bits;  // the block's largest squared step displacement (float bits)
 };
 
 static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
 static __shared__ double s_red[kNQ * 32];
 static __shared__ int s_int[64];
-static __shared__ float s_f[32];
 static __shared__ LoopState s_ls;
 
 template <typename Real>
 __device__ __forceinline__ const PairP<Real>* stab() { return (const PairP<Real>*)s_tab_raw; }
 
-__device__ __forceinline__ bool grid_barrier(Ctl* ctl, long long timeout_ns, int where)
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, long long timeout_ns, int where,
+                                             unsigned* pub_dst = nullptr)
 {
     BarState bs;
     bs.target = s_ls.bar_target;
-    bar_arrive(ctl, bs);
+    bar_arrive(ctl, bs, pub_dst, &s_ls.dmax_bits);
     if (threadIdx.x == 0) s_ls.bar_target = bs.target;
     return bar_wait(ctl, bs, timeout_ns, where, &s_ls.ok);
 }
@@ -1214,19 +1213,24 @@ __device__ __forceinline__ void run_s_pass(const Dev<Real>& d, const RunArgs& a)
     s_pass_block<Real, UNI>(d, stab<Real>(), s_ls.pc, uni_params(a, Real(0))[0]);
 }
 
-template <typename Real, bool UNI>
-__device__ void run_f_pass(const Dev<Real>& d, const RunArgs& a, int flags, long long stp, int par)
+// Folds a thread's squared displacement into the block's shared maximum (one
+// shared atomic per warp); the barrier arrival publishes it.
+__device__ __forceinline__ void warp_max_disp(float v)
 {
-    Acc<Real> acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&s_ls.dmax_bits, __float_as_uint(v));
+}
+
+template <typename Real, bool UNI>
+__device__ __forceinline__ void run_f_pass(const Dev<Real>& d, const RunArgs& a, int flags, long long stp,
+                                           Acc<Real>& acc)
+{
 #pragma unroll
     for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
     const float dmax = f_pass_block<Real, UNI>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
                                                uni_params(a, Real(0))[0], uni_params(a, Real(0))[1]);
-    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, s_red);
-    if (flags & F_OPENING) {
-        const float m = block_max(dmax, s_f);
-        if (threadIdx.x == 0 && m > 0.0f) atomicMax(&d.ctl->dmax2[stp & 1], __float_as_uint(m));
-    }
+    if (flags & F_OPENING) warp_max_disp(dmax);
 }
 
 template <typename Real>
@@ -1236,8 +1240,7 @@ __device__ void run_open_pass(const Dev<Real>& d, const RunArgs& a, long long st
     const int pc = s_ls.pc, ac = s_ls.ac;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x)
         dmax = fmaxf(dmax, open_from_stored(d, a, pc, ac, i, stp));
-    const float m = block_max(dmax, s_f);
-    if (threadIdx.x == 0 && m > 0.0f) atomicMax(&d.ctl->dmax2[stp & 1], __float_as_uint(m));
+    warp_max_disp(dmax);
 }
 
 // Deterministic reduction of one force pass's block partials: block q sums
@@ -1245,7 +1248,7 @@ __device__ void run_open_pass(const Dev<Real>& d, const RunArgs& a, long long st
 template <typename Real>
 __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
 {
-    if (blockIdx.x >= kNQ) return;
+    if (blockIdx.x >= kNQA) return;
     const int G = gridDim.x, nwp = (G + 31) / 32;
     const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w < nwp) {
@@ -1263,6 +1266,30 @@ __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
         d.ctl->thermo[blockIdx.x] = t;
     }
     __syncthreads();
+}
+
+// The barrier that ends a force pass.  After arriving (and publishing the
+// block's displacement maximum when the pass drifted), while the other blocks
+// finish, the block sums its thermo accumulators of this pass into its
+// partials, and the blocks that own a quantity reduce the previous pass's
+// partials: every block wrote those before arriving at the barrier that
+// followed that pass, which this block has passed.
+template <typename Real>
+__device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, const Acc<Real>& acc,
+                                          int par, unsigned* pub_dst, int where)
+{
+    BarState bs;
+    bs.target = s_ls.bar_target;
+    bar_arrive(d.ctl, bs, pub_dst, &s_ls.dmax_bits);
+    const int had = s_ls.have_thermo, prev = s_ls.parity;
+    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, s_red);
+    if (had) run_reduce_thermo(d, a, prev);
+    if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
+        s_ls.bar_target = bs.target;
+        s_ls.parity = par;
+        s_ls.have_thermo = 1;
+    }
+    return bar_wait(d.ctl, bs, a.timeout_ns, where, &s_ls.ok);
 }
 
 __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
@@ -1294,6 +1321,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
         s_ls.have_thermo = 0;
         s_ls.rc = 0;
         s_ls.disp = (float)ctl->disp;
+        s_ls.dmax_bits = 0u;
     }
     __syncthreads();
     const float skin_eff = (float)a.skin_eff;
@@ -1321,14 +1349,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 run_s_pass<Real, UNI>(d, a);
                 if (!grid_barrier(ctl, a.timeout_ns, 10)) return;
                 const int par = (int)(s_ls.step & 1);
-                run_f_pass<Real, UNI>(d, a, F_STORE, s_ls.step, par);
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    s_ls.parity = par;
-                    s_ls.have_thermo = 1;
-                    s_ls.state = 0;
-                }
-                if (!grid_barrier(ctl, a.timeout_ns, 11)) return;
+                Acc<Real> acc;
+                run_f_pass<Real, UNI>(d, a, F_STORE, s_ls.step, acc);
+                if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
+                if (!f_barrier(d, a, acc, par, nullptr, 11)) return;
             }
         }
         if (s_ls.rc == 0 && s_ls.remaining > 0 && s_ls.state == 0) {
@@ -1341,7 +1365,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 s_ls.pc ^= 1;
                 s_ls.state = 2;
             }
-            if (!grid_barrier(ctl, a.timeout_ns, 13)) return;
+            if (!grid_barrier(ctl, a.timeout_ns, 13, &ctl->dmax2[stp & 1])) return;
             add_disp(ctl, stp);
         }
         while (s_ls.rc == 0 && s_ls.state == 2) {
@@ -1358,26 +1382,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 if (rc) break;
             }
             run_s_pass<Real, UNI>(d, a);
-            {
-                BarState bs;
-                bs.target = s_ls.bar_target;
-                bar_arrive(ctl, bs);
-                if (threadIdx.x == 0) s_ls.bar_target = bs.target;
-                if (s_ls.have_thermo) run_reduce_thermo(d, a, s_ls.parity);  // overlapped with the wait
-                if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return;
-            }
+            if (!grid_barrier(ctl, a.timeout_ns, 20)) return;
             const bool more = s_ls.remaining > 1;
             const int par = (int)((stp + 1) & 1);
-            run_f_pass<Real, UNI>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, par);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                s_ls.parity = par;
-                s_ls.have_thermo = 1;
+            Acc<Real> acc;
+            run_f_pass<Real, UNI>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, acc);
+            if (threadIdx.x == 0) {  // every thread read `remaining` before the pass's barriers
                 s_ls.step = stp + 1;
                 s_ls.remaining--;
                 s_ls.done++;
             }
-            if (!grid_barrier(ctl, a.timeout_ns, 21)) return;
+            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21)) return;
             if (more) {
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
                 add_disp(ctl, stp + 1);
@@ -1387,7 +1402,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
             }
         }
     }
-    if (s_ls.have_thermo) run_reduce_thermo(d, a, s_ls.parity);
+    if (s_ls.have_thermo) {
+        // the last pass's partials were written after its barrier's arrival
+        if (!grid_barrier(ctl, a.timeout_ns, 30)) return;
+        run_reduce_thermo(d, a, s_ls.parity);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->state = s_ls.state;
         ctl->pos_cur = s_ls.pc;
@@ -1398,7 +1417,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
         ctl->steps_done = s_ls.done;
         ctl->need_rebuild = s_ls.need_rb;
         if (s_ls.rebuilds > 0) ctl->list_grid = s_ls.rc == 0 ? (int)gridDim.x : -1;
-        if (s_ls.have_thermo) ctl->thermo[Q_SPARE0] = (double)s_ls.step;
     }
 }
 
