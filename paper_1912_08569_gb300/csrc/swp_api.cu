@@ -480,7 +480,7 @@ int swp_create(swp_ctx** out, int n, int n_types, const double box[3], int preci
         cudaGetLastError();
         return SWP_ERR_CUDA;
     }
-    c->max_blocks = c->num_sms * std::max(1, 2048 / kBlock);
+    c->max_blocks = std::min(kMaxGrid, c->num_sms * std::max(1, 2048 / kBlock));
     std::memset(&c->hctl, 0, sizeof(Ctl));
     if (derive_cells(c) != SWP_OK) {
         delete c;

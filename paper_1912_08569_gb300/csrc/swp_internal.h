@@ -12,6 +12,7 @@ constexpr int kMaxTypes = 8;       // type-pair table is kMaxTypes^2 entries at 
 constexpr int kNQ = 12;            // per-block thermo partials: see Q_* below
 constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
 constexpr int kBlock = 1024;       // threads per block of the step kernel (one block per SM)
+constexpr int kMaxGrid = 320;      // largest grid of the step kernel (blocks)
 constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays clear)
 
 // Thermo quantities, in the order of the per-block partials.

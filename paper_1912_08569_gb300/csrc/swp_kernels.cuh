@@ -310,6 +310,7 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
         *s_ok = ok;
     }
     __syncthreads();
+    if (*s_ok == 0) asm volatile("cp.async.wait_all;" ::: "memory");  // leave no copy in flight
     return *s_ok != 0;
 }
 
@@ -767,11 +768,13 @@ __device__ __forceinline__ void cp_async_r4(R4* smem, const R4* gmem)
 // ---------------------------------------------------------------------------
 // S pass (K-b1): S_i = sum over reactive partners k inside r_cut of a vh(r_ik).
 
-constexpr int kU = 1;  // entries per thread whose loads are in flight together
-
+// staged: the block has one sub-chunk and the shared copies of its positions
+// and list ranges are current (kept by the previous force pass), so they are
+// not loaded again.  With one sub-chunk the block's S values also stay in
+// shared memory for the force pass.
 template <typename Real, bool UNI>
 __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
-                             const PairP<Real>& ps)
+                             const PairP<Real>& ps, bool staged)
 {
     typedef Stage<Real> SM;
     typedef typename Dev<Real>::R4 R4;
@@ -779,52 +782,49 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
     int b0, b1;
     block_range(d, b0, b1);
     const int t = threadIdx.x;
+    const bool single = b1 - b0 <= (int)blockDim.x;
     for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
         const int P = min((int)blockDim.x, b1 - q0);
-        if (t < P) {
-            SM::pos()[t] = pos[q0 + t];
-            SM::info()[t] = d.pinfo[q0 + t];
+        if (!staged) {
+            if (t < P) {
+                SM::pos()[t] = pos[q0 + t];
+                SM::info()[t] = d.pinfo[q0 + t];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         const int e_beg = SM::info()[0].x;
         const int e_end = SM::info()[P - 1].x + SM::info()[P - 1].y;
         Real s = Real(0);
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
-            // batches of U entries per thread: their indices, then their gathers,
-            // are all in flight together
-            for (int e0 = wb + t; e0 < we; e0 += kU * (int)blockDim.x) {
-                int jj[kU], oo[kU];
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    jj[u] = e < we ? d.ent_j[e] : 0;
-                    oo[u] = e < we ? d.ent_o[e] : 0;
+            // the thread's entries e, e + B, ...: the next entry's indices are in
+            // flight while the current entry is evaluated
+            const int B = blockDim.x;
+            int e = wb + t;
+            int j_c = 0, o_c = 0;
+            if (e < we) {
+                j_c = d.ent_j[e];
+                o_c = d.ent_o[e];
+            }
+            while (e < we) {
+                const R4 p_c = pos[j_c];
+                int j_n = 0, o_n = 0;
+                if (e + B < we) {
+                    j_n = d.ent_j[e + B];
+                    o_n = d.ent_o[e + B];
                 }
-                R4 pj[kU];
-#pragma unroll
-                for (int u = 0; u < kU; u++)
-                    if (e0 + u * (int)blockDim.x < we) pj[u] = pos[jj[u]];
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    if (e >= we) break;
-                    const R4 pi = SM::pos()[oo[u]];
-                    const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj[u]), d.ntypes, ps);
-                    Real dx, dy, dz;
-                    const Real r2 = dist2_listed(pi, pj[u], d, dx, dy, dz);
-                    Real sv = Real(0);
-                    if (r2 < p.rc2) {
-                        Real vh = Real(1);
-                        if (r2 > p.rmin2) {
-                            Real v, f;
-                            lj_eval(p, r2, v, f);
-                            vh = (p.vshift - v) * p.inv_epshat;
-                        }
-                        sv = p.a * vh;
-                    }
-                    SM::w()[e - wb] = sv;
-                }
+                const R4 pi = SM::pos()[o_c];
+                const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(p_c), d.ntypes, ps);
+                Real dx, dy, dz;
+                const Real r2 = dist2_listed(pi, p_c, d, dx, dy, dz);
+                // selected, not branched (see entry_force)
+                Real v, f;
+                lj_eval(p, r2, v, f);
+                const Real vh = r2 > p.rmin2 ? (p.vshift - v) * p.inv_epshat : Real(1);
+                SM::w()[e - wb] = r2 < p.rc2 ? p.a * vh : Real(0);
+                e += B;
+                j_c = j_n;
+                o_c = o_n;
             }
             __syncthreads();
             if (t < P) {
@@ -836,7 +836,10 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
             }
             __syncthreads();
         }
-        if (t < P) d.S[q0 + t] = s;
+        if (t < P) {
+            d.S[q0 + t] = s;
+            if (single) SM::S()[t] = s;
+        }
     }
 }
 
@@ -900,7 +903,7 @@ template <typename Real>
 __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs& a, int pc,
                                                int ac, int i, Real fx, Real fy, Real fz,
                                                int flags, long long step, PState<Real>& st,
-                                               Real wbits, Real& kin)
+                                               Real wbits, Real& kin, typename Dev<Real>::R4* keep)
 {
     typedef typename Dev<Real>::R4 R4;
     R4 v = st.v;
@@ -937,6 +940,7 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         np.z = advance_fix(d, ac, i, 2, st.q[2], ddz);
         np.w = wbits;
         d.pos[pc ^ 1][i] = np;
+        if (keep) *keep = np;
     }
     d.vel[ac][i] = v;
     return disp2;
@@ -955,22 +959,22 @@ __device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real
 {
     Real dx, dy, dz;
     const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
-    fx = fy = fz = Real(0);
     const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj), d.ntypes, pu);
-    if (!(r2 < p.rc2)) return;
+    // evaluated for every listed pair and selected by the cut-off decision
+    // (no divergent branch: about half of the listed pairs lie in the skin)
+    const bool in = r2 < p.rc2;
     Real v, ft;
     lj_eval(p, r2, v, ft);
-    acc.q[Q_U2] += Real(0.5) * (v + p.ushift);
+    acc.q[Q_U2] += in ? Real(0.5) * (v + p.ushift) : Real(0);
     if (REACT) {
-        Real vh = Real(1);
-        if (r2 > p.rmin2) {
-            vh = (p.vshift - v) * p.inv_epshat;
-            const Real h = p.a * (Si + Sj - Real(2) * p.a * vh);
-            ft *= Real(1) - h * p.inv_epshat;
-        }
-        acc.q[Q_U3] += Real(0.5) * p.a * vh * (Si - p.a * vh);
-        if (r2 < p.rbond2) acc.q[Q_BONDS] += Real(0.5);
+        const bool beyond = r2 > p.rmin2;
+        const Real vh = beyond ? (p.vshift - v) * p.inv_epshat : Real(1);
+        const Real h = p.a * (Si + Sj - Real(2) * p.a * vh);
+        ft = beyond ? ft * (Real(1) - h * p.inv_epshat) : ft;
+        acc.q[Q_U3] += in ? Real(0.5) * p.a * vh * (Si - p.a * vh) : Real(0);
+        acc.q[Q_BONDS] += (in && r2 < p.rbond2) ? Real(0.5) : Real(0);
     }
+    ft = in ? ft : Real(0);
     fx = -ft * dx;
     fy = -ft * dy;
     fz = -ft * dz;
@@ -998,6 +1002,9 @@ __device__ __forceinline__ void sum_run(const R4* w, int wb, int k0, int k1, Rea
     }
 }
 
+// With one sub-chunk per block the S pass of the same step left the block's
+// positions, list ranges and S values in shared memory, and the integrator
+// keeps the shared positions current for the next S pass.
 template <typename Real, bool UNI>
 __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const RunArgs& a, int pc,
                               int ac, int flags, long long step, Acc<Real>& acc,
@@ -1010,6 +1017,7 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
     block_range(d, b0, b1);
     const int t = threadIdx.x;
     const int n = d.n;
+    const bool single = b1 - b0 <= (int)blockDim.x;
     float dmax = 0.0f;
     for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
         const int P = min((int)blockDim.x, b1 - q0);
@@ -1020,50 +1028,37 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             if (flags & F_OPENING)
                 for (int c = 0; c < 3; c++) cp_async(&SM::xq()[3 * t + c], &d.xq[ac][c * n + i], 8);
             cp_async_commit();
-            SM::pos()[t] = pos[i];
-            SM::S()[t] = d.S[i];
-            SM::info()[t] = d.pinfo[i];
         }
-        __syncthreads();
+        if (!single) {
+            if (t < P) {
+                const int i = q0 + t;
+                SM::pos()[t] = pos[i];
+                SM::S()[t] = d.S[i];
+                SM::info()[t] = d.pinfo[i];
+            }
+            __syncthreads();
+        }
         const int e_beg = SM::info()[0].x;
         const int e_rend = SM::info()[P - 1].x + SM::info()[P - 1].y;
         const int e_end = SM::info()[P - 1].z + SM::info()[P - 1].w;
         Real fx = 0, fy = 0, fz = 0;
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
-            for (int e0 = wb + t; e0 < we; e0 += kU * (int)blockDim.x) {
-                int jj[kU], oo[kU];
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    jj[u] = e < we ? d.ent_j[e] : 0;
-                    oo[u] = e < we ? d.ent_o[e] : 0;
-                }
-                R4 pj[kU];
-                Real sj[kU];
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    if (e < we) pj[u] = pos[jj[u]];
-                    sj[u] = e < e_rend ? d.S[jj[u]] : Real(0);
-                }
-#pragma unroll
-                for (int u = 0; u < kU; u++) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    if (e >= we) break;
-                    const int o = oo[u];
-                    Real ex, ey, ez;
-                    if (e < e_rend)
-                        entry_force<Real, UNI, true>(d, tab, SM::pos()[o], pj[u], SM::S()[o], sj[u], ps, acc, ex, ey, ez);
-                    else
-                        entry_force<Real, UNI, false>(d, tab, SM::pos()[o], pj[u], Real(0), Real(0), pw, acc, ex, ey, ez);
-                    R4 r;
-                    r.x = ex;
-                    r.y = ey;
-                    r.z = ez;
-                    r.w = Real(0);
-                    SM::w4()[e - wb] = r;
-                }
+            for (int e = wb + t; e < we; e += blockDim.x) {
+                const int j_c = d.ent_j[e], o_c = d.ent_o[e];
+                const R4 pj = pos[j_c];
+                const Real sj = e < e_rend ? d.S[j_c] : Real(0);
+                Real ex, ey, ez;
+                if (e < e_rend)
+                    entry_force<Real, UNI, true>(d, tab, SM::pos()[o_c], pj, SM::S()[o_c], sj, ps, acc, ex, ey, ez);
+                else
+                    entry_force<Real, UNI, false>(d, tab, SM::pos()[o_c], pj, Real(0), Real(0), pw, acc, ex, ey, ez);
+                R4 r;
+                r.x = ex;
+                r.y = ey;
+                r.z = ez;
+                r.w = Real(0);
+                SM::w4()[e - wb] = r;
             }
             __syncthreads();
             if (t < P) {
@@ -1096,7 +1091,8 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             st.v = SM::vel()[t];
             if (flags & F_OPENING)
                 for (int c = 0; c < 3; c++) st.q[c] = SM::xq()[3 * t + c];
-            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, SM::pos()[t].w, kin));
+            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, SM::pos()[t].w, kin,
+                                             single ? &SM::pos()[t] : (R4*)nullptr));
         }
         if (kPark)
 #pragma unroll
@@ -1118,7 +1114,7 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
     PState<Real> st;
     load_pstate(d, ac, i, F_OPENING, st);
     Real unused = Real(0);
-    return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, st, pi.w, unused);
+    return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, st, pi.w, unused, (R4*)nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1139,10 +1135,13 @@ struct LoopState {
     int state, pc, ac, need_rb, remaining, done, parity, have_thermo, rc, ok;
     float disp;
     unsigned dmax_bits;  // the block's largest squared step displacement (float bits)
+    int own_ok;          // shared positions and list ranges of the block's particles are current
+    int red_pending;     // a thermo reduction's copies are in flight into s_rbuf
 };
 
 static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
 static __shared__ double s_red[kNQ * 32];
+static __shared__ double s_rbuf[kMaxGrid];
 static __shared__ int s_int[64];
 static __shared__ LoopState s_ls;
 
@@ -1198,6 +1197,7 @@ __device__ int run_rebuild(const Dev<Real>& d, const RunArgs& a)
     if (threadIdx.x == 0) {
         s_ls.rebuilds++;
         s_ls.disp = 0.0f;
+        s_ls.own_ok = 0;  // the particles were reordered
     }
     __syncthreads();
     if (any_ovf) {
@@ -1207,10 +1207,19 @@ __device__ int run_rebuild(const Dev<Real>& d, const RunArgs& a)
     return 0;
 }
 
+// One sub-chunk per block: the block's particles fit one shared staging.
+template <typename Real>
+__device__ __forceinline__ bool single_chunk(const Dev<Real>& d)
+{
+    return (d.n + (int)gridDim.x - 1) / (int)gridDim.x <= (int)blockDim.x;
+}
+
 template <typename Real, bool UNI>
 __device__ __forceinline__ void run_s_pass(const Dev<Real>& d, const RunArgs& a)
 {
-    s_pass_block<Real, UNI>(d, stab<Real>(), s_ls.pc, uni_params(a, Real(0))[0]);
+    const bool single = single_chunk(d);
+    s_pass_block<Real, UNI>(d, stab<Real>(), s_ls.pc, uni_params(a, Real(0))[0], single && s_ls.own_ok);
+    if (threadIdx.x == 0) s_ls.own_ok = single;  // every thread read it before the pass's barriers
 }
 
 // Folds a thread's squared displacement into the block's shared maximum (one
@@ -1268,12 +1277,47 @@ __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
     __syncthreads();
 }
 
+// The same reduction in two halves, kept off the blocks' critical path: at a
+// force-pass barrier block q (< kNQA) starts asynchronous copies of quantity
+// q of every block's partials of the previous pass into s_rbuf; before it
+// arrives at the next S-pass barrier it waits for them (so nothing is still
+// reading the partials when the next force pass overwrites that buffer), and
+// while waiting at that barrier it sums them in a fixed order.
+template <typename Real>
+__device__ __forceinline__ void reduce_issue(const Dev<Real>& d, const RunArgs& a, int par)
+{
+    const int b = threadIdx.x;
+    if (b < (int)gridDim.x)
+        cp_async(&s_rbuf[b], d.partials + ((size_t)par * a.max_blocks + b) * kNQ + blockIdx.x, 8);
+    cp_async_commit();
+}
+
+template <typename Real>
+__device__ __forceinline__ void reduce_finish(const Dev<Real>& d)
+{
+    const int G = gridDim.x, nwp = (G + 31) / 32;
+    const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < nwp) {
+        double v = threadIdx.x < (unsigned)G ? s_rbuf[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lw == 0) s_red[w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < nwp; k++) t += s_red[k];
+        d.ctl->thermo[blockIdx.x] = t;
+        s_ls.red_pending = 0;
+    }
+}
+
 // The barrier that ends a force pass.  After arriving (and publishing the
 // block's displacement maximum when the pass drifted), while the other blocks
 // finish, the block sums its thermo accumulators of this pass into its
-// partials, and the blocks that own a quantity reduce the previous pass's
-// partials: every block wrote those before arriving at the barrier that
-// followed that pass, which this block has passed.
+// partials, and the blocks that own a quantity start the reduction of the
+// previous pass's partials: every block wrote those before arriving at the
+// barrier that followed that pass, which this block has passed.
 template <typename Real>
 __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, const Acc<Real>& acc,
                                           int par, unsigned* pub_dst, int where)
@@ -1283,11 +1327,13 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     bar_arrive(d.ctl, bs, pub_dst, &s_ls.dmax_bits);
     const int had = s_ls.have_thermo, prev = s_ls.parity;
     block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, s_red);
-    if (had) run_reduce_thermo(d, a, prev);
+    const bool red = had && blockIdx.x < kNQA;
+    if (red) reduce_issue(d, a, prev);
     if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
         s_ls.bar_target = bs.target;
         s_ls.parity = par;
         s_ls.have_thermo = 1;
+        if (red) s_ls.red_pending = 1;
     }
     return bar_wait(d.ctl, bs, a.timeout_ns, where, &s_ls.ok);
 }
@@ -1322,6 +1368,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
         s_ls.rc = 0;
         s_ls.disp = (float)ctl->disp;
         s_ls.dmax_bits = 0u;
+        s_ls.own_ok = 0;
+        s_ls.red_pending = 0;
     }
     __syncthreads();
     const float skin_eff = (float)a.skin_eff;
@@ -1364,6 +1412,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
             if (threadIdx.x == 0) {
                 s_ls.pc ^= 1;
                 s_ls.state = 2;
+                s_ls.own_ok = 0;  // new positions in global memory only
             }
             if (!grid_barrier(ctl, a.timeout_ns, 13, &ctl->dmax2[stp & 1])) return;
             add_disp(ctl, stp);
@@ -1381,9 +1430,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 __syncthreads();
                 if (rc) break;
             }
-            run_s_pass<Real, UNI>(d, a);
-            if (!grid_barrier(ctl, a.timeout_ns, 20)) return;
             const bool more = s_ls.remaining > 1;
+            run_s_pass<Real, UNI>(d, a);
+            const bool fin = s_ls.red_pending;
+            if (fin) cp_async_wait_all();
+            {
+                BarState bs;
+                bs.target = s_ls.bar_target;
+                bar_arrive(ctl, bs);
+                if (fin) reduce_finish(d);
+                if (threadIdx.x == 0) s_ls.bar_target = bs.target;
+                if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return;
+            }
             const int par = (int)((stp + 1) & 1);
             Acc<Real> acc;
             run_f_pass<Real, UNI>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, acc);
@@ -1402,6 +1460,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
             }
         }
     }
+    cp_async_wait_all();  // a reduction started at the last barrier is not needed
     if (s_ls.have_thermo) {
         // the last pass's partials were written after its barrier's arrival
         if (!grid_barrier(ctl, a.timeout_ns, 30)) return;
