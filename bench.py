@@ -45,12 +45,17 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--lam", type=float, default=1.0)
-    ap.add_argument("--md-steps", type=int, default=1000)
+    ap.add_argument("--md-steps", type=int, default=None,
+                    help="time steps per launch (default 1000; 5000 for batch256)")
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="mix100k", choices=["mix100k", "batch256"],
+                    help="mix100k: the single 100k-particle system (default); batch256: 256 "
+                         "independent systems of 1k-32k particles in one launch per step")
+    ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
 
 
@@ -375,10 +380,142 @@ def run_ours(a):
     return 0
 
 
+BATCH_METRIC = "batched swap-potential particle-timesteps/s (independent systems, one launch)"
+
+
+def run_batch(a):
+    """Batched form: a.systems independent systems (sizes log-uniform 1k-32k,
+    density 0.2-0.6, lambda in {0, 0.5, 1, 2, 5}, kT in [0.03, 0.2]) advanced
+    a.md_steps steps per launch; one bench step = one launch."""
+    import torch
+
+    from paper_1912_08569_gb300 import SwapBatch, SwapSystem
+    from paper_1912_08569_gb300 import _abi as A
+    from paper_1912_08569_gb300 import inputs
+    from paper_1912_08569_gb300.build import build
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    wls = inputs.batch_workload(a.systems, seed=7 + rank)
+    systems = []
+    for wl in wls:
+        s = SwapSystem(wl["n"], 2, wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"])
+        s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
+        systems.append(s)
+    kT = [wl["kT"] for wl in wls]
+    dt, gamma = 0.001, 1.0
+    batch = SwapBatch(systems)
+    for s in systems:
+        s.compute_forces()
+    nn = np.array([float(s.nlist()[1][:, 1].mean()) for s in systems])
+    nn_r = np.array([float(s.nlist()[1][:, 0].mean()) for s in systems])
+    ns = np.array([wl["n"] for wl in wls], dtype=np.float64)
+    tune = batch.autotune(200, dt, kT, gamma)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(a.warmup):
+        batch.run(a.md_steps, dt, kT, gamma)
+    reb0 = np.array([s.thermo()["n_rebuilds"] for s in systems])
+    stream = systems[0].stream
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.run(a.md_steps, dt, kT, gamma, sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    batch.sync()
+    clk = clocks.stop() if clocks else None
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    t = torch.tensor([float(np.sum(launch_ms))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    n_total = float(ns.sum())
+    value = world * n_total * a.md_steps * a.steps / (total_ms / 1e3)
+    reb = (np.array([s.thermo()["n_rebuilds"] for s in systems]) - reb0) / a.steps
+    peak, peak_kind = _peaks()
+    b_alg = float(np.sum([algorithmic_bytes(n, a.md_steps, x, y, r) for n, x, y, r in zip(ns, nn, nn_r, reb)]))
+    achieved = b_alg / (float(np.mean(launch_ms)) / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind, "alg_bytes_per_launch": b_alg}
+    e2e = None
+    if not a.no_e2e:
+        pins = [(torch.from_numpy(np.ascontiguousarray(wl["x"])).pin_memory(),
+                 torch.from_numpy(np.ascontiguousarray(wl["v"])).pin_memory(),
+                 torch.from_numpy(np.ascontiguousarray(wl["types"], dtype=np.int32)).pin_memory(),
+                 torch.from_numpy(np.ascontiguousarray(wl["mass"])).pin_memory()) for wl in wls]
+        h2d = int(sum(x.numel() * 8 + v.numel() * 8 + ty.numel() * 4 + m.numel() * 8 for x, v, ty, m in pins))
+        times = []
+        for k in range(a.warmup + a.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s, (x, v, ty, m) in zip(systems, pins):
+                A.swp_set_state(s.ctx, x, v, ty, m, None, A.SWP_HOST)
+            batch.run(a.md_steps, dt, kT, gamma, sync=False)
+            for s in systems:
+                A.swp_read_thermo(s.ctx)
+            if k >= a.warmup:
+                times.append(time.perf_counter() - t0)
+        e2e = {"value": world * n_total * a.md_steps * a.steps / float(np.sum(times)), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": CTL_BYTES * len(systems)}
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        k = int(np.argsort(ns)[len(ns) // 2])  # the median-size system
+        v, steps_done, el = cpu_oracle_sample(wls[k], a.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"system {k} (N={int(ns[k])}), {steps_done} BAOAB steps of the FP64 C oracle, "
+                         f"{el:.1f} s, 1 thread"}
+    if rank == 0:
+        out = {"metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"batch{len(wls)}: {len(wls)} systems, N log-uniform 1k-32k "
+                                      f"(total {int(n_total)}), density 0.2-0.6, lambda in {{0,0.5,1,2,5}}, "
+                                      f"kT 0.03-0.2, BAOAB gamma=1 dt=0.001, skin 0.3",
+                          "systems": len(wls), "particles": int(n_total), "md_steps_per_step": a.md_steps,
+                          "split": tune[1], "l2": "flushed (512 MB write) between timed launches",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps, "clocks": clk,
+               "kernel_digest": _kernel_digest()}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     a = _args()
+    if a.md_steps is None:
+        a.md_steps = 5000 if a.workload == "batch256" else 1000
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batch256":
+        return run_batch(a)
     return run_ours(a)
 
 

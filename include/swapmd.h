@@ -171,6 +171,32 @@ SWP_API int swp_step_nve(swp_ctx* ctx, double dt, int nsteps);
  * re-bind a larger list and call again for the remaining steps. */
 SWP_API int swp_step_nvt(swp_ctx* ctx, double dt, double kT, double gamma, int nsteps);
 
+/* Batched dynamics: advance n_systems independent systems nsteps time steps
+ * each in ONE cooperative launch (the per-system step of swp_step_nvt, with
+ * dt[r], kT[r], gamma[r] for system r; gamma[r] = 0 is velocity Verlet).  The
+ * systems may differ in size, box, coefficients and temperature.  They must
+ * share precision, device and bound stream, each must have its workspace,
+ * list buffer and state, and none may appear twice; empty systems are
+ * skipped.
+ *
+ * Work split: with w the particle count of a system and T the mean count per
+ * block of the launch, a system with w > split * T gets max(1, round(w / T))
+ * blocks of its own (its device-side barriers span only those blocks); the
+ * others run on one block each, packed heaviest first onto the least-loaded
+ * block, a block advancing its systems one after the other.  split > 0
+ * (1.0 is a good default; tune it by timing).
+ *
+ * ws: device scratch of at least swp_batch_workspace_size(n_systems) bytes,
+ * owned by the caller and used until the launch completes.  Enqueued on the
+ * shared stream; errors of system r (timeout, list overflow) are latched in
+ * system r and reported by swp_sync(ctx[r]): on SWP_ERR_NLIST_OVERFLOW that
+ * system completed thermo.steps_done steps (the others are unaffected).
+ * Errors: SWP_ERR_INVALID (bad arguments, mixed precision/device/stream, ws
+ * too small, more large systems than blocks), SWP_ERR_STATE, SWP_ERR_CUDA. */
+SWP_API size_t swp_batch_workspace_size(int n_systems);
+SWP_API int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const double* kT,
+                           const double* gamma, int nsteps, double split, void* ws, size_t ws_bytes);
+
 /* Wait for the stream and report latched device errors. */
 SWP_API int swp_sync(swp_ctx* ctx);
 

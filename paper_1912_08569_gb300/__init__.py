@@ -11,10 +11,14 @@ using a ``SwapSystem`` without the built library raises.
 """
 from . import _abi  # noqa: F401
 
-__all__ = ["SwapSystem", "build"]
+__all__ = ["SwapSystem", "SwapBatch", "build"]
 
 
 def __getattr__(name):
+    if name == "SwapBatch":
+        from .system import SwapBatch
+
+        return SwapBatch
     if name == "SwapSystem":
         from .system import SwapSystem
 

@@ -46,6 +46,7 @@ EXPORTS = (
     "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
+    "swp_batch_workspace_size", "swp_batch_step",
 )
 
 
@@ -110,6 +111,9 @@ def load_library(path: str = LIB_PATH):
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
         "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+        "swp_batch_workspace_size": ([c_int], c_size_t),
+        "swp_batch_step": ([P(c_void_p), c_int, P(c_double), P(c_double), P(c_double), c_int, c_double,
+                            c_void_p, c_size_t], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -254,6 +258,20 @@ def swp_compute_forces_static(ctx, x_dev, type_dev, f_dev, thermo_dev=None, stre
                                                                 _ptr(f_dev), _ptr(thermo_dev),
                                                                 ctypes.c_void_p(stream)),
                   "swp_compute_forces_static")
+
+
+def swp_batch_workspace_size(n_systems: int) -> int:
+    return int(load_library().swp_batch_workspace_size(int(n_systems)))
+
+
+def swp_batch_step(ctxs, dt, kT, gamma, nsteps: int, split: float, ws_ptr: int, ws_bytes: int):
+    """One launch advancing every context in ctxs nsteps steps (per-system dt, kT, gamma)."""
+    m = len(ctxs)
+    arr = (ctypes.c_void_p * m)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    f = lambda v: (ctypes.c_double * m)(*[float(x) for x in v])
+    rc = load_library().swp_batch_step(arr, m, f(dt), f(kT), f(gamma), int(nsteps), float(split),
+                                       ctypes.c_void_p(ws_ptr), int(ws_bytes))
+    return _check(ctxs[0] if m else None, rc, "swp_batch_step")
 
 
 def swp_destroy(ctx):

@@ -395,18 +395,12 @@ void uniform_pairs(const swp_ctx* c, RunArgs* a)
     a->uni_other = ot < 0 ? 0 : ot;
 }
 
+// Fills the system-dependent run arguments (table upload included).
 template <typename Real>
-int run(swp_ctx* c, RunArgs a)
+int prepare_args(swp_ctx* c, RunArgs& a)
 {
-    Dev<Real>& d = dev<Real>(c);
     int rc = upload_table(c);
     if (rc) return rc;
-    int bps = 0;
-    SWP_CUDA(c, run_occupancy<Real>(kBlock, &bps));
-    if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
-    if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
-    bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
-    c->grid = c->num_sms * bps;
     a.max_blocks = c->max_blocks;
     a.timeout_ns = c->timeout_ns;
     double margin = 0.0;
@@ -423,6 +417,21 @@ int run(swp_ctx* c, RunArgs a)
         u[0] = t[a.uni_swap];
         u[1] = t[a.uni_other];
     }
+    return SWP_OK;
+}
+
+template <typename Real>
+int run(swp_ctx* c, RunArgs a)
+{
+    Dev<Real>& d = dev<Real>(c);
+    int bps = 0;
+    SWP_CUDA(c, run_occupancy<Real>(kBlock, &bps));
+    if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
+    if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
+    bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
+    c->grid = c->num_sms * bps;
+    int rc = prepare_args<Real>(c, a);
+    if (rc) return rc;
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
     SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
     return SWP_OK;
@@ -449,6 +458,138 @@ cudaMemcpyKind kind_to_dev(int where)
 cudaMemcpyKind kind_from_dev(int where)
 {
     return where == SWP_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// ---------------------------------------------------------------------------
+// Batched runs: m systems advanced by one cooperative launch of B blocks.
+//
+// Plan: with the work of a system taken as its particle count w and the mean
+// per block T = sum(w) / B, a system heavier than split * T gets a group of
+// max(1, round(w / T)) blocks of its own; the others are packed, heaviest
+// first, onto the block with the least work so far (longest-processing-time
+// rule), each running on one block.  Blocks left over when there is nothing
+// to pack go to the groups with the most work per block.
+
+struct BatchPlan {
+    std::vector<int> item_ofs;  // [B + 1]
+    std::vector<int4> items;    // (system, rank, group size, 0)
+};
+
+int plan_batch(const std::vector<long long>& w, int B, double split, BatchPlan& plan)
+{
+    const int m = (int)w.size();
+    long long W = 0;
+    for (long long x : w) W += std::max(x, 1LL);
+    const double T = (double)W / B;
+    std::vector<int> g(m, 0);
+    int used = 0;
+    std::vector<int> order(m);
+    for (int r = 0; r < m; r++) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+    for (int r : order)
+        if ((double)w[r] > split * T) {
+            g[r] = std::max(1, (int)std::llround((double)w[r] / T));
+            used += g[r];
+        }
+    bool small = false;
+    for (int r = 0; r < m; r++) small |= g[r] == 0;
+    const int need = small ? 1 : 0;
+    // too many dedicated blocks: take them back from the groups with the least work per block
+    while (used > B - need) {
+        int best = -1;
+        for (int r = 0; r < m; r++)
+            if (g[r] > 1 && (best < 0 || (double)w[r] / g[r] < (double)w[best] / g[best])) best = r;
+        if (best < 0) break;
+        g[best]--;
+        used--;
+    }
+    if (used > B - need) return -1;  // more heavy systems than blocks
+    // nothing to pack: spread the spare blocks over the groups
+    if (!small)
+        while (used < B) {
+            int best = -1;
+            for (int r = 0; r < m; r++)
+                if (g[r] > 0 && g[r] < kMaxGrid && (best < 0 || (double)w[r] / g[r] > (double)w[best] / g[best]))
+                    best = r;
+            if (best < 0) break;
+            g[best]++;
+            used++;
+        }
+    std::vector<std::vector<int4>> per(B);
+    int b = 0;
+    for (int r : order)
+        if (g[r] > 0) {
+            for (int k = 0; k < g[r]; k++) per[b + k].push_back(make_int4(r, k, g[r], 0));
+            b += g[r];
+        }
+    const int first_free = b;
+    std::vector<double> load(B, 0.0);
+    for (int r : order)
+        if (g[r] == 0) {
+            int best = first_free;
+            for (int k = first_free; k < B; k++)
+                if (load[k] < load[best]) best = k;
+            per[best].push_back(make_int4(r, 0, 1, 0));
+            load[best] += (double)std::max(w[r], 1LL);
+        }
+    plan.item_ofs.assign(B + 1, 0);
+    plan.items.clear();
+    for (int k = 0; k < B; k++) {
+        plan.item_ofs[k] = (int)plan.items.size();
+        for (const int4& it : per[k]) plan.items.push_back(it);
+    }
+    plan.item_ofs[B] = (int)plan.items.size();
+    return 0;
+}
+
+size_t batch_bytes(int m, size_t dev_size)
+{
+    return align256(dev_size * m) + align256(sizeof(RunArgs) * m) + align256(sizeof(int) * (kMaxGrid + 1)) +
+           align256(sizeof(int4) * (m + kMaxGrid));
+}
+
+template <typename Real>
+int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunArgs>& args, double split,
+              void* ws, size_t ws_bytes)
+{
+    swp_ctx* c0 = cs[idx[0]];
+    const int m = (int)idx.size();
+    int bps = 0;
+    SWP_CUDA(c0, batch_occupancy<Real>(&bps));
+    if (bps < 1) return fail(c0, SWP_ERR_CUDA, "batched step kernel does not fit on an SM");
+    const int B = std::min(kMaxGrid, c0->num_sms * std::min(bps, 2048 / kBlock));
+    if (ws_bytes < batch_bytes(m, sizeof(Dev<Real>))) return fail(c0, SWP_ERR_INVALID, "batch workspace too small");
+    std::vector<long long> w(m);
+    for (int r = 0; r < m; r++) w[r] = cs[idx[r]]->n;
+    BatchPlan plan;
+    if (plan_batch(w, B, split, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
+    std::vector<Dev<Real>> devs(m);
+    int uni = 1;
+    for (int r = 0; r < m; r++) {
+        swp_ctx* c = cs[idx[r]];
+        int rc = prepare_args<Real>(c, args[r]);
+        if (rc) return rc;
+        uni &= args[r].uni;
+        devs[r] = dev<Real>(c);
+        SWP_CUDA(c0, cudaMemsetAsync(&devs[r].ctl->barrier, 0, sizeof(unsigned long long), c0->stream));
+    }
+    for (int k = 0; k < B; k++)
+        for (int it = plan.item_ofs[k]; it < plan.item_ofs[k + 1]; it++)
+            cs[idx[plan.items[it].x]]->grid = plan.items[it].z;
+    char* base = (char*)ws;
+    Dev<Real>* d_dev = (Dev<Real>*)base;
+    RunArgs* d_args = (RunArgs*)(base + align256(sizeof(Dev<Real>) * m));
+    int* d_ofs = (int*)((char*)d_args + align256(sizeof(RunArgs) * m));
+    int4* d_items = (int4*)((char*)d_ofs + align256(sizeof(int) * (kMaxGrid + 1)));
+    // pageable host sources: each copy has read its source when the call returns
+    SWP_CUDA(c0, cudaMemcpyAsync(d_dev, devs.data(), sizeof(Dev<Real>) * m, cudaMemcpyHostToDevice, c0->stream));
+    SWP_CUDA(c0, cudaMemcpyAsync(d_args, args.data(), sizeof(RunArgs) * m, cudaMemcpyHostToDevice, c0->stream));
+    SWP_CUDA(c0, cudaMemcpyAsync(d_ofs, plan.item_ofs.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice,
+                                 c0->stream));
+    SWP_CUDA(c0, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(int4) * plan.items.size(),
+                                 cudaMemcpyHostToDevice, c0->stream));
+    SWP_CUDA(c0, launch_batch<Real>(d_dev, d_args, d_ofs, d_items, uni, B, c0->stream));
+    return SWP_OK;
 }
 
 }  // namespace
@@ -722,14 +863,15 @@ int swp_compute_forces(swp_ctx* c)
     return run_any(c, a);
 }
 
-static int step_common(swp_ctx* c, double dt, double kT, double gamma, int nsteps)
+static bool step_params_ok(double dt, double kT, double gamma, int nsteps)
 {
-    int rc = ready(c, true);
-    if (rc) return rc;
-    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !(gamma >= 0.0) || !(kT >= 0.0) ||
-        !std::isfinite(gamma) || !std::isfinite(kT))
-        return fail(c, SWP_ERR_INVALID, "need dt > 0, nsteps >= 0, gamma >= 0, kT >= 0");
-    if (c->n == 0 || nsteps == 0) return SWP_OK;
+    return dt > 0.0 && std::isfinite(dt) && nsteps >= 0 && gamma >= 0.0 && kT >= 0.0 &&
+           std::isfinite(gamma) && std::isfinite(kT);
+}
+
+// Integrator constants of a run (BAOAB when gamma > 0, else velocity Verlet).
+static RunArgs step_args(double dt, double kT, double gamma, int nsteps)
+{
     RunArgs a;
     std::memset(&a, 0, sizeof(a));
     a.nsteps = nsteps;
@@ -743,7 +885,17 @@ static int step_common(swp_ctx* c, double dt, double kT, double gamma, int nstep
     a.hdt_f = (float)a.hdt_d;
     a.c1_f = (float)a.c1;
     a.c2_f = (float)a.c2;
-    return run_any(c, a);
+    return a;
+}
+
+static int step_common(swp_ctx* c, double dt, double kT, double gamma, int nsteps)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (!step_params_ok(dt, kT, gamma, nsteps))
+        return fail(c, SWP_ERR_INVALID, "need dt > 0, nsteps >= 0, gamma >= 0, kT >= 0");
+    if (c->n == 0 || nsteps == 0) return SWP_OK;
+    return run_any(c, step_args(dt, kT, gamma, nsteps));
 }
 
 int swp_step_nve(swp_ctx* c, double dt, int nsteps) { return step_common(c, dt, 0.0, 0.0, nsteps); }
@@ -751,6 +903,41 @@ int swp_step_nve(swp_ctx* c, double dt, int nsteps) { return step_common(c, dt, 
 int swp_step_nvt(swp_ctx* c, double dt, double kT, double gamma, int nsteps)
 {
     return step_common(c, dt, kT, gamma, nsteps);
+}
+
+size_t swp_batch_workspace_size(int n_systems)
+{
+    if (n_systems < 1) return 0;
+    return batch_bytes(n_systems, std::max(sizeof(Dev<float>), sizeof(Dev<double>)));
+}
+
+int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const double* kT,
+                   const double* gamma, int nsteps, double split, void* ws, size_t ws_bytes)
+{
+    if (!ctx || n_systems < 1 || !dt || !kT || !gamma || !ws || nsteps < 0 || !(split > 0.0))
+        return SWP_ERR_INVALID;
+    for (int r = 0; r < n_systems; r++)
+        if (!ctx[r]) return SWP_ERR_INVALID;
+    swp_ctx* c0 = ctx[0];
+    std::vector<int> idx;
+    std::vector<RunArgs> args;
+    for (int r = 0; r < n_systems; r++) {
+        swp_ctx* c = ctx[r];
+        int rc = ready(c, true);
+        if (rc) return rc;
+        if (c->precision != c0->precision || c->device != c0->device || c->stream != c0->stream)
+            return fail(c0, SWP_ERR_INVALID, "batched systems need one precision, device and stream");
+        if (!step_params_ok(dt[r], kT[r], gamma[r], nsteps))
+            return fail(c, SWP_ERR_INVALID, "need dt > 0, nsteps >= 0, gamma >= 0, kT >= 0");
+        for (int q = 0; q < r; q++)
+            if (ctx[q] == c) return fail(c0, SWP_ERR_INVALID, "a system appears twice in the batch");
+        if (c->n == 0) continue;
+        idx.push_back(r);
+        args.push_back(step_args(dt[r], kT[r], gamma[r], nsteps));
+    }
+    if (idx.empty() || nsteps == 0) return SWP_OK;
+    return c0->precision == SWP_FP64 ? batch_run<double>(ctx, idx, args, split, ws, ws_bytes)
+                                     : batch_run<float>(ctx, idx, args, split, ws, ws_bytes);
 }
 
 int swp_sync(swp_ctx* c)

@@ -153,6 +153,14 @@ template <typename Real>
 cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, cudaStream_t s);
 template <typename Real>
 cudaError_t run_occupancy(int block, int* blocks_per_sm);
+// Batched launch (k_batch): per-system device structures and run arguments in
+// device memory; block b runs items[item_ofs[b] .. item_ofs[b + 1]), each
+// (system, rank in its group, group size, unused).
+template <typename Real>
+cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
+                         int uni, int grid, cudaStream_t s);
+template <typename Real>
+cudaError_t batch_occupancy(int* blocks_per_sm);
 template <typename Real>
 cudaError_t launch_set_state(const Dev<Real>& d, cudaStream_t s);
 template <typename Real>

@@ -14,11 +14,41 @@
 // pass forms S, the next forms every pair force from S_i and S_j.  Beyond
 // r_min, vh' = -v'/eps_hat, so the total force of a reactive pair is the
 // two-body force times (1 - dU3/dvh_ij / eps_hat).
-#pragma once
+//
+// This file is compiled twice (see swp_launch.cuh): with SWP_BATCHED 0 into
+// namespace swp::single (the single-system step kernel and the exchange
+// kernels) and with SWP_BATCHED 1 into swp::batched (the batched kernel), so
+// that the code a group of one block or a group of fewer blocks than
+// thermo quantities needs costs the single-system kernel nothing.
 
 #include "swp_internal.h"
 
+#ifndef SWP_BATCHED
+#error "define SWP_BATCHED (0 or 1) before including swp_kernels.cuh"
+#endif
+
 namespace swp {
+#if SWP_BATCHED
+namespace batched {
+#else
+namespace single {
+#endif
+
+constexpr bool kBatched = SWP_BATCHED != 0;
+
+// ---------------------------------------------------------------------------
+// Group of blocks that advances one system: the whole grid for a single
+// system; in a batched launch, the blocks given to that system (possibly one).
+// Every phase partitions its work over the group, and grid barriers are
+// barriers over the group.
+#if SWP_BATCHED
+static __shared__ int s_grp[2];  // [0] this block's rank in the group, [1] group size
+__device__ __forceinline__ int g_rank() { return s_grp[0]; }
+__device__ __forceinline__ int g_size() { return s_grp[1]; }
+#else
+__device__ __forceinline__ int g_rank() { return blockIdx.x; }
+__device__ __forceinline__ int g_size() { return gridDim.x; }
+#endif
 
 // ---------------------------------------------------------------------------
 // Small helpers
@@ -263,7 +293,7 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 
 // Arrival: the block's writes are ordered before a release add on the
 // counter (after the block-wide __syncthreads, thread 0's release is
-// cumulative over them).  Generation g completes at count g * gridDim.x.
+// cumulative over them).  Generation g completes at count g * (group size).
 // With pub_dst set, thread 0 first folds the block's shared maximum *pub_src
 // into the global maximum *pub_dst (and clears it), so the other blocks see
 // it after their wait.
@@ -277,7 +307,8 @@ __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_
             if (m) atomicMax(pub_dst, m);
             *pub_src = 0u;
         }
-        b.target += gridDim.x;
+        if (kBatched && g_size() == 1) return;  // a group of one block: __syncthreads is the barrier
+        b.target += g_size();
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
     }
 }
@@ -287,6 +318,10 @@ __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_
 __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long timeout_ns,
                                          int where, int* s_ok)
 {
+    if (kBatched && g_size() == 1) {
+        __syncthreads();
+        return true;
+    }
     if (threadIdx.x == 0) {
         int ok = 1;
         int spins = 0;
@@ -445,21 +480,21 @@ __device__ __forceinline__ int block_sum_int(int v, int* sh)
 template <typename Real>
 __device__ void ph_chunk_sums(const Dev<Real>& d, int* sh)
 {
-    const int ch = (d.ncell + gridDim.x - 1) / gridDim.x;
-    const int beg = min((int)blockIdx.x * ch, d.ncell), end = min(beg + ch, d.ncell);
+    const int ch = (d.ncell + g_size() - 1) / g_size();
+    const int beg = min(g_rank() * ch, d.ncell), end = min(beg + ch, d.ncell);
     int v = 0;
     for (int c = beg + threadIdx.x; c < end; c += blockDim.x) v += d.cell_cnt[c];
     int t = block_sum_int(v, sh);
-    if (threadIdx.x == 0) d.bsum[blockIdx.x] = t;
+    if (threadIdx.x == 0) d.bsum[g_rank()] = t;
 }
 
 template <typename Real>
 __device__ void ph_chunk_scan(const Dev<Real>& d, int* sh)
 {
-    const int ch = (d.ncell + gridDim.x - 1) / gridDim.x;
-    const int beg = min((int)blockIdx.x * ch, d.ncell), end = min(beg + ch, d.ncell);
+    const int ch = (d.ncell + g_size() - 1) / g_size();
+    const int beg = min(g_rank() * ch, d.ncell), end = min(beg + ch, d.ncell);
     int v = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) v += d.bsum[b];
+    for (int b = threadIdx.x; b < g_rank(); b += blockDim.x) v += d.bsum[b];
     int base = block_sum_int(v, sh);
     // scan the chunk in pieces of blockDim.x cells
     for (int c0 = beg; c0 < end; c0 += blockDim.x) {
@@ -542,8 +577,8 @@ __device__ void ph_gather(const Dev<Real>& d, int pc, int ac, int t, int nt)
 template <typename Real>
 __device__ __forceinline__ void block_range(const Dev<Real>& d, int& b0, int& b1)
 {
-    const int Pb = (d.n + (int)gridDim.x - 1) / (int)gridDim.x;
-    b0 = min((int)blockIdx.x * Pb, d.n);
+    const int Pb = (d.n + g_size() - 1) / g_size();
+    b0 = min(g_rank() * Pb, d.n);
     b1 = min(b0 + Pb, d.n);
 }
 
@@ -574,8 +609,8 @@ __device__ int ph_build_cells(const Dev<Real>& d, const PairP<Real>* tab, int pc
     const unsigned lt = (1u << lane) - 1u;
     int b0, b1;
     block_range(d, b0, b1);
-    const int Pb = (d.n + (int)gridDim.x - 1) / (int)gridDim.x;
-    const long long cap_beg = (long long)blockIdx.x * Pb * d.max_nn;
+    const int Pb = (d.n + g_size() - 1) / g_size();
+    const long long cap_beg = (long long)g_rank() * Pb * d.max_nn;
     const long long cap_end = cap_beg + (long long)Pb * d.max_nn;
     long long base = cap_beg;
     for (int q0 = b0; q0 < b1; q0 += blockDim.x) {
@@ -1163,8 +1198,8 @@ template <typename Real>
 __device__ int run_rebuild(const Dev<Real>& d, const RunArgs& a)
 {
     Ctl* ctl = d.ctl;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gn = gridDim.x * blockDim.x;
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int gt = g_rank() * blockDim.x + threadIdx.x, gn = g_size() * blockDim.x;
+    if (threadIdx.x == 0 && g_rank() == 0) {
         ctl->max_row = 0;
         ctl->overflow = 0;
     }
@@ -1211,7 +1246,7 @@ __device__ int run_rebuild(const Dev<Real>& d, const RunArgs& a)
 template <typename Real>
 __device__ __forceinline__ bool single_chunk(const Dev<Real>& d)
 {
-    return (d.n + (int)gridDim.x - 1) / (int)gridDim.x <= (int)blockDim.x;
+    return (d.n + g_size() - 1) / g_size() <= (int)blockDim.x;
 }
 
 template <typename Real, bool UNI>
@@ -1247,7 +1282,7 @@ __device__ void run_open_pass(const Dev<Real>& d, const RunArgs& a, long long st
 {
     float dmax = 0.0f;
     const int pc = s_ls.pc, ac = s_ls.ac;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x)
+    for (int i = g_rank() * blockDim.x + threadIdx.x; i < d.n; i += g_size() * blockDim.x)
         dmax = fmaxf(dmax, open_from_stored(d, a, pc, ac, i, stp));
     warp_max_disp(dmax);
 }
@@ -1257,24 +1292,25 @@ __device__ void run_open_pass(const Dev<Real>& d, const RunArgs& a, long long st
 template <typename Real>
 __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
 {
-    if (blockIdx.x >= kNQA) return;
-    const int G = gridDim.x, nwp = (G + 31) / 32;
+    const int G = g_size(), nwp = (G + 31) / 32;
     const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w < nwp) {
-        const double* src = d.partials + (size_t)par * a.max_blocks * kNQ + blockIdx.x;
-        const int b = threadIdx.x;
-        double v = b < G ? src[(size_t)b * kNQ] : 0.0;
+    for (int q = g_rank(); q < kNQA; q += G) {  // block-uniform loop
+        if (w < nwp) {
+            const double* src = d.partials + (size_t)par * a.max_blocks * kNQ + q;
+            const int b = threadIdx.x;
+            double v = b < G ? src[(size_t)b * kNQ] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lw == 0) s_red[w] = v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lw == 0) s_red[w] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < nwp; k++) t += s_red[k];
+            d.ctl->thermo[q] = t;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < nwp; k++) t += s_red[k];
-        d.ctl->thermo[blockIdx.x] = t;
-    }
-    __syncthreads();
 }
 
 // The same reduction in two halves, kept off the blocks' critical path: at a
@@ -1287,15 +1323,15 @@ template <typename Real>
 __device__ __forceinline__ void reduce_issue(const Dev<Real>& d, const RunArgs& a, int par)
 {
     const int b = threadIdx.x;
-    if (b < (int)gridDim.x)
-        cp_async(&s_rbuf[b], d.partials + ((size_t)par * a.max_blocks + b) * kNQ + blockIdx.x, 8);
+    if (b < g_size())
+        cp_async(&s_rbuf[b], d.partials + ((size_t)par * a.max_blocks + b) * kNQ + g_rank(), 8);
     cp_async_commit();
 }
 
 template <typename Real>
 __device__ __forceinline__ void reduce_finish(const Dev<Real>& d)
 {
-    const int G = gridDim.x, nwp = (G + 31) / 32;
+    const int G = g_size(), nwp = (G + 31) / 32;
     const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (w < nwp) {
         double v = threadIdx.x < (unsigned)G ? s_rbuf[threadIdx.x] : 0.0;
@@ -1307,7 +1343,7 @@ __device__ __forceinline__ void reduce_finish(const Dev<Real>& d)
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < nwp; k++) t += s_red[k];
-        d.ctl->thermo[blockIdx.x] = t;
+        d.ctl->thermo[g_rank()] = t;
         s_ls.red_pending = 0;
     }
 }
@@ -1326,9 +1362,12 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     bs.target = s_ls.bar_target;
     bar_arrive(d.ctl, bs, pub_dst, &s_ls.dmax_bits);
     const int had = s_ls.have_thermo, prev = s_ls.parity;
-    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + blockIdx.x) * kNQ, s_red);
-    const bool red = had && blockIdx.x < kNQA;
+    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ, s_red);
+    // groups of at least kNQA blocks: one quantity per block, asynchronously;
+    // smaller groups reduce every quantity here
+    const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
     if (red) reduce_issue(d, a, prev);
+    if (kBatched && had && g_size() < kNQA) run_reduce_thermo(d, a, prev);
     if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
         s_ls.bar_target = bs.target;
         s_ls.parity = par;
@@ -1345,8 +1384,11 @@ __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
     __syncthreads();
 }
 
+// One system advanced by the group of blocks this block belongs to (g_rank /
+// g_size set by the caller).  Returns false when a wait timed out (the status
+// word says so).
 template <typename Real, bool UNI>
-__global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
+__device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 {
     Ctl* ctl = d.ctl;
     PairP<Real>* tab = (PairP<Real>*)s_tab_raw;
@@ -1360,7 +1402,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
         s_ls.pc = ctl->pos_cur;
         s_ls.ac = ctl->arr_cur;
         // the list's block partition depends on the grid: rebuild if it changed
-        s_ls.need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != (int)gridDim.x);
+        s_ls.need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != g_size());
         s_ls.remaining = a.nsteps;
         s_ls.done = 0;
         s_ls.parity = 0;
@@ -1376,7 +1418,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 
     if (a.build_only) {
         const int rc = run_rebuild(d, a);
-        if (rc == 2) return;
+        if (rc == 2) return false;
         if (threadIdx.x == 0) {
             s_ls.need_rb = rc;
             s_ls.rc = rc;
@@ -1386,7 +1428,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
         if (s_ls.state == 1) {
             if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
                 const int rc = run_rebuild(d, a);
-                if (rc == 2) return;
+                if (rc == 2) return false;
                 if (threadIdx.x == 0) {
                     s_ls.need_rb = rc;
                     s_ls.rc = rc;
@@ -1395,18 +1437,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
             }
             if (s_ls.rc == 0) {
                 run_s_pass<Real, UNI>(d, a);
-                if (!grid_barrier(ctl, a.timeout_ns, 10)) return;
+                if (!grid_barrier(ctl, a.timeout_ns, 10)) return false;
                 const int par = (int)(s_ls.step & 1);
                 Acc<Real> acc;
                 run_f_pass<Real, UNI>(d, a, F_STORE, s_ls.step, acc);
                 if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
-                if (!f_barrier(d, a, acc, par, nullptr, 11)) return;
+                if (!f_barrier(d, a, acc, par, nullptr, 11)) return false;
             }
         }
         if (s_ls.rc == 0 && s_ls.remaining > 0 && s_ls.state == 0) {
             const long long stp = s_ls.step;
-            if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dmax2[stp & 1] = 0u;
-            if (!grid_barrier(ctl, a.timeout_ns, 12)) return;
+            if (threadIdx.x == 0 && g_rank() == 0) ctl->dmax2[stp & 1] = 0u;
+            if (!grid_barrier(ctl, a.timeout_ns, 12)) return false;
             run_open_pass(d, a, stp);
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -1414,15 +1456,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 s_ls.state = 2;
                 s_ls.own_ok = 0;  // new positions in global memory only
             }
-            if (!grid_barrier(ctl, a.timeout_ns, 13, &ctl->dmax2[stp & 1])) return;
+            if (!grid_barrier(ctl, a.timeout_ns, 13, &ctl->dmax2[stp & 1])) return false;
             add_disp(ctl, stp);
         }
         while (s_ls.rc == 0 && s_ls.state == 2) {
             const long long stp = s_ls.step;
-            if (threadIdx.x == 0 && blockIdx.x == 0) ctl->dmax2[(stp + 1) & 1] = 0u;
+            if (threadIdx.x == 0 && g_rank() == 0) ctl->dmax2[(stp + 1) & 1] = 0u;
             if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
                 const int rc = run_rebuild(d, a);
-                if (rc == 2) return;
+                if (rc == 2) return false;
                 if (threadIdx.x == 0) {
                     s_ls.need_rb = rc;
                     s_ls.rc = rc;
@@ -1440,7 +1482,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 bar_arrive(ctl, bs);
                 if (fin) reduce_finish(d);
                 if (threadIdx.x == 0) s_ls.bar_target = bs.target;
-                if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return;
+                if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return false;
             }
             const int par = (int)((stp + 1) & 1);
             Acc<Real> acc;
@@ -1450,7 +1492,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
                 s_ls.remaining--;
                 s_ls.done++;
             }
-            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21)) return;
+            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21)) return false;
             if (more) {
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
                 add_disp(ctl, stp + 1);
@@ -1463,10 +1505,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
     cp_async_wait_all();  // a reduction started at the last barrier is not needed
     if (s_ls.have_thermo) {
         // the last pass's partials were written after its barrier's arrival
-        if (!grid_barrier(ctl, a.timeout_ns, 30)) return;
+        if (!grid_barrier(ctl, a.timeout_ns, 30)) return false;
         run_reduce_thermo(d, a, s_ls.parity);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (g_rank() == 0 && threadIdx.x == 0) {
         ctl->state = s_ls.state;
         ctl->pos_cur = s_ls.pc;
         ctl->arr_cur = s_ls.ac;
@@ -1475,10 +1517,51 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
         ctl->n_rebuilds += s_ls.rebuilds;
         ctl->steps_done = s_ls.done;
         ctl->need_rebuild = s_ls.need_rb;
-        if (s_ls.rebuilds > 0) ctl->list_grid = s_ls.rc == 0 ? (int)gridDim.x : -1;
+        if (s_ls.rebuilds > 0) ctl->list_grid = s_ls.rc == 0 ? g_size() : -1;
     }
+    return true;
 }
 
+#if !SWP_BATCHED
+template <typename Real, bool UNI>
+__global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
+{
+    run_system<Real, UNI>(d, a);
+}
+#else
+
+// Batched launch: many independent systems in one cooperative launch.  Block
+// b works through items[item_ofs[b] .. item_ofs[b + 1]), each (system, rank in
+// the system's group, group size): a system either has a group of blocks to
+// itself or runs on one block, which then advances its systems one after the
+// other.  A block that belongs to a group of more than one block has no other
+// item, so the group barriers only ever wait for blocks working on the same
+// system.
+template <typename Real, bool UNI>
+__global__ void __launch_bounds__(kBlock, 1) k_batch(const Dev<Real>* devs, const RunArgs* args,
+                                                     const int* item_ofs, const int4* items)
+{
+    __shared__ Dev<Real> s_dev;
+    __shared__ RunArgs s_args;
+    const int i0 = item_ofs[blockIdx.x], i1 = item_ofs[blockIdx.x + 1];
+    for (int it = i0; it < i1; it++) {
+        const int4 w = items[it];
+        __syncthreads();  // the previous system is done with the shared copies
+        const int* sd = (const int*)&devs[w.x];
+        const int* sa = (const int*)&args[w.x];
+        for (int k = threadIdx.x; k < (int)(sizeof(Dev<Real>) / 4); k += blockDim.x) ((int*)&s_dev)[k] = sd[k];
+        for (int k = threadIdx.x; k < (int)(sizeof(RunArgs) / 4); k += blockDim.x) ((int*)&s_args)[k] = sa[k];
+        if (threadIdx.x == 0) {
+            s_grp[0] = w.y;
+            s_grp[1] = w.z;
+        }
+        __syncthreads();
+        if (!run_system<Real, UNI>(s_dev, s_args)) return;
+    }
+}
+#endif  // SWP_BATCHED
+
+#if !SWP_BATCHED
 // ---------------------------------------------------------------------------
 // Host-exchange kernels (user order <-> slot order).
 
@@ -1573,4 +1656,7 @@ __global__ void k_get_nlist(Dev<Real> d, int pc, int* rows, int* counts, int wid
     }
 }
 
+#endif  // !SWP_BATCHED
+
+}  // namespace single / batched
 }  // namespace swp

@@ -2,14 +2,20 @@
 // precision (swp_f32.cu, swp_f64.cu).
 #pragma once
 
+#define SWP_BATCHED 0
 #include "swp_kernels.cuh"
+#undef SWP_BATCHED
+#define SWP_BATCHED 1
+#include "swp_kernels.cuh"
+#undef SWP_BATCHED
 
 namespace swp {
+using single::Stage;
 
 template <typename Real>
 static void* run_fn(int uni)
 {
-    return uni ? (void*)k_run<Real, true> : (void*)k_run<Real, false>;
+    return uni ? (void*)single::k_run<Real, true> : (void*)single::k_run<Real, false>;
 }
 
 template <typename Real>
@@ -52,13 +58,44 @@ cudaError_t run_occupancy(int block, int* blocks_per_sm)
     return e;
 }
 
+template <typename Real>
+static void* batch_fn(int uni)
+{
+    return uni ? (void*)batched::k_batch<Real, true> : (void*)batched::k_batch<Real, false>;
+}
+
+template <typename Real>
+cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
+                         int uni, int grid, cudaStream_t s)
+{
+    void* fn = batch_fn<Real>(uni);
+    cudaError_t e = prepare_fn<Real>(fn);
+    if (e != cudaSuccess) return e;
+    void* kargs[] = {(void*)&devs, (void*)&args, (void*)&item_ofs, (void*)&items};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), kargs, run_smem_bytes<Real>(), s);
+}
+
+template <typename Real>
+cudaError_t batch_occupancy(int* blocks_per_sm)
+{
+    void* fu = batch_fn<Real>(1);
+    void* fg = batch_fn<Real>(0);
+    int bu = 0, bg = 0;
+    cudaError_t e = prepare_fn<Real>(fu);
+    if (e == cudaSuccess) e = prepare_fn<Real>(fg);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, fu, kBlock, run_smem_bytes<Real>());
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, fg, kBlock, run_smem_bytes<Real>());
+    *blocks_per_sm = bu < bg ? bu : bg;
+    return e;
+}
+
 static inline int io_grid(int n) { return n > 0 ? (n + 255) / 256 : 1; }
 
 template <typename Real>
 cudaError_t launch_set_state(const Dev<Real>& d, cudaStream_t s)
 {
     if (d.n == 0) return cudaSuccess;
-    k_set_state<Real><<<io_grid(d.n), 256, 0, s>>>(d);
+    single::k_set_state<Real><<<io_grid(d.n), 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -66,7 +103,7 @@ template <typename Real>
 cudaError_t launch_get_state(const Dev<Real>& d, int pc, int ac, cudaStream_t s)
 {
     if (d.n == 0) return cudaSuccess;
-    k_get_state<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc, ac);
+    single::k_get_state<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc, ac);
     return cudaGetLastError();
 }
 
@@ -74,7 +111,7 @@ template <typename Real>
 cudaError_t launch_get_forces(const Dev<Real>& d, int pc, cudaStream_t s)
 {
     if (d.n == 0) return cudaSuccess;
-    k_get_forces<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc);
+    single::k_get_forces<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc);
     return cudaGetLastError();
 }
 
@@ -83,7 +120,7 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
                              cudaStream_t s)
 {
     if (d.n == 0) return cudaSuccess;
-    k_get_nlist<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc, rows, counts, width);
+    single::k_get_nlist<Real><<<io_grid(d.n), 256, 0, s>>>(d, pc, rows, counts, width);
     return cudaGetLastError();
 }
 
@@ -94,6 +131,9 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
     template cudaError_t launch_get_state<R>(const Dev<R>&, int, int, cudaStream_t);             \
     template cudaError_t launch_get_forces<R>(const Dev<R>&, int, cudaStream_t);                 \
     template cudaError_t launch_get_nlist<R>(const Dev<R>&, int, int*, int*, int, cudaStream_t); \
+    template cudaError_t launch_batch<R>(const Dev<R>*, const RunArgs*, const int*, const int4*, int, int,   \
+                                         cudaStream_t);                                                   \
+    template cudaError_t batch_occupancy<R>(int*);                                               \
     template size_t run_smem_bytes<R>();
 
 }  // namespace swp

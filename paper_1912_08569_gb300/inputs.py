@@ -146,3 +146,26 @@ def workload(name: str = "mix100k", lambda3: float = 1.0, seed: int = 1, n: int 
                 tags=np.arange(n, dtype=np.uint32), n_types=2,
                 pairs=swap_pairs(lambda3=lambda3, shift=shift), kT=kT, gamma=gamma, dt=dt,
                 skin=skin, seed=seed)
+
+
+def batch_workload(n_systems: int = 256, seed: int = 7, n_min: int = 1000, n_max: int = 32000,
+                   density=(0.2, 0.6), lambdas=(0.0, 0.5, 1.0, 2.0, 5.0), kT=(0.03, 0.2)):
+    """Independent systems of uneven size for a batched run (seeded).
+
+    Sizes log-uniform in [n_min, n_max], densities uniform in ``density``,
+    lambda cycling through ``lambdas``, temperatures uniform in ``kT``; each
+    system is the binary A:B 1:1 mixture of ``workload`` (RSA positions,
+    Maxwell velocities at its temperature), BAOAB gamma 1, dt 0.001, skin 0.3.
+    """
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for k in range(n_systems):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        rho = float(rng.uniform(*density))
+        t = float(rng.uniform(*kT))
+        lam = float(lambdas[k % len(lambdas)])
+        wl = workload("mix100k", lambda3=lam, seed=seed * 1000 + k, n=n, density=rho)
+        wl["kT"] = t
+        wl["v"] = maxwell_velocities(n, t, wl["mass"], seed=seed * 1000 + k + 500)
+        out.append(wl)
+    return out

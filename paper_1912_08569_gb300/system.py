@@ -186,3 +186,78 @@ class SwapSystem:
             self.close()
         except Exception:
             pass
+
+
+class SwapBatch:
+    """Independent SwapSystem objects advanced together, one launch per call.
+
+    The systems may differ in size, box, coefficients and temperature; they
+    share precision, device and stream.  ``split`` sets which systems get
+    blocks of their own (see swp_batch_step); ``autotune`` picks it by timing.
+    """
+
+    def __init__(self, systems, split: float = 1.0):
+        import torch
+
+        self.systems = list(systems)
+        if not self.systems:
+            raise ValueError("empty batch")
+        s0 = self.systems[0]
+        for s in self.systems:
+            if s.device != s0.device or s.stream.cuda_stream != s0.stream.cuda_stream:
+                raise ValueError("batched systems need one device and one stream")
+            if s.precision != s0.precision:
+                raise ValueError("batched systems need one precision")
+        self.torch = torch
+        self.split = float(split)
+        nb = A.swp_batch_workspace_size(len(self.systems))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=s0.device)
+
+    def _per(self, v):
+        if np.ndim(v) == 0:
+            return [float(v)] * len(self.systems)
+        v = [float(x) for x in v]
+        if len(v) != len(self.systems):
+            raise ValueError("one value per system")
+        return v
+
+    def run(self, nsteps: int, dt, kT=0.0, gamma=0.0, sync: bool = True):
+        """Advance every system nsteps steps (per-system or common dt, kT, gamma)."""
+        dt, kT, gamma = self._per(dt), self._per(kT), self._per(gamma)
+        A.swp_batch_step([s.ctx for s in self.systems], dt, kT, gamma, int(nsteps), self.split,
+                         self.ws.data_ptr(), self.ws.numel())
+        if not sync:
+            return
+        for k, s in enumerate(self.systems):
+            try:
+                A.swp_sync(s.ctx)
+            except A.SwpError as e:
+                if e.code != A.SWP_ERR_NLIST_OVERFLOW:
+                    raise
+                # this system stopped at the overflow: grow its list, finish alone
+                th = A.swp_read_thermo(s.ctx, check=False)
+                s._grow(th.max_row)
+                s.run(int(nsteps) - int(th.steps_done), dt[k], kT[k], gamma[k])
+
+    def sync(self):
+        for s in self.systems:
+            A.swp_sync(s.ctx)
+
+    def autotune(self, nsteps: int, dt, kT=0.0, gamma=0.0, splits=(0.5, 1.0, 2.0, 4.0, 1e9)):
+        """Times one nsteps run per candidate split (the systems advance) and keeps the fastest."""
+        t = self.torch
+        best = None
+        for sp in splits:
+            self.split = float(sp)
+            self.run(1, dt, kT, gamma)  # warm-up (and list builds for the new grouping)
+            e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+            stream = self.systems[0].stream
+            e0.record(stream)
+            self.run(nsteps, dt, kT, gamma, sync=False)
+            e1.record(stream)
+            self.sync()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, float(sp))
+        self.split = best[1]
+        return best

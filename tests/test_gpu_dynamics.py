@@ -40,7 +40,8 @@ def _min_image(d, box):
     return d - box * np.round(d / box)
 
 
-# per-quantity trajectory tolerances after <= 20 steps:
+# per-quantity trajectory tolerances after <= 20 steps (FP32: a few ulp of the
+# positions amplified by 20 steps of the dynamics; FP64 likewise):
 TRAJ = {"fp32": dict(x=2e-6, v=2e-4), "fp64": dict(x=1e-11, v=1e-9)}
 
 
