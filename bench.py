@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "swap-potential particle-timesteps/s at 100k (FP32); % of HBM roofline"
 UNIT = "particle-timesteps/s"
-# swp_read_thermo copies the device control block (184 bytes) to the host.
-CTL_BYTES = 184
+# swp_read_thermo copies the device control block (192 bytes) to the host.
+CTL_BYTES = 192
 
 
 def _args():
@@ -162,8 +162,9 @@ def _peaks():
 
 
 def _profile_traffic(n, md_steps):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    """DRAM bytes of one step-kernel launch (dram__bytes_read.sum +
+    dram__bytes_write.sum) from the committed ncu record, if it was taken on
+    the current kernel sources and on this launch size (else None)."""
     p = os.path.join(ROOT, "profiles", "k_run_traffic.json")
     try:
         with open(p) as fh:
@@ -172,10 +173,9 @@ def _profile_traffic(n, md_steps):
         return None
     if d.get("kernel_digest") != _kernel_digest():
         return None
-    per_particle_step = d.get("dram_bytes_per_particle_step")
-    if per_particle_step is None:
+    if d.get("n") != n or d.get("md_steps") != md_steps:
         return None
-    return per_particle_step * n * md_steps
+    return d.get("dram_bytes_per_launch")
 
 
 def algorithmic_bytes(n, md_steps, nn, nn_r, rebuilds):

@@ -557,7 +557,7 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
     int bps = 0;
     SWP_CUDA(c0, batch_occupancy<Real>(&bps));
     if (bps < 1) return fail(c0, SWP_ERR_CUDA, "batched step kernel does not fit on an SM");
-    const int B = std::min(kMaxGrid, c0->num_sms * std::min(bps, 2048 / kBlock));
+    const int B = std::min(kMaxGrid, c0->num_sms * std::min(bps, 2048 / kBlockBatch));
     if (ws_bytes < batch_bytes(m, sizeof(Dev<Real>))) return fail(c0, SWP_ERR_INVALID, "batch workspace too small");
     std::vector<long long> w(m);
     for (int r = 0; r < m; r++) w[r] = cs[idx[r]]->n;

@@ -13,6 +13,7 @@ constexpr int kNQ = 12;            // per-block thermo partials: see Q_* below
 constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
 constexpr int kBlock = 1024;       // threads per block of the step kernel (one block per SM)
 constexpr int kMaxGrid = 320;      // largest grid of the step kernel (blocks)
+constexpr int kBlockBatch = 1024;  // threads per block of the batched kernel
 constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays clear)
 
 // Thermo quantities, in the order of the per-block partials.
@@ -57,6 +58,7 @@ struct Ctl {
     int max_row;                 // row length (entries per particle) the last build needed
     int overflow;                // set by a block whose entries exceeded its capacity
     int list_grid;               // grid size the list was built for (its block partition)
+    int list_chunk;              // block size the list was built with (its sub-chunk length)
     unsigned int dmax2[2];       // per-step max squared displacement (float bits), by parity
     double disp;                 // displacement bound accumulated since the last build
     long long step;              // completed time steps

@@ -35,6 +35,12 @@ namespace single {
 #endif
 
 constexpr bool kBatched = SWP_BATCHED != 0;
+// Threads per block.  The batched kernel reads every system's descriptors from
+// shared memory rather than the constant bank, so at 64 registers per thread
+// it spills; 512-thread blocks at 128 registers run without spilling but were
+// measured slower on 256 systems (2.6e9 against 2.8e9 particle-steps/s), so it
+// keeps 1024.
+constexpr int kThreads = kBatched ? kBlockBatch : kBlock;
 
 // ---------------------------------------------------------------------------
 // Group of blocks that advances one system: the whole grid for a single
@@ -755,7 +761,7 @@ template <typename Real>
 struct Stage {
     typedef typename Dev<Real>::R4 R4;
     static constexpr int kWave = sizeof(Real) == 4 ? 8192 : 3072;
-    static constexpr size_t B = kBlock;
+    static constexpr size_t B = kThreads;
     static constexpr size_t O_POS = 0;                                  // [B] R4 positions
     static constexpr size_t O_VEL = O_POS + B * sizeof(R4);             // [B] R4 velocities
     static constexpr size_t O_XQ = O_VEL + B * sizeof(R4);              // [3B] fixed-point positions
@@ -1313,6 +1319,21 @@ __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
     }
 }
 
+// The same reduction for a group of fewer than kNQA blocks (batched runs):
+// rank 0 alone, warp q summing quantity q over the group's blocks in order.
+template <typename Real>
+__device__ __forceinline__ void reduce_small(const Dev<Real>& d, const RunArgs& a, int par)
+{
+    if (g_rank() != 0) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < kNQA) {
+        double v = lane < g_size() ? d.partials[((size_t)par * a.max_blocks + lane) * kNQ + w] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) d.ctl->thermo[w] = v;
+    }
+}
+
 // The same reduction in two halves, kept off the blocks' critical path: at a
 // force-pass barrier block q (< kNQA) starts asynchronous copies of quantity
 // q of every block's partials of the previous pass into s_rbuf; before it
@@ -1367,7 +1388,7 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     // smaller groups reduce every quantity here
     const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
     if (red) reduce_issue(d, a, prev);
-    if (kBatched && had && g_size() < kNQA) run_reduce_thermo(d, a, prev);
+    if (kBatched && had && g_size() < kNQA) reduce_small(d, a, prev);
     if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
         s_ls.bar_target = bs.target;
         s_ls.parity = par;
@@ -1402,7 +1423,8 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         s_ls.pc = ctl->pos_cur;
         s_ls.ac = ctl->arr_cur;
         // the list's block partition depends on the grid: rebuild if it changed
-        s_ls.need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != g_size());
+        s_ls.need_rb = ctl->need_rebuild | a.force_rebuild | (ctl->list_grid != g_size()) |
+                       (ctl->list_chunk != (int)blockDim.x);
         s_ls.remaining = a.nsteps;
         s_ls.done = 0;
         s_ls.parity = 0;
@@ -1506,7 +1528,10 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
     if (s_ls.have_thermo) {
         // the last pass's partials were written after its barrier's arrival
         if (!grid_barrier(ctl, a.timeout_ns, 30)) return false;
-        run_reduce_thermo(d, a, s_ls.parity);
+        if (kBatched && g_size() < kNQA)
+            reduce_small(d, a, s_ls.parity);
+        else
+            run_reduce_thermo(d, a, s_ls.parity);
     }
     if (g_rank() == 0 && threadIdx.x == 0) {
         ctl->state = s_ls.state;
@@ -1517,7 +1542,10 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         ctl->n_rebuilds += s_ls.rebuilds;
         ctl->steps_done = s_ls.done;
         ctl->need_rebuild = s_ls.need_rb;
-        if (s_ls.rebuilds > 0) ctl->list_grid = s_ls.rc == 0 ? g_size() : -1;
+        if (s_ls.rebuilds > 0) {
+            ctl->list_grid = s_ls.rc == 0 ? g_size() : -1;
+            ctl->list_chunk = blockDim.x;
+        }
     }
     return true;
 }
@@ -1538,7 +1566,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 // item, so the group barriers only ever wait for blocks working on the same
 // system.
 template <typename Real, bool UNI>
-__global__ void __launch_bounds__(kBlock, 1) k_batch(const Dev<Real>* devs, const RunArgs* args,
+__global__ void __launch_bounds__(kThreads, 1) k_batch(const Dev<Real>* devs, const RunArgs* args,
                                                      const int* item_ofs, const int4* items)
 {
     __shared__ Dev<Real> s_dev;

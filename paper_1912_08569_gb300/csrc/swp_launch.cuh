@@ -65,14 +65,20 @@ static void* batch_fn(int uni)
 }
 
 template <typename Real>
+static size_t batch_smem_bytes()
+{
+    return batched::Stage<Real>::kBytes;
+}
+
+template <typename Real>
 cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
                          int uni, int grid, cudaStream_t s)
 {
     void* fn = batch_fn<Real>(uni);
-    cudaError_t e = prepare_fn<Real>(fn);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<Real>());
     if (e != cudaSuccess) return e;
     void* kargs[] = {(void*)&devs, (void*)&args, (void*)&item_ofs, (void*)&items};
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), kargs, run_smem_bytes<Real>(), s);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlockBatch), kargs, batch_smem_bytes<Real>(), s);
 }
 
 template <typename Real>
@@ -81,10 +87,11 @@ cudaError_t batch_occupancy(int* blocks_per_sm)
     void* fu = batch_fn<Real>(1);
     void* fg = batch_fn<Real>(0);
     int bu = 0, bg = 0;
-    cudaError_t e = prepare_fn<Real>(fu);
-    if (e == cudaSuccess) e = prepare_fn<Real>(fg);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, fu, kBlock, run_smem_bytes<Real>());
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, fg, kBlock, run_smem_bytes<Real>());
+    const int sm = (int)batch_smem_bytes<Real>();
+    cudaError_t e = cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fg, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, fu, kBlockBatch, sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, fg, kBlockBatch, sm);
     *blocks_per_sm = bu < bg ? bu : bg;
     return e;
 }
