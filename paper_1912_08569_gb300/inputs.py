@@ -169,3 +169,62 @@ def batch_workload(n_systems: int = 256, seed: int = 7, n_min: int = 1000, n_max
         wl["v"] = maxwell_velocities(n, t, wl["mass"], seed=seed * 1000 + k + 500)
         out.append(wl)
     return out
+
+
+def dumbbell_workload(seed: int = 1, kT: float = 0.03, n_a: int = 600, n_b: int = 400, density: float = 0.125,
+                      n: int = 100, rcut: float = 1.3, lambda3: float = 1.0):
+    """The dumbbell mixture of section "Effect of swaps": n_a A and n_b B
+    particles at the given density, A-B swap pair with exponent n, A-A and B-B
+    WCA.  Every B starts bonded: it is placed at distance 2^(1/n) (the minimum
+    of the pair potential) from its own A, in a random direction, and the
+    pairs and the free A are laid down by random sequential addition with a
+    minimum separation of 1.0 from everything else (closer A-B pairs would
+    start with the enormous energies of the n = 100 wall)."""
+    if n_b > n_a:
+        raise ValueError("needs n_b <= n_a (every B bonded to its own A)")
+    rng = np.random.Generator(np.random.Philox(seed))
+    N = n_a + n_b
+    box = cubic_box(N, density)
+    L = box[0]
+    rmin = 2.0 ** (1.0 / n)
+    pts = []
+    tree_pts = np.zeros((0, 3))
+
+    def far(c, others):
+        if len(others) == 0:
+            return True
+        d = others - c
+        d -= box * np.round(d / box)
+        return np.min(np.sum(d * d, axis=1)) >= 1.0
+
+    types = []
+    tries = 0
+    while len(types) < N:
+        tries += 1
+        if tries > 200000:
+            raise RuntimeError("dumbbell_workload: could not place particles")
+        a = f32(rng.random(3) * box)
+        a[a >= box] = 0.0
+        pair = len(types) < 2 * n_b
+        if pair:
+            u = rng.standard_normal(3)
+            u /= np.linalg.norm(u)
+            b = f32(np.mod(a + rmin * u, L))
+            b[b >= box] = 0.0
+            if not (far(a, tree_pts) and far(b, tree_pts)):
+                continue
+            tree_pts = np.concatenate([tree_pts, a[None], b[None]])
+            types += [0, 1]
+        else:
+            if not far(a, tree_pts):
+                continue
+            tree_pts = np.concatenate([tree_pts, a[None]])
+            types.append(0)
+    x = tree_pts
+    types = np.asarray(types, dtype=np.int32)
+    mass = np.ones(N)
+    v = maxwell_velocities(N, kT, mass, seed=seed + 1000)
+    pairs = swap_pairs(n=n, rcut=rcut, lambda3=lambda3)
+    return dict(name="dumbbell", n=N, density=density, box=box, x=x, v=v, types=types, mass=mass,
+                tags=np.arange(N, dtype=np.uint32), n_types=2, pairs=pairs, kT=kT, gamma=1.0, dt=0.001,
+                skin=0.3, seed=seed)
