@@ -200,6 +200,20 @@ SWP_API int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt,
 /* Wait for the stream and report latched device errors. */
 SWP_API int swp_sync(swp_ctx* ctx);
 
+/* Derivatives of the energy and of the forces with respect to the
+ * coefficients (lambda, eps, sigma) of the reactive type pair (ti, tj), at
+ * the current positions (Eq. 2b, Eq. pot, Eq. 3bp; the two-body term is
+ * linear in eps, vh depends on sigma only through sigma/r, r_min = sigma
+ * 2^(1/n) moves with sigma, r_cut stays fixed).  Needs current forces
+ * (swp_compute_forces), the unshifted form and a single reactive type pair.
+ * dU [3] (host): dU/dlambda, dU/deps, dU/dsigma.  dF_dev (device pointer or
+ * NULL): [3][n][3] doubles, dF_dev[(k n + i) 3 + c] = d F_ic / d theta_k in
+ * user order.  Uses the workspace's staging arrays (not concurrently with
+ * other reads of this context); synchronises the stream.  Errors:
+ * SWP_ERR_INVALID (bad types, not a swap pair, shifted form, more than one
+ * reactive type pair), SWP_ERR_STATE (forces not current). */
+SWP_API int swp_param_grad(swp_ctx* ctx, int ti, int tj, double dU[3], double* dF_dev);
+
 /* Synchronising reads.  swp_read_thermo fills *out with the record of the
  * last force evaluation.  swp_read_forces needs current forces (state 0):
  * f [n][3].  swp_read_state: x [n][3] wrapped into [0, L), v [n][3], img

@@ -11,6 +11,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libswapmd.so")
 
@@ -46,7 +48,7 @@ EXPORTS = (
     "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
-    "swp_batch_workspace_size", "swp_batch_step",
+    "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad",
 )
 
 
@@ -111,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
         "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+        "swp_param_grad": ([c_void_p, c_int, c_int, P(c_double), c_void_p], c_int),
         "swp_batch_workspace_size": ([c_int], c_size_t),
         "swp_batch_step": ([P(c_void_p), c_int, P(c_double), P(c_double), P(c_double), c_int, c_double,
                             c_void_p, c_size_t], c_int),
@@ -258,6 +261,14 @@ def swp_compute_forces_static(ctx, x_dev, type_dev, f_dev, thermo_dev=None, stre
                                                                 _ptr(f_dev), _ptr(thermo_dev),
                                                                 ctypes.c_void_p(stream)),
                   "swp_compute_forces_static")
+
+
+def swp_param_grad(ctx, ti: int, tj: int, dF_dev=None):
+    """dU/d(lambda, eps, sigma) of the reactive pair (ti, tj) as a numpy array;
+    dF/d(lambda, eps, sigma) into dF_dev ([3, n, 3] float64 device tensor) if given."""
+    out = (ctypes.c_double * 3)()
+    _check(ctx, load_library().swp_param_grad(ctx, int(ti), int(tj), out, _ptr(dF_dev)), "swp_param_grad")
+    return np.array(list(out))
 
 
 def swp_batch_workspace_size(n_systems: int) -> int:

@@ -190,7 +190,8 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     int* cell_fill = (int*)take(sizeof(int) * (c->ncell + n));
     int* perm = (int*)take(sizeof(int) * n);
     int* bsum = (int*)take(sizeof(int) * c->max_blocks);
-    double* partials = (double*)take(sizeof(double) * 2 * c->max_blocks * kNQ);
+    // thermo partials of the step kernel; also the scratch of the parameter derivatives (4 * 512 + 4)
+    double* partials = (double*)take(sizeof(double) * std::max<size_t>(2 * c->max_blocks * kNQ, 4 * 512 + 4));
     double* io = (double*)take(sizeof(double) * 7 * n);
     int* io_int = (int*)take(sizeof(int) * 4 * n);
     if (d) {
@@ -987,6 +988,45 @@ int swp_read_forces(swp_ctx* c, double* f, int where)
     }
     SWP_CUDA(c, cudaMemcpyAsync(f, io, sizeof(double) * 3 * c->n, kind_from_dev(where), c->stream));
     SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SWP_OK;
+}
+
+int swp_param_grad(swp_ctx* c, int ti, int tj, double dU[3], double* dF_dev)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (!dU) return fail(c, SWP_ERR_INVALID, "null output");
+    if (ti < 0 || tj < 0 || ti >= c->ntypes || tj >= c->ntypes) return fail(c, SWP_ERR_INVALID, "type out of range");
+    const PairHost& p = c->pairs[ti * c->ntypes + tj];
+    if (p.kind != KIND_SWAP) return fail(c, SWP_ERR_INVALID, "(ti, tj) is not a swap pair");
+    if (p.shift) return fail(c, SWP_ERR_INVALID, "parameter derivatives need the unshifted form");
+    for (int a = 0; a < c->ntypes; a++)
+        for (int b = a; b < c->ntypes; b++)
+            if (c->pairs[a * c->ntypes + b].kind == KIND_SWAP && !((a == ti && b == tj) || (a == tj && b == ti)))
+                return fail(c, SWP_ERR_INVALID, "parameter derivatives need a single reactive type pair");
+    dU[0] = dU[1] = dU[2] = 0.0;
+    if (c->n == 0) return SWP_OK;
+    rc = sync_ctl(c);
+    if (rc) return rc;
+    if (c->hctl.state != 0) return fail(c, SWP_ERR_STATE, "forces are not current: call swp_compute_forces");
+    const double lam = p.lambda3, eps = p.eps, sig = p.sigma;
+    double* part;
+    if (c->precision == SWP_FP64) {
+        part = c->dd.partials;
+        SWP_CUDA(c, launch_param_grad<double>(c->dd, c->hctl.pos_cur, c->dd.io, part, lam, eps, sig, dF_dev,
+                                               part + 2048, c->stream));
+    } else {
+        part = c->df.partials;
+        SWP_CUDA(c, launch_param_grad<float>(c->df, c->hctl.pos_cur, c->df.io, part, lam, eps, sig, dF_dev,
+                                              part + 2048, c->stream));
+    }
+    double t[4];
+    SWP_CUDA(c, cudaMemcpyAsync(t, part + 2048, sizeof t, cudaMemcpyDeviceToHost, c->stream));
+    SWP_CUDA(c, cudaStreamSynchronize(c->stream));
+    // t = (T, sum_i (sum_j vh q - S D), sum_pairs v/eps, sum_pairs Q)
+    dU[0] = eps * t[0];
+    dU[1] = t[2] + lam * t[0];
+    dU[2] = (eps * t[3] + lam * eps * t[1]) / sig;
     return SWP_OK;
 }
 

@@ -163,6 +163,10 @@ cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* 
                          int uni, int grid, cudaStream_t s);
 template <typename Real>
 cudaError_t batch_occupancy(int* blocks_per_sm);
+// Derivatives with respect to one reactive type pair's (lambda, eps, sigma).
+template <typename Real>
+cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* part, double lam, double eps,
+                              double sig, double* out, double* total, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_set_state(const Dev<Real>& d, cudaStream_t s);
 template <typename Real>

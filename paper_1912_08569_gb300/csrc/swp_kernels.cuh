@@ -1684,6 +1684,139 @@ __global__ void k_get_nlist(Dev<Real> d, int pc, int* rows, int* counts, int wid
     }
 }
 
+// ---------------------------------------------------------------------------
+// Derivatives with respect to the reactive pair's coefficients (lambda, eps,
+// sigma), at the current positions and list, for one reactive type pair
+// (a^2 = lambda eps) and the unshifted form.  With x = (sigma/r)^n:
+//   v = 4 eps (x^2 - x),  vh = 4 (x - x^2) beyond r_min (1 inside),
+//   Q = 4 n (2x^2 - x) (= -r v'/eps), q = Q beyond r_min (0 inside) (= r vh'),
+//   S_i = sum_k vh_ik, D_i = sum_k q_ik (over i's reactive partners inside r_cut),
+//   T = sum_i sum_{j<k} vh_ij vh_ik = 1/2 sum_i (S_i^2 - sum_j vh_ij^2),
+//   U = sum_pairs v + lambda eps T (+ the pairs that do not depend on theta).
+// Then dU/dlambda = eps T, dU/deps = sum_pairs v/eps + lambda T,
+//   dU/dsigma = (eps sum_pairs Q + lambda eps sum_i (sum_j vh_ij q_ij - S_i D_i)) / sigma,
+// and, with the pair force F_i = -ft (x_j - x_i), ft = eps (Q - lambda g q) / r^2,
+// g = S_i + S_j - 2 vh:
+//   dft/dlambda = -eps g q / r^2,   dft/deps = (Q - lambda g q) / r^2,
+//   dft/dsigma = (eps Q_s - lambda eps ((2q - D_i - D_j) q + g q_s)) / (sigma r^2),
+//   Q_s = 4 n^2 x (4x - 1) (= sigma dQ/dsigma), q_s = Q_s beyond r_min (0 inside).
+// Decisions (inside r_cut, beyond r_min) are the force kernels' own.
+
+template <typename Real>
+__device__ __forceinline__ Real pair_x(const PairP<Real>& p, Real r2)
+{
+    const Real s2 = p.sig2 * recip(r2);
+    Real x = ipow(s2, p.nhalf);
+    if (p.odd) x *= sqrt(s2);
+    return x;
+}
+
+// Pass 1: S_i and D_i per slot into sd[2i], sd[2i+1]; per-block sums of
+// (T, sum_i (sum_j vh q - S D), sum_pairs v/eps, sum_pairs Q) into part[4b..].
+template <typename Real>
+__global__ void k_pgrad_sums(Dev<Real> d, int pc, double* sd, double* part)
+{
+    __shared__ double red[4][32];
+    const int n = d.n;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const typename Dev<Real>::R4 pi = d.pos[pc][i];
+        const int4 inf = d.pinfo[i];
+        double S = 0.0, D = 0.0, v2 = 0.0, vq = 0.0, ve = 0.0, qq = 0.0;
+        for (int e = inf.x; e < inf.x + inf.y; e++) {
+            const typename Dev<Real>::R4 pj = d.pos[pc][d.ent_j[e]];
+            const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
+            Real dx, dy, dz;
+            const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+            if (!(r2 < p.rc2)) continue;
+            const double x = (double)pair_x(p, r2), nn = (double)p.n_real;
+            const bool beyond = r2 > p.rmin2;
+            const double vh = beyond ? 4.0 * (x - x * x) : 1.0;
+            const double Q = 4.0 * nn * (2.0 * x * x - x);
+            const double q = beyond ? Q : 0.0;
+            S += vh;
+            D += q;
+            v2 += vh * vh;
+            vq += vh * q;
+            ve += 0.5 * 4.0 * (x * x - x);  // each pair is listed from both ends
+            qq += 0.5 * Q;
+        }
+        sd[2 * i] = S;
+        sd[2 * i + 1] = D;
+        acc[0] += 0.5 * (S * S - v2);
+        acc[1] += vq - S * D;
+        acc[2] += ve;
+        acc[3] += qq;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int k = 0; k < nw; k++) t += red[threadIdx.x][k];
+        part[4 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// Pass 2: dF/dtheta per particle, in user order: out[(k n + tag) 3 + c].
+template <typename Real>
+__global__ void k_pgrad_forces(Dev<Real> d, int pc, const double* sd, double lam, double eps, double sig,
+                               double* out)
+{
+    const int n = d.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const typename Dev<Real>::R4 pi = d.pos[pc][i];
+        const int4 inf = d.pinfo[i];
+        const double Si = sd[2 * i], Di = sd[2 * i + 1];
+        double g3[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        for (int e = inf.x; e < inf.x + inf.y; e++) {
+            const int j = d.ent_j[e];
+            const typename Dev<Real>::R4 pj = d.pos[pc][j];
+            const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
+            Real dx, dy, dz;
+            const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+            if (!(r2 < p.rc2)) continue;
+            const double x = (double)pair_x(p, r2), nn = (double)p.n_real, rr = (double)r2;
+            const bool beyond = r2 > p.rmin2;
+            const double vh = beyond ? 4.0 * (x - x * x) : 1.0;
+            const double Q = 4.0 * nn * (2.0 * x * x - x);
+            const double q = beyond ? Q : 0.0;
+            const double Qs = 4.0 * nn * nn * x * (4.0 * x - 1.0);
+            const double qs = beyond ? Qs : 0.0;
+            const double g = Si + sd[2 * j] - 2.0 * vh;
+            const double Dsum = Di + sd[2 * j + 1];
+            const double dft[3] = {-eps * g * q / rr, (Q - lam * g * q) / rr,
+                                   (eps * Qs - lam * eps * ((2.0 * q - Dsum) * q + g * qs)) / (sig * rr)};
+            const double dv[3] = {(double)dx, (double)dy, (double)dz};
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) g3[k][c] -= dft[k] * dv[c];
+        }
+        const int tag = packed_of(pi.w) >> kTypeBits;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) out[((size_t)k * n + tag) * 3 + c] = g3[k][c];
+    }
+}
+
+// Pass 3: one block adds the per-block sums in block order.
+static __global__ void k_pgrad_total(const double* part, int nblocks, double* total)
+{
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; b++) t += part[4 * b + threadIdx.x];
+        total[threadIdx.x] = t;
+    }
+}
+
 #endif  // !SWP_BATCHED
 
 }  // namespace single / batched

@@ -2,6 +2,8 @@
 // precision (swp_f32.cu, swp_f64.cu).
 #pragma once
 
+#include <algorithm>
+
 #define SWP_BATCHED 0
 #include "swp_kernels.cuh"
 #undef SWP_BATCHED
@@ -131,6 +133,26 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
     return cudaGetLastError();
 }
 
+// Parameter derivatives (k_pgrad_*): S/D per slot into sd [2n], dF/dtheta
+// into out [3][n][3] (user order) when out is not null, the four sums into
+// total [4]; part: scratch of 4 * 512 doubles.
+template <typename Real>
+cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* part, double lam, double eps,
+                              double sig, double* out, double* total, cudaStream_t s)
+{
+    const int blocks = std::max(1, std::min(512, (d.n + 255) / 256));
+    single::k_pgrad_sums<Real><<<blocks, 256, 0, s>>>(d, pc, sd, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (out) {
+        single::k_pgrad_forces<Real><<<blocks, 256, 0, s>>>(d, pc, sd, lam, eps, sig, out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    single::k_pgrad_total<<<1, 32, 0, s>>>(part, blocks, total);
+    return cudaGetLastError();
+}
+
 #define SWP_INSTANTIATE(R)                                                                       \
     template cudaError_t launch_run<R>(const Dev<R>&, const RunArgs&, int, int, cudaStream_t);   \
     template cudaError_t run_occupancy<R>(int, int*);                                            \
@@ -141,6 +163,8 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
     template cudaError_t launch_batch<R>(const Dev<R>*, const RunArgs*, const int*, const int4*, int, int,   \
                                          cudaStream_t);                                                   \
     template cudaError_t batch_occupancy<R>(int*);                                               \
+    template cudaError_t launch_param_grad<R>(const Dev<R>&, int, double*, double*, double, double, double, \
+                                              double*, double*, cudaStream_t);                            \
     template size_t run_smem_bytes<R>();
 
 }  // namespace swp
