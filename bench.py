@@ -52,9 +52,11 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="mix100k", choices=["mix100k", "batch256"],
+    ap.add_argument("--workload", default="mix100k", choices=["mix100k", "batch256", "diff20k"],
                     help="mix100k: the single 100k-particle system (default); batch256: 256 "
-                         "independent systems of 1k-32k particles in one launch per step")
+                         "independent systems of 1k-32k particles in one launch per step; diff20k: "
+                         "force-matching gradient over 64 snapshots of 20k particles")
+    ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
 
@@ -508,6 +510,101 @@ def run_batch(a):
     return 0
 
 
+DIFF_METRIC = "force-matching gradient particle-evaluations/s (energy, forces, dU and dF by theta; 20k)"
+
+
+def run_diff(a):
+    """Differentiable form: one bench step = the gradient of a force-matching
+    loss (mean squared force error over a.snapshots snapshots of 20,000
+    particles, density 0.4) with respect to the reactive pair's (lambda, eps,
+    sigma), through autodiff.energy and a double backward.  The reference
+    forces are this library's own at theta_ref = (1, 1, 1) (a synthetic
+    target; accuracy against the oracle is covered by the tests)."""
+    import torch
+
+    from paper_1912_08569_gb300 import SwapSystem, autodiff, inputs
+    from paper_1912_08569_gb300.build import build
+
+    rank, world, local = _dist()
+    if world > 1 and rank != 0:
+        return 0  # one GPU: the differentiable form runs on rank 0 only
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    build()
+    snaps = [inputs.workload("mix100k", n=20000, density=0.4, seed=100 + k) for k in range(a.snapshots)]
+    wl = snaps[0]
+    s = SwapSystem(wl["n"], 2, wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"])
+    model = autodiff.SwapModel(s, wl["pairs"], wl["types"])
+    xs = [torch.tensor(w["x"], dtype=torch.float64, device=dev) for w in snaps]
+    theta_ref = torch.tensor([1.0, 1.0, 1.0], dtype=torch.float64, device=dev)
+    with torch.no_grad():
+        refs = [autodiff.forces(model, x, theta_ref).detach() for x in xs]
+    theta0 = [1.3, 0.9, 1.02]
+
+    def grad_step():
+        theta = torch.tensor(theta0, dtype=torch.float64, device=dev, requires_grad=True)
+        loss = 0.0
+        for x, Fr in zip(xs, refs):
+            xr = x.clone().requires_grad_(True)
+            U = autodiff.energy(model, xr, theta)
+            (gx,) = torch.autograd.grad(U, xr, create_graph=True)
+            loss = loss + ((-gx - Fr) ** 2).mean()
+        (loss / len(xs)).backward()
+        return theta.grad
+
+    def plain_step():
+        th = torch.tensor(theta0, dtype=torch.float64, device=dev)
+        for x in xs:
+            model.evaluate(x, th, want_grad=False)
+
+    for _ in range(a.warmup):
+        grad_step()
+    clocks = Clocks(0)
+    clocks.start()
+    time.sleep(0.3)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record()
+    for _ in range(a.steps):
+        g = grad_step()
+    e[1].record()
+    torch.cuda.synchronize()
+    t_grad = e[0].elapsed_time(e[1]) / 1e3
+    e[2].record()
+    for _ in range(a.steps):
+        plain_step()
+    e[3].record()
+    torch.cuda.synchronize()
+    t_plain = e[2].elapsed_time(e[3]) / 1e3
+    clk = clocks.stop()
+    n_eval = a.steps * len(xs) * wl["n"]
+    value = n_eval / t_grad
+    _, counts = s.nlist()
+    nn, nn_r = float(counts[:, 1].mean()), float(counts[:, 0].mean())
+    # bytes one snapshot's kernels must move per particle: state in (28) + one force
+    # evaluation with a list build (160 + 4 (nn + nn_r) + 120 + 4 nn) + forces out (24) +
+    # the two derivative passes (2 x (32 + 4 nn_r) + 16 + 72)
+    b_alg = n_eval * (28 + 160 + 4 * (nn + nn_r) + 120 + 4 * nn + 24 + 2 * (32 + 4 * nn_r) + 16 + 72)
+    peak, peak_kind = _peaks()
+    achieved = b_alg / t_grad / 1e9
+    out = {"metric": DIFF_METRIC, "value": value, "unit": "particle-evaluations/s", "n_gpus": 1,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_grad / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"diff20k: {len(xs)} snapshots of 20,000 particles, A:B 1:1, density 0.4, "
+                                  f"n=10, r_cut=1.5, theta0=(1.3, 0.9, 1.02), target forces at theta=(1,1,1)",
+                      "snapshots": len(xs), "particles": wl["n"], "parallelism": "single GPU",
+                      "l2": "not flushed (host-synchronising steps between evaluations)"},
+           "plain": {"value": n_eval / t_plain, "unit": "particle-evaluations/s",
+                     "what": "energy and forces only, same snapshots"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "peak_kind": peak_kind},
+           "grad": [float(v) for v in g.cpu().tolist()], "cpu_baseline": None, "e2e": None,
+           "gpu_launches": a.steps * len(xs) * 6, "clocks": clk, "kernel_digest": _kernel_digest()}
+    print(json.dumps(out), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.md_steps is None:
@@ -516,6 +613,8 @@ def main():
         return run_reference(a)
     if a.workload == "batch256":
         return run_batch(a)
+    if a.workload == "diff20k":
+        return run_diff(a)
     return run_ours(a)
 
 
