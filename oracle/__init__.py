@@ -16,6 +16,10 @@ follows:
   forces as -dU/dx, virial as in Eq. p3, bond count.
 * ``nlist``: neighbour-list membership for a given skin (the set every valid
   Verlet list built from a cell list must contain, and nothing more).
+* ``forces(..., bonds=...)`` / ``run(..., bonds=...)``: harmonic bonds
+  k/2 (r - r0)^2 of a fixed topology added to the pair terms (the chains of the
+  vitrimer network; the paper does not give the form, the harmonic one with
+  k = 100, r0 = 1 is this build's configuration).
 * ``run``: velocity Verlet (NVE) or BAOAB Langevin (NVT; the paper's
   "canonical Langevin dynamics" of section "Self-assembly pitfalls").
 * ``philox4x32_10`` / ``normals3``: the counter-based generator of Salmon et al.
@@ -85,9 +89,13 @@ def _load():
             lib.orc_nlist.argtypes = [ctypes.c_int, dp, ip, ctypes.c_int, vp, dp, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, ip, ip]
             lib.orc_nlist.restype = ctypes.c_int
+            lib.orc_bonds.argtypes = [ctypes.c_int, dp, dp, ctypes.c_long, ip, ctypes.c_double, ctypes.c_double,
+                                      dp, dp, dp, dp]
+            lib.orc_bonds.restype = None
             lib.orc_run.argtypes = [ctypes.c_int, dp, dp, ip, ip, dp, up, ctypes.c_int, vp, dp,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, dp]
+                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, dp, ctypes.c_long, ip,
+                                    ctypes.c_double, ctypes.c_double]
             lib.orc_run.restype = ctypes.c_int
             lib.orc_v2.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
             lib.orc_v2.restype = ctypes.c_double
@@ -158,12 +166,22 @@ def u2(r: float, **pair) -> float:
     return _load().orc_u2(t.ctypes.data, float(r))
 
 
-def forces(x, types, ntypes, table, box, fp32: bool = False):
+def _bond_arrays(bonds):
+    if bonds is None or len(bonds) == 0:
+        return 0, np.zeros(2, dtype=np.int32)
+    b = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+    return b.shape[0], b
+
+
+def forces(x, types, ntypes, table, box, fp32: bool = False, bonds=None, kbond: float = 0.0,
+           r0: float = 1.0):
     """Energies, forces, virial and bond count of a configuration.
 
     Returns a dict with U2, U3, W (6: xx yy zz xy xz yz), n_bonds, F (n x 3),
     scale_U2, scale_U3, scale_W and fscale (n) -- the error scales used by the
     parity tolerances (sum of |term| + r |d term / dr| over the terms summed).
+    bonds ([m, 2] indices): harmonic bonds k/2 (r - r0)^2 added to F, W and
+    their scales; their energy is returned as U_bond (0 without bonds).
     """
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     n = x.shape[0]
@@ -178,9 +196,19 @@ def forces(x, types, ntypes, table, box, fp32: bool = False):
                             int(bool(fp32)), _dp(F), _dp(out), _dp(sc), _dp(fs))
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
+    nb, b = _bond_arrays(bonds)
+    ub, sub = 0.0, 0.0
+    if nb:
+        ob = np.zeros(7)
+        sb = np.zeros(2)
+        _load().orc_bonds(n, _dp(x), _dp(box), nb, _ip(b), float(kbond), float(r0), _dp(F), _dp(ob), _dp(fs),
+                          _dp(sb))
+        out[2:8] += ob[1:7]
+        ub, sub = ob[0], sb[0]
+        sc[2] += sb[1]
     return dict(U2=out[0], U3=out[1], W=out[2:8].copy(), n_bonds=int(round(out[8])),
                 F=F[:n].copy(), scale_U2=sc[0], scale_U3=sc[1], scale_W=sc[2],
-                fscale=fs[:n].copy())
+                fscale=fs[:n].copy(), U_bond=ub, scale_Ub=sub)
 
 
 def nlist(x, types, ntypes, table, box, skin: float, fp32: bool = False, maxn: int = 256):
@@ -203,10 +231,11 @@ def nlist(x, types, ntypes, table, box, skin: float, fp32: bool = False, maxn: i
 
 
 def run(x, v, types, mass, tags, ntypes, table, box, dt, nsteps, kT=0.0, gamma=0.0,
-        seed=0, step0=0, fp32=False, img=None):
+        seed=0, step0=0, fp32=False, img=None, bonds=None, kbond=0.0, r0=1.0):
     """Advance (x, v) by nsteps (BAOAB if gamma > 0, else velocity Verlet).
 
-    Returns (x, v, img, thermo) with thermo[s] = [U2, U3, K, W(6), n_bonds].
+    Returns (x, v, img, thermo) with thermo[s] = [U2, U3, K, W(6), n_bonds,
+    U_bond] (W includes the bonds' virial).
     """
     x = np.array(x, dtype=np.float64).reshape(-1, 3)
     v = np.array(v, dtype=np.float64).reshape(-1, 3)
@@ -217,11 +246,13 @@ def run(x, v, types, mass, tags, ntypes, table, box, dt, nsteps, kT=0.0, gamma=0
     tg = np.ascontiguousarray(tags, dtype=np.uint32)
     box = np.ascontiguousarray(box, dtype=np.float64)
     tab = np.ascontiguousarray(table, dtype=PAIR_DTYPE)
-    th = np.zeros((max(nsteps, 1), 10))
+    th = np.zeros((max(nsteps, 1), 11))
+    nb, b = _bond_arrays(bonds)
     rc = _load().orc_run(n, _dp(x), _dp(v), _ip(im), _ip(ty), _dp(m),
                          tg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), int(ntypes),
                          tab.ctypes.data, _dp(box), int(bool(fp32)), float(dt), int(nsteps),
-                         float(kT), float(gamma), int(seed), int(step0), _dp(th))
+                         float(kT), float(gamma), int(seed), int(step0), _dp(th), nb, _ip(b), float(kbond),
+                         float(r0))
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return x, v, im, th[:nsteps]

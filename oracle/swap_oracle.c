@@ -28,6 +28,9 @@
  *   - the virial is W_ab = -sum over pair vectors r_ij (= x_i - x_j) of
  *     (r_ij)_a dU/d(r_ij)_b, which for the triplets is the content of Eq. p3.
  *
+ * Optional harmonic bonds (orc_bonds): u = k/2 (r - r0)^2 for listed pairs,
+ * minimum image, no cut-off, no exclusion of the bonded pair's own pair term.
+ *
  * Optional "shifted" form of a swap pair (off by default, the paper's literal
  * form is unshifted): v_s = v - v(r_cut) and vh_s = (v(r_cut) - v)/(eps +
  * v(r_cut)) beyond r_min, continuous at r_cut and still equal to 1 at r_min.
@@ -511,6 +514,56 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
     return 0;
 }
 
+/* Harmonic bonds of a fixed topology (the chains of the vitrimer network, a
+ * NEXT item of this build; the paper's vitrimer section uses bonded chains
+ * without giving a form): u = k/2 (r - r0)^2 for every listed pair (i, j),
+ * minimum image, no cut-off.  ADDS the forces to force (3n, may be NULL) and
+ * the scales to fscale (n, may be NULL); out[0] = bond energy, out[1..6] =
+ * virial (xx yy zz xy xz yz, same convention as orc_forces); scale[0..1] =
+ * energy and virial error scales (may be NULL). */
+void orc_bonds(int n, const double *x, const double *box, long nb, const int *bonds, double k,
+               double r0, double *force, double *out, double *fscale, double *scale)
+{
+    double U = 0.0, W[6] = {0, 0, 0, 0, 0, 0}, sU = 0.0, sW = 0.0;
+    (void)n;
+    for (long b = 0; b < nb; b++) {
+        int i = bonds[2 * b], j = bonds[2 * b + 1];
+        double d[3];
+        for (int c = 0; c < 3; c++)
+            d[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]); /* r_ij = x_i - x_j */
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double u = 0.5 * k * (r - r0) * (r - r0);
+        double du = k * (r - r0), d2u = k;
+        U += u;
+        sU += fabs(u) + r * fabs(du);
+        double g = -du / r;
+        if (force)
+            for (int c = 0; c < 3; c++) {
+                force[3 * i + c] += g * d[c];
+                force[3 * j + c] -= g * d[c];
+            }
+        W[0] += g * d[0] * d[0];
+        W[1] += g * d[1] * d[1];
+        W[2] += g * d[2] * d[2];
+        W[3] += g * d[0] * d[1];
+        W[4] += g * d[0] * d[2];
+        W[5] += g * d[1] * d[2];
+        sW += r * fabs(du) + r * r * fabs(d2u);
+        if (fscale) {
+            double sc = fabs(du) + r * fabs(d2u);
+            fscale[i] += sc;
+            fscale[j] += sc;
+        }
+    }
+    out[0] = U;
+    for (int c = 0; c < 6; c++)
+        out[1 + c] = W[c];
+    if (scale) {
+        scale[0] = sU;
+        scale[1] = sW;
+    }
+}
+
 /* Neighbour-list membership: for every particle i, the sorted indices j != i
  * whose squared decision distance is below (r_cut(ti,tj) + skin)^2, for
  * interacting type pairs only.  counts[i] = number of such j; nbr is n*maxn
@@ -604,19 +657,37 @@ void orc_normals3(uint64_t seed, uint64_t step, uint32_t tag, uint32_t purpose, 
 /* Advance nsteps from step index step0.  BAOAB when gamma > 0 (NVT), else
  * velocity Verlet (NVE).  x is kept wrapped into [0, L) with image counts in
  * img (3n ints, may be NULL).  thermo (may be NULL) receives per step
- * [U2, U3, K, W0..W5, n_bonds] (10 doubles) after the step.  Langevin step k
- * (advancing state step0+k) draws its normals with step value step0+k and the
- * particle's tag, purpose 1. */
+ * [U2, U3, K, W0..W5, n_bonds, U_bond] (11 doubles) after the step (W includes
+ * the bonds' virial).  Langevin step k (advancing state step0+k) draws its
+ * normals with step value step0+k and the particle's tag, purpose 1.  nb
+ * harmonic bonds (orc_bonds; nb = 0: none) act besides the pair terms. */
+static int run_forces(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
+                      const double *box, int fp32, double *F, double *out, long nb, const int *bonds,
+                      double kb, double r0)
+{
+    if (orc_forces(n, x, type, ntypes, tab, box, fp32, F, out, NULL, NULL))
+        return -1;
+    out[9] = 0.0;
+    if (nb > 0) {
+        double ob[7];
+        orc_bonds(n, x, box, nb, bonds, kb, r0, F, ob, NULL, NULL);
+        for (int c = 0; c < 6; c++)
+            out[2 + c] += ob[1 + c];
+        out[9] = ob[0];
+    }
+    return 0;
+}
+
 int orc_run(int n, double *x, double *v, int *img, const int *type, const double *mass,
             const uint32_t *tag, int ntypes, const orc_pair *tab, const double *box, int fp32,
             double dt, int nsteps, double kT, double gamma, uint64_t seed, uint64_t step0,
-            double *thermo)
+            double *thermo, long nb, const int *bonds, double kb, double r0)
 {
     double *F = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
-    double out[9];
+    double out[10];
     if (!F)
         return -1;
-    if (orc_forces(n, x, type, ntypes, tab, box, fp32, F, out, NULL, NULL)) {
+    if (run_forces(n, x, type, ntypes, tab, box, fp32, F, out, nb, bonds, kb, r0)) {
         free(F);
         return -1;
     }
@@ -650,7 +721,7 @@ int orc_run(int n, double *x, double *v, int *img, const int *type, const double
                 }
             }
         }
-        if (orc_forces(n, x, type, ntypes, tab, box, fp32, F, out, NULL, NULL)) {
+        if (run_forces(n, x, type, ntypes, tab, box, fp32, F, out, nb, bonds, kb, r0)) {
             free(F);
             return -1;
         }
@@ -663,13 +734,14 @@ int orc_run(int n, double *x, double *v, int *img, const int *type, const double
             }
         }
         if (thermo) {
-            double *t = &thermo[(long)s * 10];
+            double *t = &thermo[(long)s * 11];
             t[0] = out[0];
             t[1] = out[1];
             t[2] = K;
             for (int q = 0; q < 6; q++)
                 t[3 + q] = out[2 + q];
             t[9] = out[8];
+            t[10] = out[9];
         }
     }
     free(F);

@@ -482,3 +482,91 @@ def test_inputs_recipe():
     assert box[0] == float(np.float32(box[0]))
     ty = inputs.alternating_types(5000)
     assert (ty == 0).sum() == 2500
+
+
+# ---------------------------------------------------------------------------
+# Harmonic bonds (the vitrimer network's chains): u = k/2 (r - r0)^2.
+
+def test_single_bond_closed_form(orc):
+    box = np.array([20.0, 20.0, 20.0])
+    x = np.array([[5.0, 5.0, 5.0], [6.3, 5.0, 5.0]])
+    ty = np.array([0, 0], dtype=np.int32)
+    pairs = {(0, 0): dict(kind=0)}  # no pair interaction: the bond alone
+    tab = orc.pair_table(1, {(0, 0): dict(kind=0, eps=1.0, sigma=1.0, n=6)})
+    r = orc.forces(x, ty, 1, tab, box, bonds=[[0, 1]], kbond=100.0, r0=1.0)
+    assert r["U_bond"] == pytest.approx(0.5 * 100.0 * 0.3 ** 2, rel=1e-14)
+    # stretched bond pulls the two together: F_0 along +x, F_1 along -x
+    np.testing.assert_allclose(r["F"], [[30.0, 0, 0], [-30.0, 0, 0]], rtol=1e-13, atol=1e-12)
+    assert r["W"][0] == pytest.approx(-30.0 * 1.3, rel=1e-13)  # r_ij F_ij with r_ij = -1.3, F = +30
+    del pairs
+
+
+def test_bonded_chain_forces_are_minus_gradient(orc):
+    """Chains bonded along the tags, with the swap and WCA pair terms: forces by
+    central differences of the total energy."""
+    h = 1e-6
+    for s in range(10, 60):
+        x, ty, box = _small_system(s, n=30, L=5.6)
+        pairs = inputs.swap_pairs(lambda3=1.0, shift=1)
+        if _far_from_kinks(x, box, pairs, ty, h):
+            break
+    else:
+        pytest.skip("no configuration away from the cut-off kinks")
+    bonds = [[i, i + 1] for i in range(0, 29) if i % 10 != 9]  # three chains of 10
+    tab = orc.pair_table(2, pairs)
+    kw = dict(bonds=bonds, kbond=100.0, r0=1.0)
+    r = orc.forces(x, ty, 2, tab, box, **kw)
+    assert r["U_bond"] > 0.0
+    Fnum = np.zeros_like(x)
+    for i in range(len(x)):
+        for c in range(3):
+            xp = x.copy()
+            xp[i, c] += h
+            xm = x.copy()
+            xm[i, c] -= h
+            up = orc.forces(xp, ty, 2, tab, box, **kw)
+            um = orc.forces(xm, ty, 2, tab, box, **kw)
+            Fnum[i, c] = -((up["U2"] + up["U3"] + up["U_bond"]) - (um["U2"] + um["U3"] + um["U_bond"])) / (2 * h)
+    err = np.linalg.norm(Fnum - r["F"], axis=1)
+    assert np.all(err <= 1e-6 * (r["fscale"] + 1.0))
+    assert np.linalg.norm(r["F"].sum(0)) < 1e-10 * r["fscale"].sum()
+
+
+def test_bonded_virial_trace_by_box_scaling(orc):
+    x, ty, box = _small_system(5, n=30, L=5.6)
+    pairs = inputs.swap_pairs(lambda3=2.0, shift=1)
+    tab = orc.pair_table(2, pairs)
+    kw = dict(bonds=[[i, i + 1] for i in range(29)], kbond=100.0, r0=1.0)
+    r = orc.forces(x, ty, 2, tab, box, **kw)
+    h = 1e-7
+
+    def U(s):
+        o = orc.forces(x * s, ty, 2, tab, box * s, **kw)
+        return o["U2"] + o["U3"] + o["U_bond"]
+
+    trW = -(U(1 + h) - U(1 - h)) / (2 * h)
+    assert trW == pytest.approx(r["W"][:3].sum(), rel=1e-5, abs=1e-6 * r["scale_W"])
+
+
+def test_bonded_nve_conserves_energy(orc):
+    """Velocity Verlet with bonds: the total energy including the bonds drifts
+    like dt^2."""
+    x, ty, box = _small_system(7, n=30, L=5.6)
+    pairs = inputs.swap_pairs(lambda3=1.0, shift=1)
+    tab = orc.pair_table(2, pairs)
+    kw = dict(bonds=[[i, i + 1] for i in range(0, 29) if i % 10 != 9], kbond=100.0, r0=1.0)
+    rng = np.random.default_rng(3)
+    v0 = rng.standard_normal((30, 3)) * 0.3
+    m = np.ones(30)
+    tags = np.arange(30, dtype=np.uint32)
+    drift = []
+    for dt in (0.002, 0.001):
+        n = int(round(0.4 / dt))
+        xo, vo, _, th = orc.run(x, v0, ty, m, tags, 2, tab, box, dt, n, **kw)
+        E = th[:, 0] + th[:, 1] + th[:, 2] + th[:, 10]
+        r0 = orc.forces(x, ty, 2, tab, box, **kw)
+        E0 = r0["U2"] + r0["U3"] + r0["U_bond"] + 0.5 * (v0 ** 2).sum()
+        drift.append(np.max(np.abs(E - E0)))
+    assert drift[1] < drift[0] / 3.0  # second order in dt
+    # the random configuration starts with stretched bonds (violent motion): a loose bound
+    assert drift[1] < 5e-3 * abs(E0)
