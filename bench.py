@@ -52,10 +52,11 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="mix100k", choices=["mix100k", "batch256", "diff20k"],
+    ap.add_argument("--workload", default="mix100k", choices=["mix100k", "batch256", "diff20k", "vitrimer2m"],
                     help="mix100k: the single 100k-particle system (default); batch256: 256 "
                          "independent systems of 1k-32k particles in one launch per step; diff20k: "
-                         "force-matching gradient over 64 snapshots of 20k particles")
+                         "force-matching gradient over 64 snapshots of 20k particles; vitrimer2m: "
+                         "2M-bead bonded network with swapping crosslinkers")
     ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
@@ -605,16 +606,113 @@ def run_diff(a):
     return 0
 
 
+VIT_METRIC = "vitrimer particle-timesteps/s (2M beads, chains of 50, harmonic bonds, swap crosslinks; FP32)"
+
+
+def run_vitrimer(a):
+    """Vitrimer network: 2,000,000 beads (chains of 50 with harmonic bonds k=100,
+    r0=1, 10 % reactive A beads, as many free B crosslinkers, WCA between all
+    other pairs, A-B swap pair lambda 1), density 0.85, BAOAB kT 0.5; one bench
+    step = one launch of a.md_steps steps (defaults: 5 x 2000 = 10,000 timed
+    steps)."""
+    import torch
+
+    from paper_1912_08569_gb300 import SwapSystem, inputs
+    from paper_1912_08569_gb300.build import build
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    wl = inputs.vitrimer_workload(2_000_000, seed=1 + rank)
+    n = wl["n"]
+    s = SwapSystem(n, wl["n_types"], wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"])
+    s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
+    s.set_bonds(wl["bonds"], wl["kbond"], wl["r0"])
+    s.compute_forces()
+    dt, kT, gamma = wl["dt"], wl["kT"], wl["gamma"]
+    for _ in range(a.warmup):
+        s.run(a.md_steps, dt, kT, gamma)
+    _, counts = s.nlist()
+    nn, nn_r = float(counts[:, 1].mean()), float(counts[:, 0].mean())
+    th0 = s.thermo()
+    stream = s.stream
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(a.md_steps, dt, kT, gamma, sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    s.sync()
+    th1 = s.thermo()
+    clk = clocks.stop() if clocks else None
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    t = torch.tensor([float(np.sum(launch_ms))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * n * a.md_steps * a.steps / (total_ms / 1e3)
+    rebuilds = (th1["n_rebuilds"] - th0["n_rebuilds"]) / a.steps
+    # the pair path's bytes plus, per particle-step, the bonds: partner tags (16),
+    # their slots (8) and positions (32)
+    b_alg = algorithmic_bytes(n, a.md_steps, nn, nn_r, rebuilds) + n * a.md_steps * 56.0
+    peak, peak_kind = _peaks()
+    achieved = b_alg / (float(np.mean(launch_ms)) / 1e3) / 1e9
+    if rank == 0:
+        out = {"metric": VIT_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"vitrimer2m: {n} beads, chains of 50 (k=100, r0=1), 10% A + free B "
+                                      f"crosslinkers 1:1, WCA otherwise, density 0.85, lambda=1, BAOAB kT=0.5 "
+                                      f"gamma=1 dt=0.001, skin 0.3, lattice start",
+                          "n_particles": n, "md_steps_per_step": a.md_steps, "parallelism": f"replicas x{world}",
+                          "l2": "working set larger than L2 (not flushed)"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                            "alg_bytes_per_launch": b_alg, "nn_mean": nn, "nn_reactive_mean": nn_r,
+                            "rebuilds_per_launch": rebuilds},
+               "cpu_baseline": None, "e2e": None, "gpu_launches": a.steps, "clocks": clk,
+               "kernel_digest": _kernel_digest(),
+               "thermo_last": {"U2": th1["U2"], "U3": th1["U3"], "K": th1["K"], "n_bonds": th1["n_bonds"]}}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    s.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.md_steps is None:
-        a.md_steps = 5000 if a.workload == "batch256" else 1000
+        a.md_steps = {"batch256": 5000, "vitrimer2m": 2000}.get(a.workload, 1000)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batch256":
         return run_batch(a)
     if a.workload == "diff20k":
         return run_diff(a)
+    if a.workload == "vitrimer2m":
+        return run_vitrimer(a)
     return run_ours(a)
 
 

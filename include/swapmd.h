@@ -200,6 +200,18 @@ SWP_API int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt,
 /* Wait for the stream and report latched device errors. */
 SWP_API int swp_sync(swp_ctx* ctx);
 
+/* Harmonic bonds of a fixed topology, u = k/2 (r - r0)^2 per bond (minimum
+ * image, no cut-off), acting besides the pair terms, which still act between
+ * bonded particles (no exclusion).  They build the chains of the vitrimer
+ * network (the paper's section "Applications to vitrimers" names bonded
+ * chains carrying the swapping groups without giving their form; the
+ * harmonic form is this library's).  bonds: host [n_bonds][2] tags; at most
+ * 4 bonds per particle.  n_bonds = 0 removes them.  The bond energy is
+ * reported inside thermo.U2 and the bonds' virial inside thermo.W.  Marks
+ * forces stale.  Errors: SWP_ERR_INVALID (tag out of range, self bond,
+ * duplicate, more than 4 bonds on a particle, k < 0 or r0 < 0). */
+SWP_API int swp_set_bonds(swp_ctx* ctx, int n_bonds, const int32_t* bonds, double k, double r0);
+
 /* Derivatives of the energy and of the forces with respect to the
  * coefficients (lambda, eps, sigma) of the reactive type pair (ti, tj), at
  * the current positions (Eq. 2b, Eq. pot, Eq. 3bp; the two-body term is

@@ -48,7 +48,7 @@ EXPORTS = (
     "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
-    "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad",
+    "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds",
 )
 
 
@@ -114,6 +114,7 @@ def load_library(path: str = LIB_PATH):
         "swp_destroy": ([c_void_p], c_int),
         "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
         "swp_param_grad": ([c_void_p, c_int, c_int, P(c_double), c_void_p], c_int),
+        "swp_set_bonds": ([c_void_p, c_int, c_void_p, c_double, c_double], c_int),
         "swp_batch_workspace_size": ([c_int], c_size_t),
         "swp_batch_step": ([P(c_void_p), c_int, P(c_double), P(c_double), P(c_double), c_int, c_double,
                             c_void_p, c_size_t], c_int),
@@ -261,6 +262,13 @@ def swp_compute_forces_static(ctx, x_dev, type_dev, f_dev, thermo_dev=None, stre
                                                                 _ptr(f_dev), _ptr(thermo_dev),
                                                                 ctypes.c_void_p(stream)),
                   "swp_compute_forces_static")
+
+
+def swp_set_bonds(ctx, bonds, k: float, r0: float):
+    """Harmonic bonds k/2 (r - r0)^2 between the tag pairs bonds [m, 2] (empty: none)."""
+    b = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+    return _check(ctx, load_library().swp_set_bonds(ctx, int(b.shape[0]), _ptr(b) if b.size else None, float(k),
+                                                   float(r0)), "swp_set_bonds")
 
 
 def swp_param_grad(ctx, ti: int, tj: int, dF_dev=None):

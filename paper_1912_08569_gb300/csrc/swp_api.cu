@@ -54,6 +54,9 @@ struct swp_ctx {
     cudaStream_t stream = nullptr;
     bool ws_bound = false, nl_bound = false, state_set = false, table_dirty = true;
     bool layout_dirty = true;
+    std::vector<int> bond_host;  // [n][kMaxBonds] partner tags by tag (-1: none); empty: no bonds
+    double bond_k = 0.0, bond_r0 = 1.0;
+    bool bonds_dirty = false;
     Dev<float> df;
     Dev<double> dd;
     Ctl hctl;
@@ -194,6 +197,8 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     double* partials = (double*)take(sizeof(double) * std::max<size_t>(2 * c->max_blocks * kNQ, 4 * 512 + 4));
     double* io = (double*)take(sizeof(double) * 7 * n);
     int* io_int = (int*)take(sizeof(int) * 4 * n);
+    int* bond_tag = (int*)take(sizeof(int) * kMaxBonds * n);
+    int* slot_of_tag = (int*)take(sizeof(int) * n);
     if (d) {
         d->n = c->n;
         d->ntypes = c->ntypes;
@@ -232,6 +237,11 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
         d->io = io;
         d->io_int = io_int;
         d->table = table;
+        d->bond_tag = bond_tag;
+        d->slot_of_tag = slot_of_tag;
+        d->has_bonds = 0;  // set per run (prepare_args) when bonds were given
+        d->bond_k = Real(0);
+        d->bond_r0 = Real(1);
     }
     return off;
 }
@@ -296,6 +306,7 @@ int refresh_layout(swp_ctx* c)
     else layout<float>(c, (char*)c->ws, &c->df);
     if (c->precision == SWP_FP64) set_list(c, (char*)c->nl, &c->dd);
     else set_list(c, (char*)c->nl, &c->df);
+    c->bonds_dirty = !c->bond_host.empty();  // the bond table moved with the layout
     return SWP_OK;
 }
 
@@ -402,6 +413,15 @@ int prepare_args(swp_ctx* c, RunArgs& a)
 {
     int rc = upload_table(c);
     if (rc) return rc;
+    Dev<Real>& dv = dev<Real>(c);
+    if (c->bonds_dirty) {
+        SWP_CUDA(c, cudaMemcpyAsync(dv.bond_tag, c->bond_host.data(), sizeof(int) * c->bond_host.size(),
+                                    cudaMemcpyHostToDevice, c->stream));
+        c->bonds_dirty = false;
+    }
+    dv.has_bonds = c->bond_host.empty() ? 0 : 1;
+    dv.bond_k = (Real)c->bond_k;
+    dv.bond_r0 = (Real)c->bond_r0;
     a.max_blocks = c->max_blocks;
     a.timeout_ns = c->timeout_ns;
     double margin = 0.0;
@@ -565,13 +585,14 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
     BatchPlan plan;
     if (plan_batch(w, B, split, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
     std::vector<Dev<Real>> devs(m);
-    int uni = 1;
+    int uni = 1, bonds = 0;
     for (int r = 0; r < m; r++) {
         swp_ctx* c = cs[idx[r]];
         int rc = prepare_args<Real>(c, args[r]);
         if (rc) return rc;
         uni &= args[r].uni;
         devs[r] = dev<Real>(c);
+        bonds |= devs[r].has_bonds;
         SWP_CUDA(c0, cudaMemsetAsync(&devs[r].ctl->barrier, 0, sizeof(unsigned long long), c0->stream));
     }
     for (int k = 0; k < B; k++)
@@ -589,7 +610,7 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
                                  c0->stream));
     SWP_CUDA(c0, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(int4) * plan.items.size(),
                                  cudaMemcpyHostToDevice, c0->stream));
-    SWP_CUDA(c0, launch_batch<Real>(d_dev, d_args, d_ofs, d_items, uni, B, c0->stream));
+    SWP_CUDA(c0, launch_batch<Real>(d_dev, d_args, d_ofs, d_items, uni, bonds, B, c0->stream));
     return SWP_OK;
 }
 
@@ -684,6 +705,35 @@ int swp_set_pair(swp_ctx* c, int ti, int tj, int kind, double eps, double sigma,
                                     c->cell_rank.data(), sizeof(int) * 2 * c->ncell,
                                     cudaMemcpyHostToDevice, c->stream));
     }
+    return mark_stale(c);
+}
+
+int swp_set_bonds(swp_ctx* c, int n_bonds, const int32_t* bonds, double k, double r0)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (n_bonds < 0 || (n_bonds > 0 && !bonds) || !(k >= 0.0) || !std::isfinite(k) || !(r0 >= 0.0) ||
+        !std::isfinite(r0))
+        return fail(c, SWP_ERR_INVALID, "need n_bonds >= 0, bonds, k >= 0, r0 >= 0");
+    std::vector<int> tab;
+    if (n_bonds > 0) {
+        tab.assign((size_t)c->n * kMaxBonds, -1);
+        std::vector<int> cnt(c->n, 0);
+        for (int b = 0; b < n_bonds; b++) {
+            const int i = bonds[2 * b], j = bonds[2 * b + 1];
+            if (i < 0 || j < 0 || i >= c->n || j >= c->n || i == j)
+                return fail(c, SWP_ERR_INVALID, "bond with a tag out of range or bonded to itself");
+            if (cnt[i] >= kMaxBonds || cnt[j] >= kMaxBonds)
+                return fail(c, SWP_ERR_INVALID, "more than 4 bonds on one particle");
+            for (int q = 0; q < cnt[i]; q++)
+                if (tab[(size_t)i * kMaxBonds + q] == j) return fail(c, SWP_ERR_INVALID, "bond listed twice");
+            tab[(size_t)i * kMaxBonds + cnt[i]++] = j;
+            tab[(size_t)j * kMaxBonds + cnt[j]++] = i;
+        }
+    }
+    c->bond_host.swap(tab);
+    c->bond_k = k;
+    c->bond_r0 = r0;
+    c->bonds_dirty = !c->bond_host.empty();
     return mark_stale(c);
 }
 
@@ -1183,6 +1233,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
         SWP_CUDA(c, cudaGetSymbolAddress(&p, g_static_scratch));
         g_static_addr[dev] = p;
     }
+    if (!c->bond_host.empty()) return fail(c, SWP_ERR_INVALID, "bonded systems are not supported here");
     char* base = (char*)g_static_addr[dev];
     const size_t ws = layout<Real>(c, nullptr, nullptr);
     const size_t nl = list_bytes(c);

@@ -14,6 +14,7 @@ constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
 constexpr int kBlock = 1024;       // threads per block of the step kernel (one block per SM)
 constexpr int kMaxGrid = 320;      // largest grid of the step kernel (blocks)
 constexpr int kBlockBatch = 1024;  // threads per block of the batched kernel
+constexpr int kMaxBonds = 4;       // harmonic bonds per particle (chains: 2)
 constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays clear)
 
 // Thermo quantities, in the order of the per-block partials.
@@ -123,6 +124,10 @@ struct Dev {
     double* io;        // host-exchange staging: [3n] x, [3n] v, [n] mass
     int* io_int;       // staging: [n] types, [3n] images
     const PairP<Real>* table;  // [ntypes * ntypes]
+    int* bond_tag;     // [n][kMaxBonds] bonded partners' tags by tag (-1: none)
+    int* slot_of_tag;  // [n] slot of every tag (written at each rebuild when has_bonds)
+    int has_bonds;     // harmonic bonds k/2 (r - r0)^2 act (the vitrimer network's chains)
+    Real bond_k, bond_r0;
 };
 
 // What one launch of the step kernel does.
@@ -160,7 +165,7 @@ cudaError_t run_occupancy(int block, int* blocks_per_sm);
 // (system, rank in its group, group size, unused).
 template <typename Real>
 cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
-                         int uni, int grid, cudaStream_t s);
+                         int uni, int bonds, int grid, cudaStream_t s);
 template <typename Real>
 cudaError_t batch_occupancy(int* blocks_per_sm);
 // Derivatives with respect to one reactive type pair's (lambda, eps, sigma).

@@ -555,7 +555,9 @@ __device__ void ph_gather(const Dev<Real>& d, int pc, int ac, int t, int nt)
     const int n = d.n;
     for (int q = t; q < n; q += nt) {
         int p = d.perm[q];
-        d.pos[pc ^ 1][q] = d.pos[pc][p];
+        const typename Dev<Real>::R4 pp = d.pos[pc][p];
+        d.pos[pc ^ 1][q] = pp;
+        if (d.has_bonds) d.slot_of_tag[packed_of(pp.w) >> kTypeBits] = q;
         d.vel[ac ^ 1][q] = d.vel[ac][p];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -1046,7 +1048,7 @@ __device__ __forceinline__ void sum_run(const R4* w, int wb, int k0, int k1, Rea
 // With one sub-chunk per block the S pass of the same step left the block's
 // positions, list ranges and S values in shared memory, and the integrator
 // keeps the shared positions current for the next S pass.
-template <typename Real, bool UNI>
+template <typename Real, bool UNI, bool BONDS>
 __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const RunArgs& a, int pc,
                               int ac, int flags, long long step, Acc<Real>& acc,
                               const PairP<Real>& ps, const PairP<Real>& pw)
@@ -1108,6 +1110,32 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
                 sum_run(SM::w4(), wb, max(inf.z, wb), min(inf.z + inf.w, we), fx, fy, fz);
             }
             __syncthreads();
+        }
+        // harmonic bonds (vitrimer chains): F_i = k (r - r0) (x_j - x_i) / r, half
+        // of the energy and virial to each end (added to the two-body terms)
+        if (BONDS && d.has_bonds && t < P) {  // BONDS: some system of the launch has bonds
+            const R4 pi = SM::pos()[t];
+            const int tag = packed_of(pi.w) >> kTypeBits;
+            for (int b = 0; b < kMaxBonds; b++) {
+                const int pt = d.bond_tag[tag * kMaxBonds + b];
+                if (pt < 0) break;
+                const R4 pj = pos[d.slot_of_tag[pt]];
+                Real dx, dy, dz;
+                const Real r = sqrt(dist2_listed(pi, pj, d, dx, dy, dz));
+                const Real dr = r - d.bond_r0;
+                const Real g = d.bond_k * dr / r;
+                fx += g * dx;
+                fy += g * dy;
+                fz += g * dz;
+                acc.q[Q_U2] += Real(0.25) * d.bond_k * dr * dr;
+                const Real hf = Real(-0.5) * g;
+                acc.q[Q_W0 + 0] += hf * dx * dx;
+                acc.q[Q_W0 + 1] += hf * dy * dy;
+                acc.q[Q_W0 + 2] += hf * dz * dz;
+                acc.q[Q_W0 + 3] += hf * dx * dy;
+                acc.q[Q_W0 + 4] += hf * dx * dz;
+                acc.q[Q_W0 + 5] += hf * dy * dz;
+            }
         }
         // FP32: park the thermo accumulators in the (now free) wave buffer while
         // the integrator runs, so they do not hold registers at its peak
@@ -1272,13 +1300,13 @@ __device__ __forceinline__ void warp_max_disp(float v)
     if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&s_ls.dmax_bits, __float_as_uint(v));
 }
 
-template <typename Real, bool UNI>
+template <typename Real, bool UNI, bool BONDS>
 __device__ __forceinline__ void run_f_pass(const Dev<Real>& d, const RunArgs& a, int flags, long long stp,
                                            Acc<Real>& acc)
 {
 #pragma unroll
     for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
-    const float dmax = f_pass_block<Real, UNI>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
+    const float dmax = f_pass_block<Real, UNI, BONDS>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
                                                uni_params(a, Real(0))[0], uni_params(a, Real(0))[1]);
     if (flags & F_OPENING) warp_max_disp(dmax);
 }
@@ -1408,7 +1436,7 @@ __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
 // One system advanced by the group of blocks this block belongs to (g_rank /
 // g_size set by the caller).  Returns false when a wait timed out (the status
 // word says so).
-template <typename Real, bool UNI>
+template <typename Real, bool UNI, bool BONDS>
 __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 {
     Ctl* ctl = d.ctl;
@@ -1462,7 +1490,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 if (!grid_barrier(ctl, a.timeout_ns, 10)) return false;
                 const int par = (int)(s_ls.step & 1);
                 Acc<Real> acc;
-                run_f_pass<Real, UNI>(d, a, F_STORE, s_ls.step, acc);
+                run_f_pass<Real, UNI, BONDS>(d, a, F_STORE, s_ls.step, acc);
                 if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
                 if (!f_barrier(d, a, acc, par, nullptr, 11)) return false;
             }
@@ -1508,7 +1536,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             }
             const int par = (int)((stp + 1) & 1);
             Acc<Real> acc;
-            run_f_pass<Real, UNI>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, acc);
+            run_f_pass<Real, UNI, BONDS>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, acc);
             if (threadIdx.x == 0) {  // every thread read `remaining` before the pass's barriers
                 s_ls.step = stp + 1;
                 s_ls.remaining--;
@@ -1551,10 +1579,10 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 }
 
 #if !SWP_BATCHED
-template <typename Real, bool UNI>
+template <typename Real, bool UNI, bool BONDS>
 __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 {
-    run_system<Real, UNI>(d, a);
+    run_system<Real, UNI, BONDS>(d, a);
 }
 #else
 
@@ -1565,7 +1593,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 // other.  A block that belongs to a group of more than one block has no other
 // item, so the group barriers only ever wait for blocks working on the same
 // system.
-template <typename Real, bool UNI>
+template <typename Real, bool UNI, bool BONDS>
 __global__ void __launch_bounds__(kThreads, 1) k_batch(const Dev<Real>* devs, const RunArgs* args,
                                                      const int* item_ofs, const int4* items)
 {
@@ -1584,7 +1612,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch(const Dev<Real>* devs, co
             s_grp[1] = w.z;
         }
         __syncthreads();
-        if (!run_system<Real, UNI>(s_dev, s_args)) return;
+        if (!run_system<Real, UNI, BONDS>(s_dev, s_args)) return;
     }
 }
 #endif  // SWP_BATCHED

@@ -15,9 +15,10 @@ namespace swp {
 using single::Stage;
 
 template <typename Real>
-static void* run_fn(int uni)
+static void* run_fn(int uni, int bonds = 0)
 {
-    return uni ? (void*)single::k_run<Real, true> : (void*)single::k_run<Real, false>;
+    if (bonds) return uni ? (void*)single::k_run<Real, true, true> : (void*)single::k_run<Real, false, true>;
+    return uni ? (void*)single::k_run<Real, true, false> : (void*)single::k_run<Real, false, false>;
 }
 
 template <typename Real>
@@ -37,7 +38,7 @@ static cudaError_t prepare_fn(void* fn)
 template <typename Real>
 cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, cudaStream_t s)
 {
-    void* fn = run_fn<Real>(a.uni);
+    void* fn = run_fn<Real>(a.uni, d.has_bonds);
     cudaError_t e = prepare_fn<Real>(fn);
     if (e != cudaSuccess) return e;
     Dev<Real> dd = d;
@@ -49,21 +50,24 @@ cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block
 template <typename Real>
 cudaError_t run_occupancy(int block, int* blocks_per_sm)
 {
-    void* fu = run_fn<Real>(1);
-    void* fg = run_fn<Real>(0);
-    int bu = 0, bg = 0;
-    cudaError_t e = prepare_fn<Real>(fu);
-    if (e == cudaSuccess) e = prepare_fn<Real>(fg);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, fu, block, run_smem_bytes<Real>());
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, fg, block, run_smem_bytes<Real>());
-    *blocks_per_sm = bu < bg ? bu : bg;
+    int best = 1 << 30;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 4 && e == cudaSuccess; v++) {  // every (uniform, bonds) variant
+        void* fn = run_fn<Real>(v & 1, v >> 1);
+        int b = 0;
+        e = prepare_fn<Real>(fn);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, run_smem_bytes<Real>());
+        best = b < best ? b : best;
+    }
+    *blocks_per_sm = best;
     return e;
 }
 
 template <typename Real>
-static void* batch_fn(int uni)
+static void* batch_fn(int uni, int bonds = 0)
 {
-    return uni ? (void*)batched::k_batch<Real, true> : (void*)batched::k_batch<Real, false>;
+    if (bonds) return uni ? (void*)batched::k_batch<Real, true, true> : (void*)batched::k_batch<Real, false, true>;
+    return uni ? (void*)batched::k_batch<Real, true, false> : (void*)batched::k_batch<Real, false, false>;
 }
 
 template <typename Real>
@@ -74,9 +78,9 @@ static size_t batch_smem_bytes()
 
 template <typename Real>
 cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
-                         int uni, int grid, cudaStream_t s)
+                         int uni, int bonds, int grid, cudaStream_t s)
 {
-    void* fn = batch_fn<Real>(uni);
+    void* fn = batch_fn<Real>(uni, bonds);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<Real>());
     if (e != cudaSuccess) return e;
     void* kargs[] = {(void*)&devs, (void*)&args, (void*)&item_ofs, (void*)&items};
@@ -86,15 +90,17 @@ cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* 
 template <typename Real>
 cudaError_t batch_occupancy(int* blocks_per_sm)
 {
-    void* fu = batch_fn<Real>(1);
-    void* fg = batch_fn<Real>(0);
-    int bu = 0, bg = 0;
     const int sm = (int)batch_smem_bytes<Real>();
-    cudaError_t e = cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fg, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu, fu, kBlockBatch, sm);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, fg, kBlockBatch, sm);
-    *blocks_per_sm = bu < bg ? bu : bg;
+    int best = 1 << 30;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 4 && e == cudaSuccess; v++) {  // every (uniform, bonds) variant
+        void* fn = batch_fn<Real>(v & 1, v >> 1);
+        int b = 0;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBlockBatch, sm);
+        best = b < best ? b : best;
+    }
+    *blocks_per_sm = best;
     return e;
 }
 
@@ -160,7 +166,7 @@ cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* pa
     template cudaError_t launch_get_state<R>(const Dev<R>&, int, int, cudaStream_t);             \
     template cudaError_t launch_get_forces<R>(const Dev<R>&, int, cudaStream_t);                 \
     template cudaError_t launch_get_nlist<R>(const Dev<R>&, int, int*, int*, int, cudaStream_t); \
-    template cudaError_t launch_batch<R>(const Dev<R>*, const RunArgs*, const int*, const int4*, int, int,   \
+    template cudaError_t launch_batch<R>(const Dev<R>*, const RunArgs*, const int*, const int4*, int, int, int, \
                                          cudaStream_t);                                                   \
     template cudaError_t batch_occupancy<R>(int*);                                               \
     template cudaError_t launch_param_grad<R>(const Dev<R>&, int, double*, double*, double, double, double, \

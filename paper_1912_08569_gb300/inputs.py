@@ -228,3 +228,64 @@ def dumbbell_workload(seed: int = 1, kT: float = 0.03, n_a: int = 600, n_b: int 
     return dict(name="dumbbell", n=N, density=density, box=box, x=x, v=v, types=types, mass=mass,
                 tags=np.arange(N, dtype=np.uint32), n_types=2, pairs=pairs, kT=kT, gamma=1.0, dt=0.001,
                 skin=0.3, seed=seed)
+
+
+def vitrimer_workload(n_total: int = 2_000_000, chain_len: int = 50, per_chain_a: int = 5, density: float = 0.85,
+                      kT: float = 0.5, seed: int = 1, kbond: float = 100.0, r0: float = 1.0, lambda3: float = 1.0):
+    """A vitrimer-like network: linear chains of chain_len beads joined by
+    harmonic bonds (kbond, r0), per_chain_a of each chain's beads reactive
+    (type A = 0), as many free crosslinkers (type B = 1), the other chain beads
+    plain (type C = 2).  A-B: the swap pair (n = 10, r_cut = 1.5, lambda3); every
+    other pair: WCA (sigma = eps = 1); the bonded pairs keep their WCA.
+
+    Start: a simple cubic lattice filling the box at the given density,
+    visited along a boustrophedon path (consecutive sites are lattice
+    neighbours); each chain takes chain_len consecutive sites followed by its
+    per_chain_a crosslinkers, so the crosslinkers are spread through the
+    melt.  The A beads are drawn per chain (seeded).  Returns the usual
+    workload dict plus "bonds" [m, 2] (tags) and the bond constants.
+    """
+    rng = np.random.Generator(np.random.Philox(seed))
+    unit = chain_len + per_chain_a
+    n_chains = max(1, n_total // unit)
+    N = n_chains * unit
+    box = cubic_box(N, density)
+    L = box[0]
+    m = int(np.ceil(N ** (1.0 / 3.0) - 1e-9))
+    a = L / m
+    # boustrophedon order of the m^3 sites
+    sites = []
+    for z in range(m):
+        ys = range(m) if z % 2 == 0 else range(m - 1, -1, -1)
+        for k, y in enumerate(ys):
+            xs = range(m) if (z * m + k) % 2 == 0 else range(m - 1, -1, -1)
+            for x in xs:
+                sites.append((x, y, z))
+                if len(sites) == N:
+                    break
+            if len(sites) == N:
+                break
+        if len(sites) == N:
+            break
+    pos = f32((np.asarray(sites, dtype=np.float64) + 0.5) * a)
+    types = np.full(N, 2, dtype=np.int32)
+    bonds = []
+    for c in range(n_chains):
+        base = c * unit
+        bonds.extend([(base + i, base + i + 1) for i in range(chain_len - 1)])
+        reactive = rng.choice(chain_len, size=per_chain_a, replace=False)
+        types[base + reactive] = 0
+        types[base + chain_len: base + unit] = 1
+    mass = np.ones(N)
+    v = maxwell_velocities(N, kT, mass, seed=seed + 1000)
+    sw = dict(kind=2, eps=1.0, sigma=1.0, n=10, rcut=1.5, lambda3=lambda3, shift=0,
+              rbond=((1.0 - np.sqrt(0.5)) / 2.0) ** (-1.0 / 10))
+    wca = dict(kind=1, eps=1.0, sigma=1.0, n=6)
+    pairs = {(0, 1): sw}
+    for ti in range(3):
+        for tj in range(ti, 3):
+            if (ti, tj) != (0, 1):
+                pairs[(ti, tj)] = wca
+    return dict(name="vitrimer", n=N, density=density, box=box, x=pos, v=v, types=types, mass=mass,
+                tags=np.arange(N, dtype=np.uint32), n_types=3, pairs=pairs, kT=kT, gamma=1.0, dt=0.001, skin=0.3,
+                seed=seed, bonds=np.asarray(bonds, dtype=np.int32), kbond=kbond, r0=r0)

@@ -94,6 +94,10 @@ class SwapSystem:
                           cv(img, np.int32)]
         A.swp_set_state(self.ctx, *self._keep, where=where)
 
+    def set_bonds(self, bonds, k: float, r0: float):
+        """Harmonic bonds k/2 (r - r0)^2 between tag pairs (an [m, 2] array)."""
+        A.swp_set_bonds(self.ctx, bonds, k, r0)
+
     def set_step(self, step: int):
         A.swp_set_step(self.ctx, step)
 
