@@ -47,7 +47,7 @@ def _args():
     ap.add_argument("--lam", type=float, default=1.0)
     ap.add_argument("--md-steps", type=int, default=None,
                     help="time steps per launch (default 1000; 5000 for batch256)")
-    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--particles", "--n", dest="n", type=int, default=100_000)
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -67,6 +67,23 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value, device):
+    """The largest value over the ranks of the default process group (the
+    value itself without one): timed regions are reported as the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, steps_per_launch, launches, total_ms):
+    """Whole-job rate: every rank's units times steps over the slowest rank's time."""
+    return world * units_per_rank * steps_per_launch * launches / (total_ms / 1e3)
 
 
 def _workload(n, lam, rank):
@@ -313,12 +330,9 @@ def run_ours(a):
     total_ms = float(np.sum(launch_ms))
     assert th1["step"] - th0["step"] == a.steps * a.md_steps, "timed launches did not complete"
     rebuilds = (th1["n_rebuilds"] - th0["n_rebuilds"]) / a.steps
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / a.steps
-    value = world * n * a.md_steps * a.steps / (total_ms / 1e3)
+    value = job_throughput(world, n, a.md_steps, a.steps, total_ms)
 
     # roofline of the persistent step kernel (the only kernel in the timed region)
     peak, peak_kind = _peaks()
@@ -349,10 +363,8 @@ def run_ours(a):
             el = time.perf_counter() - t0
             if k >= a.warmup:
                 times.append(el)
-        tt = torch.tensor([float(np.sum(times))], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * n * a.md_steps * a.steps / float(tt.item()), "unit": UNIT,
+        e2e_ms = 1e3 * max_over_ranks(float(np.sum(times)), dev)
+        e2e = {"value": job_throughput(world, n, a.md_steps, a.steps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": CTL_BYTES,
                "last_U": float(rec.U2 + rec.U3)}
 
@@ -450,12 +462,9 @@ def run_batch(a):
     batch.sync()
     clk = clocks.stop() if clocks else None
     launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    t = torch.tensor([float(np.sum(launch_ms))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(launch_ms)), dev)
     n_total = float(ns.sum())
-    value = world * n_total * a.md_steps * a.steps / (total_ms / 1e3)
+    value = job_throughput(world, n_total, a.md_steps, a.steps, total_ms)
     reb = (np.array([s.thermo()["n_rebuilds"] for s in systems]) - reb0) / a.steps
     peak, peak_kind = _peaks()
     b_alg = float(np.sum([algorithmic_bytes(n, a.md_steps, x, y, r) for n, x, y, r in zip(ns, nn, nn_r, reb)]))
@@ -480,7 +489,8 @@ def run_batch(a):
                 A.swp_read_thermo(s.ctx)
             if k >= a.warmup:
                 times.append(time.perf_counter() - t0)
-        e2e = {"value": world * n_total * a.md_steps * a.steps / float(np.sum(times)), "unit": UNIT,
+        e2e_ms = 1e3 * max_over_ranks(float(np.sum(times)), dev)
+        e2e = {"value": job_throughput(world, n_total, a.md_steps, a.steps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": CTL_BYTES * len(systems)}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -666,11 +676,8 @@ def run_vitrimer(a):
     th1 = s.thermo()
     clk = clocks.stop() if clocks else None
     launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    t = torch.tensor([float(np.sum(launch_ms))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * n * a.md_steps * a.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(np.sum(launch_ms)), dev)
+    value = job_throughput(world, n, a.md_steps, a.steps, total_ms)
     rebuilds = (th1["n_rebuilds"] - th0["n_rebuilds"]) / a.steps
     # the pair path's bytes plus, per particle-step, the bonds: partner tags (16),
     # their slots (8) and positions (32)
