@@ -435,7 +435,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total)
 }
 
 // ---------------------------------------------------------------------------
-// Neighbour-list rebuild phases (K-a): bin by cell, counting sort with a
+// Neighbour-list rebuild phases: bin by cell, counting sort with a
 // deterministic order inside each cell, gather every per-particle array into
 // the sorted order, then one row per particle from the 27-cell stencil.
 
@@ -590,7 +590,7 @@ __device__ __forceinline__ void block_range(const Dev<Real>& d, int& b0, int& b1
     b1 = min(b0 + Pb, d.n);
 }
 
-// Builds the block's entries (K-a, last step), one warp per cell: the warp
+// Builds the block's entries (last rebuild phase), one warp per cell: the warp
 // loads the 27 stencil ranges of its cell once, then tests its member
 // particles against the candidates 32 at a time with warp ballots.  A
 // counting sweep, a block scan that places every particle's runs (reactive
@@ -809,7 +809,7 @@ __device__ __forceinline__ void cp_async_r4(R4* smem, const R4* gmem)
 }
 
 // ---------------------------------------------------------------------------
-// S pass (K-b1): S_i = sum over reactive partners k inside r_cut of a vh(r_ik).
+// S pass: S_i = sum over reactive partners k inside r_cut of a vh(r_ik).
 
 // staged: the block has one sub-chunk and the shared copies of its positions
 // and list ranges are current (kept by the previous force pass), so they are
@@ -887,7 +887,7 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
 }
 
 // ---------------------------------------------------------------------------
-// Force pass (K-b2) fused with the integrator (K-c).
+// Force pass fused with the integrator.
 //
 // flags: closing = finish the current step with the second half kick;
 //        opening = start the next step: half kick, half drift, (Langevin O),
