@@ -228,6 +228,24 @@ def cpu_oracle_sample(wl, seconds, steps_cap=200):
     return wl["n"] * nsteps / el, nsteps, el
 
 
+def accuracy_vs_oracle(oracle, s, wl):
+    """Error of the GPU's forces and thermo record on a snapshot of the run
+    against the FP64 oracle at the same positions (FP32 decisions), per
+    quantity, relative to the oracle's error scales."""
+    s.compute_forces()
+    x, _, _ = s.state()
+    F = s.forces()
+    th = s.thermo()
+    ref = oracle.forces(x, wl["types"], wl["n_types"], oracle.pair_table(wl["n_types"], wl["pairs"]), wl["box"],
+                        fp32=True)
+    ferr = np.linalg.norm(F - ref["F"], axis=1) / np.maximum(ref["fscale"], 1e-300)
+    return {"F_max_err_over_scale": float(ferr.max()),
+            "U2_err_over_scale": abs(th["U2"] - ref["U2"]) / ref["scale_U2"],
+            "U3_err_over_scale": abs(th["U3"] - ref["U3"]) / max(ref["scale_U3"], 1e-300),
+            "W_max_err_over_scale": float(np.max(np.abs(th["W"] - ref["W"]))) / ref["scale_W"],
+            "n_bonds_diff": int(th["n_bonds"] - ref["n_bonds"]), "tolerance": 1e-5}
+
+
 def run_reference(a):
     rank, world, _ = _dist()
     if rank != 0:
@@ -376,7 +394,8 @@ def run_ours(a):
         v, steps_done, el = cpu_oracle_sample(wl, a.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"N={n}, {steps_done} BAOAB steps of the FP64 C oracle (explicit triplet "
-                         f"loop, cell list every step), {el:.1f} s, 1 thread"}
+                         f"loop, cell list every step), {el:.1f} s, 1 thread",
+               "accuracy": accuracy_vs_oracle(oracle, s, wl)}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
