@@ -56,3 +56,14 @@ def test_relaxation_time_order_of_paper(runs):
 def test_kernel_bond_count_matches_positions(runs):
     for r in runs.values():
         assert r["bond_count_diff"] <= 1
+
+
+def test_light_partners_swap_faster():
+    """Half of the A particles at mass 1/10: their bonds relax faster than those
+    of the heavy A (the paper: 60 against 98 at kT = 0.03)."""
+    from paper_1912_08569_gb300 import validation
+
+    r = validation.run(kT=0.03, replicas=4, t_max=200.0, light_mass=0.1)
+    light, heavy = r["mass_split"]["light"], r["mass_split"]["heavy"]
+    assert light["tau"] < heavy["tau"], (light["tau"], heavy["tau"])
+    assert r["bonded_fraction_min"] >= 0.99
