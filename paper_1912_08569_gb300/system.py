@@ -72,7 +72,8 @@ class SwapSystem:
         self._bind_nlist()
         self.grows += 1
 
-    def set_launch(self, lanes: int, blocks_per_sm: int = 0):
+    def set_launch(self, blocks_per_sm: int = 0):
+        """Resident step-kernel blocks per SM (0: as many as fit)."""
         A.swp_set_launch(self.ctx, blocks_per_sm)
 
     def set_timeout(self, ns: int):
