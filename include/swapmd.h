@@ -246,6 +246,15 @@ SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev,
  * follows the grid). */
 SWP_API int swp_set_launch(swp_ctx* ctx, int blocks_per_sm);
 
+/* Upper bound on the step kernel's blocks (0, the default: the resident
+ * blocks of every SM).  The step's work is spread over the blocks and every
+ * time step passes two grid-wide barriers, whose cost grows with the number
+ * of blocks: a system of a few thousand particles runs faster on fewer
+ * blocks (one block: no grid barrier at all).  Results do not depend on it
+ * beyond the order of floating-point sums.  Negative: SWP_ERR_INVALID.
+ * Changing it marks the list stale (its block partition follows the grid). */
+SWP_API int swp_set_grid(swp_ctx* ctx, int blocks);
+
 /* Bound, in nanoseconds, on every device-side wait (default 2 s). */
 SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);
 

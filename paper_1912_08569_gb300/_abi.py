@@ -46,7 +46,7 @@ EXPORTS = (
     "swp_abi_version", "swp_create", "swp_set_pair", "swp_set_nlist", "swp_workspace_size",
     "swp_nlist_size", "swp_bind_workspace", "swp_bind_nlist", "swp_set_state", "swp_set_step",
     "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
-    "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch",
+    "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch", "swp_set_grid",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
     "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds",
 )
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "swp_read_state": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int], c_int),
         "swp_read_nlist": ([c_void_p, c_void_p, c_void_p, c_int], c_int),
         "swp_set_launch": ([c_void_p, c_int], c_int),
+        "swp_set_grid": ([c_void_p, c_int], c_int),
         "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
@@ -246,6 +247,10 @@ def swp_read_nlist(ctx, rows_dev, counts_dev, width: int):
 
 def swp_set_launch(ctx, blocks_per_sm: int = 0):
     return _check(ctx, load_library().swp_set_launch(ctx, int(blocks_per_sm)), "swp_set_launch")
+
+
+def swp_set_grid(ctx, blocks: int = 0):
+    return _check(ctx, load_library().swp_set_grid(ctx, int(blocks)), "swp_set_grid")
 
 
 def swp_set_timeout(ctx, ns: int):

@@ -45,7 +45,7 @@ struct swp_ctx {
     int nc[3] = {3, 3, 3};
     int ncell = 27;
     int device = 0, num_sms = 0;
-    int bps_req = 0, grid = 0, max_blocks = 0;
+    int bps_req = 0, grid_req = 0, grid = 0, max_blocks = 0;
     long long timeout_ns = 2000000000LL;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -441,6 +441,14 @@ int prepare_args(swp_ctx* c, RunArgs& a)
     return SWP_OK;
 }
 
+// Blocks of the step kernel: the resident blocks of every SM, or fewer on
+// request (a small system spends less on its grid barriers with fewer blocks).
+int step_grid(const swp_ctx* c, int bps)
+{
+    const int g = c->num_sms * bps;
+    return c->grid_req > 0 ? std::min(g, c->grid_req) : g;
+}
+
 template <typename Real>
 int run(swp_ctx* c, RunArgs a)
 {
@@ -450,7 +458,7 @@ int run(swp_ctx* c, RunArgs a)
     if (bps < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
     if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
     bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
-    c->grid = c->num_sms * bps;
+    c->grid = step_grid(c, bps);
     int rc = prepare_args<Real>(c, a);
     if (rc) return rc;
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
@@ -1130,6 +1138,15 @@ int swp_set_launch(swp_ctx* c, int blocks_per_sm)
     return SWP_OK;
 }
 
+int swp_set_grid(swp_ctx* c, int blocks)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (blocks < 0) return fail(c, SWP_ERR_INVALID, "blocks must be >= 0");
+    c->grid_req = blocks;
+    if (c->ws_bound && c->state_set && c->n > 0) return mark_stale(c);
+    return SWP_OK;
+}
+
 int swp_set_timeout(swp_ctx* c, int64_t ns)
 {
     if (!c) return SWP_ERR_INVALID;
@@ -1277,7 +1294,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     a.timeout_ns = c->timeout_ns;
     a.skin_eff = c->skin;
     a.seed = c->seed;
-    SWP_CUDA(c, launch_run<Real>(d, a, c->num_sms * bps, kBlock, s));
+    SWP_CUDA(c, launch_run<Real>(d, a, step_grid(c, bps), kBlock, s));
     SWP_CUDA(c, cudaMemcpyAsync(&h, d.ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
     SWP_CUDA(c, cudaStreamSynchronize(s));
     if (h.status & kStatusTimeout) return fail(c, SWP_ERR_TIMEOUT, "a device-side wait timed out");

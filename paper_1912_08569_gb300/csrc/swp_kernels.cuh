@@ -313,7 +313,7 @@ __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_
             if (m) atomicMax(pub_dst, m);
             *pub_src = 0u;
         }
-        if (kBatched && g_size() == 1) return;  // a group of one block: __syncthreads is the barrier
+        if (g_size() == 1) return;  // a group of one block: __syncthreads is the barrier
         b.target += g_size();
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
     }
@@ -1347,7 +1347,7 @@ __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
     }
 }
 
-// The same reduction for a group of fewer than kNQA blocks (batched runs):
+// The same reduction for a group of fewer than kNQA blocks:
 // rank 0 alone, warp q summing quantity q over the group's blocks in order.
 template <typename Real>
 __device__ __forceinline__ void reduce_small(const Dev<Real>& d, const RunArgs& a, int par)
@@ -1414,9 +1414,9 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ, s_red);
     // groups of at least kNQA blocks: one quantity per block, asynchronously;
     // smaller groups reduce every quantity here
-    const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
+    const bool red = had && g_size() >= kNQA && g_rank() < kNQA;
     if (red) reduce_issue(d, a, prev);
-    if (kBatched && had && g_size() < kNQA) reduce_small(d, a, prev);
+    if (had && g_size() < kNQA) reduce_small(d, a, prev);
     if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
         s_ls.bar_target = bs.target;
         s_ls.parity = par;
@@ -1556,7 +1556,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
     if (s_ls.have_thermo) {
         // the last pass's partials were written after its barrier's arrival
         if (!grid_barrier(ctl, a.timeout_ns, 30)) return false;
-        if (kBatched && g_size() < kNQA)
+        if (g_size() < kNQA)
             reduce_small(d, a, s_ls.parity);
         else
             run_reduce_thermo(d, a, s_ls.parity);

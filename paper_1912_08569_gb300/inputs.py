@@ -171,6 +171,52 @@ def batch_workload(n_systems: int = 256, seed: int = 7, n_min: int = 1000, n_max
     return out
 
 
+class _SeparationGrid:
+    """Points laid down one by one with a minimum separation dmin (minimum
+    image): far(c) tells whether c is at least dmin from every point added so
+    far, looking only at the 27 cells around c (cells at least dmin wide), so
+    that it gives the same answer as a check against every point."""
+
+    def __init__(self, box, dmin):
+        self.box = np.asarray(box, dtype=np.float64)
+        self.dmin2 = dmin * dmin
+        self.m = np.floor(self.box / (dmin * (1.0 + 1e-6))).astype(np.int64)
+        self.use_cells = bool(np.all(self.m >= 3))
+        self.cells = {}
+        self.all = []
+
+    def _cell(self, c):
+        return tuple(int(k) for k in np.minimum((c / self.box * self.m).astype(np.int64), self.m - 1))
+
+    def far(self, c):
+        if not self.all:
+            return True
+        if self.use_cells:
+            cx, cy, cz = self._cell(c)
+            mx, my, mz = (int(v) for v in self.m)
+            near = []
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        near.extend(self.cells.get(((cx + dx) % mx, (cy + dy) % my, (cz + dz) % mz), ()))
+            if not near:
+                return True
+            others = np.array(near, dtype=np.float64)
+        else:
+            others = np.array(self.all, dtype=np.float64)
+        d = others - c
+        d -= self.box * np.round(d / self.box)
+        return np.min(np.sum(d * d, axis=1)) >= self.dmin2
+
+    def add(self, c):
+        self.all.append(c)
+        if self.use_cells:
+            self.cells.setdefault(self._cell(c), []).append(c)
+
+    def points(self):
+        return np.array(self.all, dtype=np.float64).reshape(-1, 3)
+
+
 def dumbbell_workload(seed: int = 1, kT: float = 0.03, n_a: int = 600, n_b: int = 400, density: float = 0.125,
                       n: int = 100, rcut: float = 1.3, lambda3: float = 1.0):
     """The dumbbell mixture of section "Effect of swaps": n_a A and n_b B
@@ -187,21 +233,12 @@ def dumbbell_workload(seed: int = 1, kT: float = 0.03, n_a: int = 600, n_b: int 
     box = cubic_box(N, density)
     L = box[0]
     rmin = 2.0 ** (1.0 / n)
-    pts = []
-    tree_pts = np.zeros((0, 3))
-
-    def far(c, others):
-        if len(others) == 0:
-            return True
-        d = others - c
-        d -= box * np.round(d / box)
-        return np.min(np.sum(d * d, axis=1)) >= 1.0
-
+    grid = _SeparationGrid(box, 1.0)
     types = []
     tries = 0
     while len(types) < N:
         tries += 1
-        if tries > 200000:
+        if tries > 200000 + 20 * N:
             raise RuntimeError("dumbbell_workload: could not place particles")
         a = f32(rng.random(3) * box)
         a[a >= box] = 0.0
@@ -211,16 +248,17 @@ def dumbbell_workload(seed: int = 1, kT: float = 0.03, n_a: int = 600, n_b: int 
             u /= np.linalg.norm(u)
             b = f32(np.mod(a + rmin * u, L))
             b[b >= box] = 0.0
-            if not (far(a, tree_pts) and far(b, tree_pts)):
+            if not (grid.far(a) and grid.far(b)):
                 continue
-            tree_pts = np.concatenate([tree_pts, a[None], b[None]])
+            grid.add(a)
+            grid.add(b)
             types += [0, 1]
         else:
-            if not far(a, tree_pts):
+            if not grid.far(a):
                 continue
-            tree_pts = np.concatenate([tree_pts, a[None]])
+            grid.add(a)
             types.append(0)
-    x = tree_pts
+    x = grid.points()
     types = np.asarray(types, dtype=np.int32)
     mass = np.ones(N)
     v = maxwell_velocities(N, kT, mass, seed=seed + 1000)

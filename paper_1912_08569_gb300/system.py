@@ -76,6 +76,10 @@ class SwapSystem:
         """Resident step-kernel blocks per SM (0: as many as fit)."""
         A.swp_set_launch(self.ctx, blocks_per_sm)
 
+    def set_grid(self, blocks: int = 0):
+        """Upper bound on the step kernel's blocks (0: every SM's resident blocks)."""
+        A.swp_set_grid(self.ctx, blocks)
+
     def set_timeout(self, ns: int):
         A.swp_set_timeout(self.ctx, ns)
 
