@@ -47,16 +47,21 @@ def _args():
     ap.add_argument("--lam", type=float, default=1.0)
     ap.add_argument("--md-steps", type=int, default=None,
                     help="time steps per launch (default 1000; 5000 for batch256)")
-    ap.add_argument("--particles", "--n", dest="n", type=int, default=100_000)
+    ap.add_argument("--particles", "--n", dest="n", type=int, default=None,
+                    help="particles (default 100,000; 16,384 for dumbbell)")
+    ap.add_argument("--rcut", type=float, default=1.3, help="A-B cut-off of the dumbbell workload")
+    ap.add_argument("--grid", type=int, default=0, help="step-kernel blocks (0: every SM)")
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="mix100k", choices=["mix100k", "batch256", "diff20k", "vitrimer2m"],
+    ap.add_argument("--workload", default="mix100k",
+                    choices=["mix100k", "batch256", "diff20k", "vitrimer2m", "dumbbell"],
                     help="mix100k: the single 100k-particle system (default); batch256: 256 "
                          "independent systems of 1k-32k particles in one launch per step; diff20k: "
                          "force-matching gradient over 64 snapshots of 20k particles; vitrimer2m: "
-                         "2M-bead bonded network with swapping crosslinkers")
+                         "2M-bead bonded network with swapping crosslinkers; dumbbell: the paper's "
+                         "timing system (dumbbell mixture, n=100) at --particles and --rcut")
     ap.add_argument("--snapshots", type=int, default=64)
     ap.add_argument("--systems", type=int, default=256)
     return ap.parse_args()
@@ -90,6 +95,16 @@ def _workload(n, lam, rank):
     from paper_1912_08569_gb300 import inputs
 
     return inputs.workload("mix100k", lambda3=lam, n=n, seed=1 + rank)
+
+
+def _dumbbell(n, rcut, rank):
+    """The paper's timing system: n particles, A:B = 3:2 as in the 600 + 400
+    dumbbell mixture, every B bonded to an A at the start, density 0.125, A-B
+    swap pair n=100 with cut-off rcut (1.3 or 1.15), BAOAB kT=0.03."""
+    from paper_1912_08569_gb300 import inputs
+
+    na = (3 * n) // 5
+    return inputs.dumbbell_workload(seed=1 + rank, kT=0.03, n_a=na, n_b=n - na, rcut=rcut)
 
 
 def _config(a, n, world):
@@ -253,6 +268,8 @@ def run_reference(a):
     import oracle
 
     oracle.build()
+    if a.workload == "dumbbell":
+        return run_reference_dumbbell(a, oracle)
     wl = _workload(a.n, a.lam, 0)
     tab = oracle.pair_table(wl["n_types"], wl["pairs"])
     t0 = time.perf_counter()
@@ -306,6 +323,8 @@ def run_ours(a):
     s = SwapSystem(n, 2, wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"],
                    blocks_per_sm=a.bps)
     s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
+    if a.grid:
+        s.set_grid(a.grid)
     s.compute_forces()
     _, counts = s.nlist()
     nn = float(counts[:, 1].mean())
@@ -727,10 +746,146 @@ def run_vitrimer(a):
     return 0
 
 
+DUMB_METRIC = "dumbbell-mixture particle-timesteps/s (the paper's timing system, n=100; FP32)"
+
+
+def _dumb_config(a, n, world):
+    return {"workload": f"dumbbell: N={n}, A:B 3:2 (every B bonded at the start), density 0.125, n=100, "
+                        f"r_cut={a.rcut:g}, lambda=1, WCA A-A and B-B, BAOAB kT=0.03 gamma=1 dt=0.001, skin 0.3",
+            "n_particles": n, "r_cut": a.rcut, "md_steps_per_step": a.md_steps, "grid": a.grid or "all SMs",
+            "l2": "flushed (512 MB write) between timed launches", "parallelism": f"replicas x{world}"}
+
+
+def run_reference_dumbbell(a, oracle):
+    """The oracle on the dumbbell workload: bounded samples, one thread."""
+    wl = _dumbbell(a.n, a.rcut, 0)
+    tab = oracle.pair_table(wl["n_types"], wl["pairs"])
+    t0 = time.perf_counter()
+    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True)
+    t_force = time.perf_counter() - t0
+    per = int(max(1, min(500, 4.0 / max(t_force, 1e-6))))
+    x, v = wl["x"], wl["v"]
+    times = []
+    for k in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        x, v, _, _ = oracle.run(x, v, wl["types"], wl["mass"], wl["tags"], wl["n_types"], tab, wl["box"],
+                                wl["dt"], per, kT=wl["kT"], gamma=wl["gamma"], seed=wl["seed"], step0=k * per,
+                                fp32=True)
+        if k >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = wl["n"] * per / (ms / 1e3)
+    sample = f"N={wl['n']}, {per} BAOAB steps per step of the FP64 C oracle (1 thread)"
+    out = {"impl": "reference", "metric": DUMB_METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _dumb_config(a, wl["n"], 1), "timesteps_per_s": per / (ms / 1e3),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_dumbbell(a):
+    """The paper's timing system (a mixture of dumbbells, every particle
+    reactive or repelled, n = 100, r_cut 1.3 or 1.15) at a.n particles: one
+    bench step = one launch of the persistent step kernel over a.md_steps time
+    steps; also reported as time steps per second, the paper's measure."""
+    import torch
+
+    from paper_1912_08569_gb300 import SwapSystem
+    from paper_1912_08569_gb300.build import build
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    wl = _dumbbell(a.n, a.rcut, rank)
+    n = wl["n"]
+    s = SwapSystem(n, wl["n_types"], wl["box"], wl["pairs"], precision="fp32", seed=wl["seed"], skin=wl["skin"])
+    s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
+    s.set_grid(a.grid)
+    s.compute_forces()
+    dt, kT, gamma = wl["dt"], wl["kT"], wl["gamma"]
+    for _ in range(a.warmup):
+        s.run(a.md_steps, dt, kT, gamma)
+    _, counts = s.nlist()
+    nn, nn_r = float(counts[:, 1].mean()), float(counts[:, 0].mean())
+    th0 = s.thermo()
+    stream = s.stream
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(a.md_steps, dt, kT, gamma, sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    s.sync()
+    th1 = s.thermo()
+    clk = clocks.stop() if clocks else None
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    assert th1["step"] - th0["step"] == a.steps * a.md_steps, "timed launches did not complete"
+    total_ms = max_over_ranks(float(np.sum(launch_ms)), dev)
+    value = job_throughput(world, n, a.md_steps, a.steps, total_ms)
+    rebuilds = (th1["n_rebuilds"] - th0["n_rebuilds"]) / a.steps
+    b_alg = algorithmic_bytes(n, a.md_steps, nn, nn_r, rebuilds)
+    peak, peak_kind = _peaks()
+    achieved = b_alg / (float(np.mean(launch_ms)) / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        v, steps_done, el = cpu_oracle_sample(wl, a.cpu_seconds, steps_cap=2000)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "timesteps_per_s": v / n,
+               "sample": f"N={n}, {steps_done} BAOAB steps of the FP64 C oracle, {el:.1f} s, 1 thread",
+               "accuracy": accuracy_vs_oracle(oracle, s, wl)}
+    if rank == 0:
+        out = {"metric": DUMB_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _dumb_config(a, n, world),
+               "timesteps_per_s": a.md_steps * a.steps / (total_ms / 1e3),
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                            "alg_bytes_per_launch": b_alg, "nn_mean": nn, "nn_reactive_mean": nn_r,
+                            "rebuilds_per_launch": rebuilds},
+               "cpu_baseline": cpu, "e2e": None, "gpu_launches": a.steps, "clocks": clk,
+               "kernel_digest": _kernel_digest(),
+               "thermo_last": {"U2": th1["U2"], "U3": th1["U3"], "K": th1["K"], "n_bonds": th1["n_bonds"]}}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    s.close()
+    return 0
+
+
 def main():
     a = _args()
+    if a.n is None:
+        a.n = 16384 if a.workload == "dumbbell" else 100_000
     if a.md_steps is None:
-        a.md_steps = {"batch256": 5000, "vitrimer2m": 2000}.get(a.workload, 1000)
+        a.md_steps = {"batch256": 5000, "vitrimer2m": 2000, "dumbbell": 4000}.get(a.workload, 1000)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batch256":
@@ -739,6 +894,8 @@ def main():
         return run_diff(a)
     if a.workload == "vitrimer2m":
         return run_vitrimer(a)
+    if a.workload == "dumbbell":
+        return run_dumbbell(a)
     return run_ours(a)
 
 

@@ -95,7 +95,7 @@ typedef struct {
 SWP_API int swp_abi_version(void);
 
 /* Create a context for n particles of n_types types (1..8) in a periodic
- * orthorhombic box box[3] (> 0).  precision is SWP_FP32 or SWP_FP64; seed
+ * orthorhombic box box[3] (edges in [2^-8, 30000]).  precision is SWP_FP32 or SWP_FP64; seed
  * keys the Langevin noise.  In FP32 the box lengths are rounded to float32;
  * in both the box is then rounded to the 2^-48 fixed-point grid.  Uses the
  * current CUDA device.  n may be 0 (every call is then a no-op).  n < 2^27.
@@ -247,12 +247,13 @@ SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev,
 SWP_API int swp_set_launch(swp_ctx* ctx, int blocks_per_sm);
 
 /* Upper bound on the step kernel's blocks (0, the default: the resident
- * blocks of every SM).  The step's work is spread over the blocks and every
- * time step passes two grid-wide barriers, whose cost grows with the number
- * of blocks: a system of a few thousand particles runs faster on fewer
- * blocks (one block: no grid barrier at all).  Results do not depend on it
- * beyond the order of floating-point sums.  Negative: SWP_ERR_INVALID.
- * Changing it marks the list stale (its block partition follows the grid). */
+ * blocks of every SM); requests below 10 run on 10 blocks (one per thermo
+ * quantity reduced in parallel), or on every SM's if there are fewer.  A
+ * smaller grid leaves SMs free for other work on the device; the time per
+ * step of a small system hardly depends on it (each step's dependent phases,
+ * not the grid barriers, set it).  Results do not depend on it beyond the
+ * order of floating-point sums.  Negative: SWP_ERR_INVALID.  Changing it
+ * marks the list stale (its block partition follows the grid). */
 SWP_API int swp_set_grid(swp_ctx* ctx, int blocks);
 
 /* Bound, in nanoseconds, on every device-side wait (default 2 s). */

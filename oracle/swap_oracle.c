@@ -37,11 +37,21 @@
  *
  * Decisions that turn a distance into an integer (is a pair inside its
  * cut-off, inside the neighbour-list radius, inside the bond radius) can be
- * taken in FP32 (fp32 = 1): the minimum-image displacement and
- * d2 = (dx*dx + dy*dy) + dz*dz are evaluated in IEEE float, one rounding per
- * operation, no contraction (build with -ffp-contract=off), and compared with
- * the float of (cut*cut computed in double).  The values of the potential are
- * always evaluated in FP64 from the double displacement.
+ * taken in FP32 (fp32 = 1), on 32-bit fractions of the box edges:
+ *   - each box edge is rounded to float, then to the 2^-48 grid: Lq =
+ *     round(L 2^48) (halves away from zero), L' = Lq 2^-48;
+ *   - a coordinate x is wrapped and put on the same grid: k = floor(x / L'),
+ *     q = round-half-even((x - k L') 2^48), then q -= Lq if q >= Lq and
+ *     q += Lq if q < 0;
+ *   - its fraction is u = floor(q f / 2^64) with f = floor(2^96 / Lq);
+ *   - a displacement component is the difference u_j - u_i taken modulo
+ *     2^32 as a signed 32-bit integer (this is the minimum image), converted
+ *     to float and multiplied by the float of Lq 2^-80 (the edge per 2^32);
+ *   - d2 = (dx*dx + dy*dy) + dz*dz in IEEE float, one rounding per
+ *     operation, no contraction (build with -ffp-contract=off), compared with
+ *     the float of (cut*cut computed in double).
+ * The values of the potential are always evaluated in FP64 from the double
+ * displacement.
  *
  * Integrators: velocity Verlet (NVE) and BAOAB Langevin (NVT), Leimkuhler &
  * Matthews (2013).  The Langevin noise uses Philox4x32-10 (Salmon, Moraes,
@@ -170,33 +180,75 @@ static double wrap_d(double d, double L)
     return d;
 }
 
-static float wrap_f(float d, float L, float hL)
+/* What the decisions of one call need: the positions and box, and in FP32
+ * the box fractions of every coordinate (computed once). */
+typedef struct {
+    const double *x, *box;
+    int fp32;
+    uint32_t *u; /* [3n] */
+    float s[3];  /* float of Lq 2^-80 */
+} decider;
+
+/* 32-bit fraction of coordinate x along an edge of Lq grid units (the rule
+ * in the header). */
+static uint32_t box_fraction(double x, long long Lq, uint64_t f)
 {
-    if (d > hL)
-        return d - L;
-    if (d < -hL)
-        return d + L;
-    return d;
+    double L = (double)Lq * 0x1p-48;
+    double k = floor(x / L);
+    double xw = x - k * L;
+    long long q = llrint(xw * 0x1p48);
+    if (q >= Lq)
+        q -= Lq;
+    if (q < 0)
+        q += Lq;
+    return (uint32_t)(((unsigned __int128)(uint64_t)q * f) >> 64);
 }
 
-/* Squared minimum-image distance used for integer decisions. */
-static double decision_d2(const double *xi, const double *xj, const double *box, int fp32)
+static int decider_init(decider *dc, int n, const double *x, const double *box, int fp32)
 {
-    if (fp32) {
-        float dx = (float)xj[0] - (float)xi[0];
-        float dy = (float)xj[1] - (float)xi[1];
-        float dz = (float)xj[2] - (float)xi[2];
-        float Lx = (float)box[0], Ly = (float)box[1], Lz = (float)box[2];
-        dx = wrap_f(dx, Lx, 0.5f * Lx);
-        dy = wrap_f(dy, Ly, 0.5f * Ly);
-        dz = wrap_f(dz, Lz, 0.5f * Lz);
-        float s = dx * dx;
-        float t = dy * dy;
+    dc->x = x;
+    dc->box = box;
+    dc->fp32 = fp32;
+    dc->u = NULL;
+    if (!fp32)
+        return 0;
+    dc->u = (uint32_t *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(uint32_t));
+    if (!dc->u)
+        return -1;
+    for (int c = 0; c < 3; c++) {
+        long long Lq = llround((double)(float)box[c] * 0x1p48);
+        uint64_t f = (uint64_t)(((unsigned __int128)1 << 96) / (unsigned __int128)Lq);
+        dc->s[c] = (float)((double)Lq * 0x1p-80);
+        for (int i = 0; i < n; i++)
+            dc->u[3 * i + c] = box_fraction(x[3 * i + c], Lq, f);
+    }
+    return 0;
+}
+
+static void decider_free(decider *dc)
+{
+    free(dc->u);
+    dc->u = NULL;
+}
+
+/* Squared minimum-image distance of particles i and j used for integer
+ * decisions. */
+static double decision_d2(const decider *dc, int i, int j)
+{
+    if (dc->fp32) {
+        float d[3];
+        for (int c = 0; c < 3; c++) {
+            int32_t du = (int32_t)(dc->u[3 * j + c] - dc->u[3 * i + c]);
+            d[c] = (float)du * dc->s[c];
+        }
+        float s = d[0] * d[0];
+        float t = d[1] * d[1];
         s = s + t;
-        t = dz * dz;
+        t = d[2] * d[2];
         s = s + t;
         return (double)s;
     }
+    const double *xi = &dc->x[3 * i], *xj = &dc->x[3 * j], *box = dc->box;
     double dx = wrap_d(xj[0] - xi[0], box[0]);
     double dy = wrap_d(xj[1] - xi[1], box[1]);
     double dz = wrap_d(xj[2] - xi[2], box[2]);
@@ -257,8 +309,9 @@ static int pv_push(pairvec *v, int i, int j)
 /* All unordered pairs i<j whose squared decision distance is below the
  * pair type's cut2 (cut = pair cut-off + extra).  Returns 0 or -1 (memory). */
 static int find_pairs(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
-                      const double *box, int fp32, double extra, pairvec *out)
+                      const double *box, const decider *dc, double extra, pairvec *out)
 {
+    const int fp32 = dc->fp32;
     double cmax = 0.0;
     for (int t = 0; t < ntypes * ntypes; t++) {
         double c = pair_rcut(&tab[t]);
@@ -282,7 +335,7 @@ static int find_pairs(int n, const double *x, const int *type, int ntypes, const
                 double c = pair_rcut(p);
                 if (c <= 0.0)
                     continue;
-                if (decision_d2(&x[3 * i], &x[3 * j], box, fp32) < decision_cut2(c + extra, fp32))
+                if (decision_d2(dc, i, j) < decision_cut2(c + extra, fp32))
                     if (pv_push(out, i, j))
                         return -1;
             }
@@ -332,8 +385,7 @@ static int find_pairs(int n, const double *x, const int *type, int ntypes, const
                         double cut = pair_rcut(p);
                         if (cut <= 0.0)
                             continue;
-                        if (decision_d2(&x[3 * i], &x[3 * j], box, fp32) <
-                            decision_cut2(cut + extra, fp32))
+                        if (decision_d2(dc, i, j) < decision_cut2(cut + extra, fp32))
                             if (pv_push(out, i, j)) {
                                 free(head);
                                 free(next);
@@ -364,8 +416,13 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
                double *fscale)
 {
     pairvec pv = {0, 0, 0};
-    if (find_pairs(n, x, type, ntypes, tab, box, fp32, 0.0, &pv))
+    decider dc;
+    if (decider_init(&dc, n, x, box, fp32))
         return -1;
+    if (find_pairs(n, x, type, ntypes, tab, box, &dc, 0.0, &pv)) {
+        decider_free(&dc);
+        return -1;
+    }
     double U2 = 0, U3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
     double sU2 = 0, sU3 = 0, sW = 0;
     long nb = 0;
@@ -378,6 +435,7 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
     int *rcount = (int *)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
     if (!rcount) {
         free(pv.a);
+        decider_free(&dc);
         return -1;
     }
 
@@ -414,7 +472,7 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
         if (p->kind == ORC_KIND_SWAP) {
             rcount[i]++;
             rcount[j]++;
-            if (decision_d2(&x[3 * i], &x[3 * j], box, fp32) < decision_cut2(p->rbond, fp32))
+            if (decision_d2(&dc, i, j) < decision_cut2(p->rbond, fp32))
                 nb++;
         }
     }
@@ -430,6 +488,7 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
         free(rpart);
         free(rcount);
         free(pv.a);
+        decider_free(&dc);
         return -1;
     }
     rstart[0] = 0;
@@ -511,6 +570,7 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
     free(rpart);
     free(rcount);
     free(pv.a);
+    decider_free(&dc);
     return 0;
 }
 
@@ -573,7 +633,12 @@ int orc_nlist(int n, const double *x, const int *type, int ntypes, const orc_pai
               const double *box, int fp32, double skin, int maxn, int *counts, int *nbr)
 {
     pairvec pv = {0, 0, 0};
-    if (find_pairs(n, x, type, ntypes, tab, box, fp32, skin, &pv))
+    decider dc;
+    if (decider_init(&dc, n, x, box, fp32))
+        return -1;
+    int rc = find_pairs(n, x, type, ntypes, tab, box, &dc, skin, &pv);
+    decider_free(&dc);
+    if (rc)
         return -1;
     for (int i = 0; i < n; i++)
         counts[i] = 0;

@@ -176,8 +176,9 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     };
     Ctl* ctl = (Ctl*)take(sizeof(Ctl));
     PairP<Real>* table = (PairP<Real>*)take(sizeof(PairP<Real>) * kMaxTypes * kMaxTypes);
-    R4* pos0 = (R4*)take(sizeof(R4) * n);
-    R4* pos1 = (R4*)take(sizeof(R4) * n);
+    typedef typename Dev<Real>::P4 P4;
+    P4* pos0 = (P4*)take(sizeof(P4) * n);
+    P4* pos1 = (P4*)take(sizeof(P4) * n);
     long long* xq0 = (long long*)take(sizeof(long long) * 3 * n);
     long long* xq1 = (long long*)take(sizeof(long long) * 3 * n);
     int* img0 = (int*)take(sizeof(int) * 3 * n);
@@ -213,6 +214,8 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
             d->hL[k] = (Real)(0.5 * (double)(Real)L);
             d->inv_cw[k] = (Real)(c->nc[k] / L);
             d->iL[k] = (Real)(1.0 / (double)(Real)L);
+            d->fmul[k] = (unsigned long long)(((unsigned __int128)1 << 96) / (unsigned __int128)q);
+            d->fscale[k] = (float)((double)q * 0x1p-80);
         }
         d->pos[0] = pos0;
         d->pos[1] = pos1;
@@ -442,11 +445,11 @@ int prepare_args(swp_ctx* c, RunArgs& a)
 }
 
 // Blocks of the step kernel: the resident blocks of every SM, or fewer on
-// request (a small system spends less on its grid barriers with fewer blocks).
+// request, but at least kNQA (the thermo quantities are reduced one per block).
 int step_grid(const swp_ctx* c, int bps)
 {
     const int g = c->num_sms * bps;
-    return c->grid_req > 0 ? std::min(g, c->grid_req) : g;
+    return c->grid_req > 0 ? std::min(g, std::max(c->grid_req, kNQA)) : g;
 }
 
 template <typename Real>
@@ -636,7 +639,7 @@ int swp_create(swp_ctx** out, int n, int n_types, const double box[3], int preci
     if (n < 0 || n >= kMaxTag || n_types < 1 || n_types > kMaxTypes || !box) return SWP_ERR_INVALID;
     if (precision != SWP_FP32 && precision != SWP_FP64) return SWP_ERR_INVALID;
     for (int k = 0; k < 3; k++)
-        if (!(box[k] > 0.0) || !std::isfinite(box[k]) || box[k] > 30000.0) return SWP_ERR_INVALID;
+        if (!(box[k] >= 0x1p-8) || !std::isfinite(box[k]) || box[k] > 30000.0) return SWP_ERR_INVALID;
     swp_ctx* c = new swp_ctx();
     c->n = n;
     c->ntypes = n_types;

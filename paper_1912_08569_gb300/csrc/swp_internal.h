@@ -89,10 +89,25 @@ struct Vec4<double> {
     typedef dbl4 type;
 };
 
+// Position snapshot of one particle: FP64, (x, y, z, packed bits) in double;
+// FP32, (u, v, w, packed bits) with each coordinate a 32-bit fraction of its
+// box edge (see Dev::fmul).
+template <typename Real>
+struct PosVec;
+template <>
+struct PosVec<float> {
+    typedef int4 type;
+};
+template <>
+struct PosVec<double> {
+    typedef dbl4 type;
+};
+
 // Pointers and sizes of one context's device state (passed by value).
 template <typename Real>
 struct Dev {
     typedef typename Vec4<Real>::type R4;
+    typedef typename PosVec<Real>::type P4;
     int n;
     int ntypes;
     int max_nn;
@@ -103,7 +118,13 @@ struct Dev {
     Real inv_cw[3];  // cells per unit length
     Real iL[3];      // 1 / L
     long long Lq[3]; // box in fixed-point units
-    R4* pos[2];      // snapshot (x, y, z, packed tag/type bits), ping-pong
+    // FP32 snapshot coordinates: u = floor(q fmul / 2^64) with q the fixed-point
+    // coordinate and fmul = floor(2^96 / Lq), a 32-bit fraction of the box edge;
+    // a displacement is the wrap-around difference of two fractions (the
+    // minimum image) times fscale = Lq 2^-80, the box edge per 2^32
+    unsigned long long fmul[3];
+    float fscale[3];
+    P4* pos[2];      // snapshot (coordinates, packed tag/type bits), ping-pong
     long long* xq[2];  // fixed-point positions, SoA [3][n], two sets (reorder)
     int* img[2];       // image counts, SoA [3][n], two sets
     R4* vel[2];        // (vx, vy, vz, 1/m), two sets

@@ -94,6 +94,10 @@ __device__ __forceinline__ int packed_of(double w) { return (int)__double_as_lon
 __device__ __forceinline__ float pack_w(int v, float) { return __int_as_float(v); }
 __device__ __forceinline__ double pack_w(int v, double) { return __longlong_as_double((long long)v); }
 
+// Packed tag/type bits of a position snapshot.
+__device__ __forceinline__ int pos_bits(const int4& p) { return p.w; }
+__device__ __forceinline__ int pos_bits(const dbl4& p) { return packed_of(p.w); }
+
 // Fixed point <-> arithmetic precision.  FP32: through 32-bit halves (the
 // 64-bit conversions are slow on this part).  q = hi 2^32 + lo with hi and lo
 // converted exactly whenever q carries at most 24 significant bits (every
@@ -124,8 +128,38 @@ __device__ __forceinline__ const PairP<double>* uni_params(const RunArgs& a, dou
 __device__ __forceinline__ float pick(float, float f, double) { return f; }
 __device__ __forceinline__ double pick(double, float, double d) { return d; }
 
-template <typename R4>
-__device__ __forceinline__ int type_of(const R4& p) { return packed_of(p.w) & ((1 << kTypeBits) - 1); }
+template <typename P4>
+__device__ __forceinline__ int type_of(const P4& p) { return pos_bits(p) & ((1 << kTypeBits) - 1); }
+
+// Snapshot coordinate c of fixed-point coordinate q: FP32, the 32-bit box
+// fraction floor(q fmul / 2^64); FP64, the coordinate itself.
+__device__ __forceinline__ int snap_coord(long long q, int c, const Dev<float>& d)
+{
+    return (int)__umul64hi((unsigned long long)q, d.fmul[c]);
+}
+__device__ __forceinline__ double snap_coord(long long q, int, const Dev<double>&) { return fix_to_real(q, 0.0); }
+__device__ __forceinline__ int snap_bits(int b, const Dev<float>&) { return b; }
+__device__ __forceinline__ double snap_bits(int b, const Dev<double>&) { return pack_w(b, 0.0); }
+
+// FP32 minimum-image displacement of box fractions a -> b along c: the
+// wrap-around difference of the fractions (exact), converted and scaled with
+// one rounding each.
+__device__ __forceinline__ float frac_delta(int a, int b, int c, const Dev<float>& d)
+{
+    return __fmul_rn(__int2float_rn((int)((unsigned)b - (unsigned)a)), d.fscale[c]);
+}
+
+__device__ __forceinline__ float frac_dist2(const int4& pi, const int4& pj, const Dev<float>& d, float& dx,
+                                            float& dy, float& dz)
+{
+    dx = frac_delta(pi.x, pj.x, 0, d);
+    dy = frac_delta(pi.y, pj.y, 1, d);
+    dz = frac_delta(pi.z, pj.z, 2, d);
+    float s = mul_rn(dx, dx);
+    s = add_rn(s, mul_rn(dy, dy));
+    s = add_rn(s, mul_rn(dz, dz));
+    return s;
+}
 
 // Squared minimum-image distance of j from i, in the decision precision;
 // returns dx = x_j - x_i (wrapped) for the force evaluation.
@@ -166,6 +200,19 @@ __device__ __forceinline__ Real dist2_listed(const R4& pi, const R4& pj, const D
     s = add_rn(s, mul_rn(dy, dy));
     s = add_rn(s, mul_rn(dz, dz));
     return s;
+}
+
+// FP32 snapshots: one rule for every distance (the fraction difference is
+// already the minimum image).
+__device__ __forceinline__ float dist2(const int4& pi, const int4& pj, const Dev<float>& d, float& dx, float& dy,
+                                       float& dz)
+{
+    return frac_dist2(pi, pj, d, dx, dy, dz);
+}
+__device__ __forceinline__ float dist2_listed(const int4& pi, const int4& pj, const Dev<float>& d, float& dx,
+                                              float& dy, float& dz)
+{
+    return frac_dist2(pi, pj, d, dx, dy, dz);
 }
 
 template <typename Real>
@@ -313,7 +360,7 @@ __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_
             if (m) atomicMax(pub_dst, m);
             *pub_src = 0u;
         }
-        if (g_size() == 1) return;  // a group of one block: __syncthreads is the barrier
+        if (kBatched && g_size() == 1) return;  // a group of one block: __syncthreads is the barrier
         b.target += g_size();
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
     }
@@ -451,6 +498,14 @@ __device__ __forceinline__ void cell_coords(const Dev<Real>& d, const typename D
     cz = min(max(cz, 0), d.nc[2] - 1);
 }
 
+// FP32 snapshots: the cell of a box fraction u is floor(u nc / 2^32), exact.
+__device__ __forceinline__ void cell_coords(const Dev<float>& d, const int4& p, int& cx, int& cy, int& cz)
+{
+    cx = min((int)__umulhi((unsigned)p.x, (unsigned)d.nc[0]), d.nc[0] - 1);
+    cy = min((int)__umulhi((unsigned)p.y, (unsigned)d.nc[1]), d.nc[1] - 1);
+    cz = min((int)__umulhi((unsigned)p.z, (unsigned)d.nc[2]), d.nc[2] - 1);
+}
+
 template <typename Real>
 __device__ void ph_bin(const Dev<Real>& d, int pc, int t, int nt)
 {
@@ -555,9 +610,9 @@ __device__ void ph_gather(const Dev<Real>& d, int pc, int ac, int t, int nt)
     const int n = d.n;
     for (int q = t; q < n; q += nt) {
         int p = d.perm[q];
-        const typename Dev<Real>::R4 pp = d.pos[pc][p];
+        const typename Dev<Real>::P4 pp = d.pos[pc][p];
         d.pos[pc ^ 1][q] = pp;
-        if (d.has_bonds) d.slot_of_tag[packed_of(pp.w) >> kTypeBits] = q;
+        if (d.has_bonds) d.slot_of_tag[pos_bits(pp) >> kTypeBits] = q;
         d.vel[ac ^ 1][q] = d.vel[ac][p];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -599,7 +654,7 @@ __device__ __forceinline__ void block_range(const Dev<Real>& d, int& b0, int& b1
 // cnt: blockDim.x int2 of shared memory.  Returns the block's entry count
 // per particle (rounded up), the row length a capacity check needs.
 template <typename Real>
-__device__ __forceinline__ int rank_of(const Dev<Real>& d, const typename Dev<Real>::R4& p)
+__device__ __forceinline__ int rank_of(const Dev<Real>& d, const typename Dev<Real>::P4& p)
 {
     int cx, cy, cz;
     cell_coords(d, p, cx, cy, cz);
@@ -610,9 +665,9 @@ template <typename Real>
 __device__ int ph_build_cells(const Dev<Real>& d, const PairP<Real>* tab, int pc, int2* cnt,
                               int* sh, int* overflow)
 {
-    typedef typename Dev<Real>::R4 R4;
+    typedef typename Dev<Real>::P4 P4;
     constexpr int NCH = 4;  // candidate chunks of 32 held at once
-    const R4* pos = d.pos[pc];
+    const P4* pos = d.pos[pc];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     int b0, b1;
@@ -676,7 +731,7 @@ __device__ int ph_build_cells(const Dev<Real>& d, const PairP<Real>* tab, int pc
                     // Candidate tc lies in the range idx = number of ranges that end
                     // at or before it; every lane runs every shuffle (no divergence).
                     int cq[NCH];
-                    R4 cp[NCH];
+                    P4 cp[NCH];
                     int idx[NCH];
 #pragma unroll
                     for (int k = 0; k < NCH; k++) idx[k] = 0;
@@ -697,7 +752,7 @@ __device__ int ph_build_cells(const Dev<Real>& d, const PairP<Real>* tab, int pc
                     for (int k = 0; k < NCH; k++)
                         if (cq[k] >= 0) cp[k] = pos[cq[k]];
                     for (int i = m0; i < m1; i++) {
-                        const R4 pi = pos[i];
+                        const P4 pi = pos[i];
                         const int ti = type_of(pi);
                         int2 run = cnt[i - q0];
 #pragma unroll
@@ -762,10 +817,11 @@ extern __shared__ __align__(32) unsigned char g_dyn[];
 template <typename Real>
 struct Stage {
     typedef typename Dev<Real>::R4 R4;
+    typedef typename Dev<Real>::P4 P4;
     static constexpr int kWave = sizeof(Real) == 4 ? 8192 : 3072;
     static constexpr size_t B = kThreads;
-    static constexpr size_t O_POS = 0;                                  // [B] R4 positions
-    static constexpr size_t O_VEL = O_POS + B * sizeof(R4);             // [B] R4 velocities
+    static constexpr size_t O_POS = 0;                                  // [B] P4 positions
+    static constexpr size_t O_VEL = O_POS + B * sizeof(P4);             // [B] R4 velocities
     static constexpr size_t O_XQ = O_VEL + B * sizeof(R4);              // [3B] fixed-point positions
     static constexpr size_t O_INFO = O_XQ + 3 * B * sizeof(long long);  // [B] int4 pinfo
     static constexpr size_t O_S = O_INFO + B * sizeof(int4);            // [B] S
@@ -773,7 +829,7 @@ struct Stage {
     static constexpr size_t kBytes = O_W + (size_t)kWave * sizeof(R4);
     static size_t bytes(int) { return kBytes; }
 
-    static __device__ __forceinline__ R4* pos() { return (R4*)(g_dyn + O_POS); }
+    static __device__ __forceinline__ P4* pos() { return (P4*)(g_dyn + O_POS); }
     static __device__ __forceinline__ R4* vel() { return (R4*)(g_dyn + O_VEL); }
     static __device__ __forceinline__ long long* xq() { return (long long*)(g_dyn + O_XQ); }
     static __device__ __forceinline__ int4* info() { return (int4*)(g_dyn + O_INFO); }
@@ -820,8 +876,8 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
                              const PairP<Real>& ps, bool staged)
 {
     typedef Stage<Real> SM;
-    typedef typename Dev<Real>::R4 R4;
-    const R4* pos = d.pos[pc];
+    typedef typename Dev<Real>::P4 P4;
+    const P4* pos = d.pos[pc];
     int b0, b1;
     block_range(d, b0, b1);
     const int t = threadIdx.x;
@@ -850,13 +906,13 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
                 o_c = d.ent_o[e];
             }
             while (e < we) {
-                const R4 p_c = pos[j_c];
+                const P4 p_c = pos[j_c];
                 int j_n = 0, o_n = 0;
                 if (e + B < we) {
                     j_n = d.ent_j[e + B];
                     o_n = d.ent_o[e + B];
                 }
-                const R4 pi = SM::pos()[o_c];
+                const P4 pi = SM::pos()[o_c];
                 const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(p_c), d.ntypes, ps);
                 Real dx, dy, dz;
                 const Real r2 = dist2_listed(pi, p_c, d, dx, dy, dz);
@@ -921,10 +977,10 @@ __device__ __forceinline__ void load_pstate(const Dev<Real>& d, int ac, int i, i
 }
 
 // Adds a displacement to one fixed-point coordinate, wraps it into the box
-// (counting the image) and returns the new snapshot coordinate.
+// (counting the image) and returns the new fixed-point coordinate.
 template <typename Real>
-__device__ __forceinline__ Real advance_fix(const Dev<Real>& d, int ac, int i, int c, long long q0,
-                                            Real dx)
+__device__ __forceinline__ long long advance_fix(const Dev<Real>& d, int ac, int i, int c, long long q0,
+                                                 Real dx)
 {
     const int n = d.n;
     long long q = q0 + real_to_fix(dx);
@@ -937,7 +993,7 @@ __device__ __forceinline__ Real advance_fix(const Dev<Real>& d, int ac, int i, i
         d.img[ac][c * n + i] -= 1;
     }
     d.xq[ac][c * n + i] = q;
-    return fix_to_real(q, Real(0));
+    return q;
 }
 
 // Advances particle i given its force.  Returns the squared displacement of
@@ -946,9 +1002,10 @@ template <typename Real>
 __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs& a, int pc,
                                                int ac, int i, Real fx, Real fy, Real fz,
                                                int flags, long long step, PState<Real>& st,
-                                               Real wbits, Real& kin, typename Dev<Real>::R4* keep)
+                                               int wbits, Real& kin, typename Dev<Real>::P4* keep)
 {
     typedef typename Dev<Real>::R4 R4;
+    typedef typename Dev<Real>::P4 P4;
     R4 v = st.v;
     const Real im = v.w;
     const Real hdt = pick(Real(0), a.hdt_f, a.hdt_d);
@@ -966,7 +1023,7 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         Real ddx = hdt * v.x, ddy = hdt * v.y, ddz = hdt * v.z;
         if (a.langevin) {
             Real z[3];
-            normals3(a.seed, step, (unsigned)(packed_of(wbits) >> kTypeBits), z);
+            normals3(a.seed, step, (unsigned)(wbits >> kTypeBits), z);
             const Real c1 = pick(Real(0), a.c1_f, a.c1_d);
             const Real sd = pick(Real(0), a.c2_f, a.c2_d) * sqrt(im);
             v.x = c1 * v.x + sd * z[0];
@@ -977,11 +1034,11 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         ddy += hdt * v.y;
         ddz += hdt * v.z;
         disp2 = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
-        R4 np;
-        np.x = advance_fix(d, ac, i, 0, st.q[0], ddx);
-        np.y = advance_fix(d, ac, i, 1, st.q[1], ddy);
-        np.z = advance_fix(d, ac, i, 2, st.q[2], ddz);
-        np.w = wbits;
+        P4 np;
+        np.x = snap_coord(advance_fix(d, ac, i, 0, st.q[0], ddx), 0, d);
+        np.y = snap_coord(advance_fix(d, ac, i, 1, st.q[1], ddy), 1, d);
+        np.z = snap_coord(advance_fix(d, ac, i, 2, st.q[2], ddz), 2, d);
+        np.w = snap_bits(wbits, d);
         d.pos[pc ^ 1][i] = np;
         if (keep) *keep = np;
     }
@@ -995,8 +1052,8 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
 // purely two-body pair.
 template <typename Real, bool UNI, bool REACT>
 __device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real>* tab,
-                                            const typename Dev<Real>::R4& pi,
-                                            const typename Dev<Real>::R4& pj, Real Si, Real Sj,
+                                            const typename Dev<Real>::P4& pi,
+                                            const typename Dev<Real>::P4& pj, Real Si, Real Sj,
                                             const PairP<Real>& pu, Acc<Real>& acc, Real& fx,
                                             Real& fy, Real& fz)
 {
@@ -1055,7 +1112,8 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
 {
     typedef Stage<Real> SM;
     typedef typename Dev<Real>::R4 R4;
-    const R4* pos = d.pos[pc];
+    typedef typename Dev<Real>::P4 P4;
+    const P4* pos = d.pos[pc];
     int b0, b1;
     block_range(d, b0, b1);
     const int t = threadIdx.x;
@@ -1089,7 +1147,7 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             const int we = min(wb + SM::wave, e_end);
             for (int e = wb + t; e < we; e += blockDim.x) {
                 const int j_c = d.ent_j[e], o_c = d.ent_o[e];
-                const R4 pj = pos[j_c];
+                const P4 pj = pos[j_c];
                 const Real sj = e < e_rend ? d.S[j_c] : Real(0);
                 Real ex, ey, ez;
                 if (e < e_rend)
@@ -1114,12 +1172,12 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         // harmonic bonds (vitrimer chains): F_i = k (r - r0) (x_j - x_i) / r, half
         // of the energy and virial to each end (added to the two-body terms)
         if (BONDS && d.has_bonds && t < P) {  // BONDS: some system of the launch has bonds
-            const R4 pi = SM::pos()[t];
-            const int tag = packed_of(pi.w) >> kTypeBits;
+            const P4 pi = SM::pos()[t];
+            const int tag = pos_bits(pi) >> kTypeBits;
             for (int b = 0; b < kMaxBonds; b++) {
                 const int pt = d.bond_tag[tag * kMaxBonds + b];
                 if (pt < 0) break;
-                const R4 pj = pos[d.slot_of_tag[pt]];
+                const P4 pj = pos[d.slot_of_tag[pt]];
                 Real dx, dy, dz;
                 const Real r = sqrt(dist2_listed(pi, pj, d, dx, dy, dz));
                 const Real dr = r - d.bond_r0;
@@ -1160,8 +1218,8 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             st.v = SM::vel()[t];
             if (flags & F_OPENING)
                 for (int c = 0; c < 3; c++) st.q[c] = SM::xq()[3 * t + c];
-            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, SM::pos()[t].w, kin,
-                                             single ? &SM::pos()[t] : (R4*)nullptr));
+            dmax = fmaxf(dmax, integrate_one(d, a, pc, ac, i, fx, fy, fz, flags, step, st, pos_bits(SM::pos()[t]),
+                                             kin, single ? &SM::pos()[t] : (P4*)nullptr));
         }
         if (kPark)
 #pragma unroll
@@ -1179,11 +1237,12 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
 {
     typedef typename Dev<Real>::R4 R4;
     const R4 f = d.force[i];
-    const R4 pi = d.pos[pc][i];
+    const typename Dev<Real>::P4 pi = d.pos[pc][i];
     PState<Real> st;
     load_pstate(d, ac, i, F_OPENING, st);
     Real unused = Real(0);
-    return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, st, pi.w, unused, (R4*)nullptr);
+    return integrate_one(d, a, pc, ac, i, f.x, f.y, f.z, F_OPENING, step, st, pos_bits(pi), unused,
+                         (typename Dev<Real>::P4*)nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1347,7 +1406,7 @@ __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
     }
 }
 
-// The same reduction for a group of fewer than kNQA blocks:
+// The same reduction for a group of fewer than kNQA blocks (batched runs):
 // rank 0 alone, warp q summing quantity q over the group's blocks in order.
 template <typename Real>
 __device__ __forceinline__ void reduce_small(const Dev<Real>& d, const RunArgs& a, int par)
@@ -1414,9 +1473,9 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ, s_red);
     // groups of at least kNQA blocks: one quantity per block, asynchronously;
     // smaller groups reduce every quantity here
-    const bool red = had && g_size() >= kNQA && g_rank() < kNQA;
+    const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
     if (red) reduce_issue(d, a, prev);
-    if (had && g_size() < kNQA) reduce_small(d, a, prev);
+    if (kBatched && had && g_size() < kNQA) reduce_small(d, a, prev);
     if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
         s_ls.bar_target = bs.target;
         s_ls.parity = par;
@@ -1556,7 +1615,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
     if (s_ls.have_thermo) {
         // the last pass's partials were written after its barrier's arrival
         if (!grid_barrier(ctl, a.timeout_ns, 30)) return false;
-        if (g_size() < kNQA)
+        if (kBatched && g_size() < kNQA)
             reduce_small(d, a, s_ls.parity);
         else
             run_reduce_thermo(d, a, s_ls.parity);
@@ -1625,17 +1684,19 @@ template <typename Real>
 __global__ void k_set_state(Dev<Real> d)
 {
     typedef typename Dev<Real>::R4 R4;
+    typedef typename Dev<Real>::P4 P4;
     const int n = d.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        R4 p;
-        Real* pc[3] = {&p.x, &p.y, &p.z};
+        long long qs[3];
         for (int c = 0; c < 3; c++) {
+            // wrap into [0, L) and round to the fixed-point grid: one rounding per
+            // operation (no contraction), so the conversion is reproducible
             double L = (double)d.Lq[c] * kInvFix;
             double x = d.io[3 * i + c];
-            double fl = floor(x / L);
+            double fl = floor(__ddiv_rn(x, L));
             int im = (int)fl;
-            double xw = x - fl * L;
-            long long q = __double2ll_rn(xw * kFix);
+            double xw = __dsub_rn(x, __dmul_rn(fl, L));
+            long long q = __double2ll_rn(__dmul_rn(xw, kFix));
             if (q >= d.Lq[c]) {
                 q -= d.Lq[c];
                 im++;
@@ -1646,10 +1707,14 @@ __global__ void k_set_state(Dev<Real> d)
             }
             d.xq[0][c * n + i] = q;
             d.img[0][c * n + i] = im + d.io_int[n + 3 * i + c];
-            *pc[c] = fix_to_real(q, Real(0));
+            qs[c] = q;
         }
         int ty = d.io_int[i];
-        p.w = pack_w((i << kTypeBits) | ty, Real(0));
+        P4 p;
+        p.x = snap_coord(qs[0], 0, d);
+        p.y = snap_coord(qs[1], 1, d);
+        p.z = snap_coord(qs[2], 2, d);
+        p.w = snap_bits((i << kTypeBits) | ty, d);
         d.pos[0][i] = p;
         R4 v;
         v.x = (Real)d.io[3 * n + 3 * i + 0];
@@ -1666,8 +1731,8 @@ __global__ void k_get_state(Dev<Real> d, int pc, int ac)
     typedef typename Dev<Real>::R4 R4;
     const int n = d.n;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        R4 p = d.pos[pc][q];
-        int tag = packed_of(p.w) >> kTypeBits;
+        const int bits = pos_bits(d.pos[pc][q]);
+        int tag = bits >> kTypeBits;
         R4 v = d.vel[ac][q];
         for (int c = 0; c < 3; c++) {
             d.io[3 * tag + c] = (double)d.xq[ac][c * n + q] * kInvFix;
@@ -1676,7 +1741,7 @@ __global__ void k_get_state(Dev<Real> d, int pc, int ac)
         d.io[3 * n + 3 * tag + 0] = (double)v.x;
         d.io[3 * n + 3 * tag + 1] = (double)v.y;
         d.io[3 * n + 3 * tag + 2] = (double)v.z;
-        d.io_int[tag] = packed_of(p.w) & ((1 << kTypeBits) - 1);
+        d.io_int[tag] = bits & ((1 << kTypeBits) - 1);
     }
 }
 
@@ -1686,7 +1751,7 @@ __global__ void k_get_forces(Dev<Real> d, int pc)
     typedef typename Dev<Real>::R4 R4;
     const int n = d.n;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        int tag = packed_of(d.pos[pc][q].w) >> kTypeBits;
+        int tag = pos_bits(d.pos[pc][q]) >> kTypeBits;
         R4 f = d.force[q];
         d.io[3 * tag + 0] = (double)f.x;
         d.io[3 * tag + 1] = (double)f.y;
@@ -1699,16 +1764,16 @@ __global__ void k_get_nlist(Dev<Real> d, int pc, int* rows, int* counts, int wid
 {
     const int n = d.n;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const int tag = packed_of(d.pos[pc][q].w) >> kTypeBits;
+        const int tag = pos_bits(d.pos[pc][q]) >> kTypeBits;
         const int4 inf = d.pinfo[q];
         counts[2 * tag] = inf.y;
         counts[2 * tag + 1] = inf.y + inf.w;
         int* out = rows + (size_t)tag * width;
         int k = 0;
         for (int e = inf.x; e < inf.x + inf.y && k < width; e++, k++)
-            out[k] = packed_of(d.pos[pc][d.ent_j[e]].w) >> kTypeBits;
+            out[k] = pos_bits(d.pos[pc][d.ent_j[e]]) >> kTypeBits;
         for (int e = inf.z; e < inf.z + inf.w && k < width; e++, k++)
-            out[k] = packed_of(d.pos[pc][d.ent_j[e]].w) >> kTypeBits;
+            out[k] = pos_bits(d.pos[pc][d.ent_j[e]]) >> kTypeBits;
     }
 }
 
@@ -1748,11 +1813,11 @@ __global__ void k_pgrad_sums(Dev<Real> d, int pc, double* sd, double* part)
     const int n = d.n;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const typename Dev<Real>::R4 pi = d.pos[pc][i];
+        const typename Dev<Real>::P4 pi = d.pos[pc][i];
         const int4 inf = d.pinfo[i];
         double S = 0.0, D = 0.0, v2 = 0.0, vq = 0.0, ve = 0.0, qq = 0.0;
         for (int e = inf.x; e < inf.x + inf.y; e++) {
-            const typename Dev<Real>::R4 pj = d.pos[pc][d.ent_j[e]];
+            const typename Dev<Real>::P4 pj = d.pos[pc][d.ent_j[e]];
             const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
             Real dx, dy, dz;
             const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
@@ -1799,13 +1864,13 @@ __global__ void k_pgrad_forces(Dev<Real> d, int pc, const double* sd, double lam
 {
     const int n = d.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const typename Dev<Real>::R4 pi = d.pos[pc][i];
+        const typename Dev<Real>::P4 pi = d.pos[pc][i];
         const int4 inf = d.pinfo[i];
         const double Si = sd[2 * i], Di = sd[2 * i + 1];
         double g3[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
         for (int e = inf.x; e < inf.x + inf.y; e++) {
             const int j = d.ent_j[e];
-            const typename Dev<Real>::R4 pj = d.pos[pc][j];
+            const typename Dev<Real>::P4 pj = d.pos[pc][j];
             const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
             Real dx, dy, dz;
             const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
@@ -1827,7 +1892,7 @@ __global__ void k_pgrad_forces(Dev<Real> d, int pc, const double* sd, double lam
 #pragma unroll
                 for (int c = 0; c < 3; c++) g3[k][c] -= dft[k] * dv[c];
         }
-        const int tag = packed_of(pi.w) >> kTypeBits;
+        const int tag = pos_bits(pi) >> kTypeBits;
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll

@@ -19,19 +19,31 @@ def _wrap(d, L):
     return d
 
 
+def _box_fraction(x, L):
+    """32-bit fraction of coordinate x along an edge L (FP32 decisions): the
+    edge rounded to float and to the 2^-48 grid (Lq units), x wrapped into it
+    and rounded half-even to the grid (q), then floor(q floor(2^96 / Lq) / 2^64)."""
+    Lq = math.floor(float(np.float32(L)) * 2.0 ** 48 + 0.5)
+    Lp = Lq * 2.0 ** -48
+    k = math.floor(x / Lp)
+    xw = x - k * Lp
+    q = round(xw * 2.0 ** 48)  # Python rounds halves to even
+    if q >= Lq:
+        q -= Lq
+    if q < 0:
+        q += Lq
+    return (q * ((1 << 96) // Lq)) >> 64, Lq
+
+
 def _d2_decision(xi, xj, box, fp32):
     if fp32:
         f = np.float32
         acc = []
         for c in range(3):
-            d = f(xj[c]) - f(xi[c])
-            L = f(box[c])
-            h = f(0.5) * L
-            if d > h:
-                d = d - L
-            elif d < -h:
-                d = d + L
-            acc.append(d)
+            ui, Lq = _box_fraction(xi[c], box[c])
+            uj, _ = _box_fraction(xj[c], box[c])
+            du = ((uj - ui + 2 ** 31) % 2 ** 32) - 2 ** 31  # signed 32-bit wrap: the minimum image
+            acc.append(f(du) * f(Lq * 2.0 ** -80))
         s = acc[0] * acc[0]
         s = s + acc[1] * acc[1]
         s = s + acc[2] * acc[2]

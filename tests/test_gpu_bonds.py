@@ -54,6 +54,28 @@ def test_bonded_forces_match_oracle(orc, precision):
     assert th["n_bonds"] == ref["n_bonds"]
 
 
+def test_vitrimer_full_size_forces_fp32(orc):
+    """The 2M-bead network of the benchmark (box of 133 sigma) after a short
+    run: every particle's force, the energies, virial and bond count against
+    the oracle at the positions the run reached."""
+    wl = inputs.vitrimer_workload(2_000_000, seed=1)
+    assert wl["box"][0] > 128.0
+    s = _gpu(wl, "fp32")
+    s.run(200, wl["dt"], wl["kT"], wl["gamma"])
+    s.compute_forces()
+    x, _, _ = s.state()
+    F = s.forces()
+    th = s.thermo()
+    ref = _oracle(orc, wl, x, True)
+    assert_forces_match(F, ref, TOL["fp32"], "vitrimer2m")
+    tol = TOL["fp32"]
+    assert abs(th["U2"] - (ref["U2"] + ref["U_bond"])) <= tol * (ref["scale_U2"] + ref["scale_Ub"])
+    assert abs(th["U3"] - ref["U3"]) <= tol * ref["scale_U3"]
+    assert np.all(np.abs(th["W"] - ref["W"]) <= tol * ref["scale_W"])
+    assert th["n_bonds"] == ref["n_bonds"]
+    s.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_bonded_trajectory_matches_oracle(orc, precision):
     wl = _wl(n=2200, seed=3)

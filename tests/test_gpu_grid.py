@@ -1,11 +1,10 @@
 """Step kernel on fewer blocks than SMs (swp_set_grid) against the FP64 oracle.
 
-A grid of one block takes no grid barrier; grids of fewer than ten blocks
-(the number of thermo quantities) reduce the block partials on one block; a
-block of a small grid walks its particles in several sub-chunks.  Each must
-give the oracle's forces, thermo record and trajectories at the usual
-tolerances, and a change of grid between runs must rebuild the list and
-carry on.
+Requests below ten blocks run on ten (one block per thermo quantity reduced
+in parallel); a block of a small grid walks its particles in several
+sub-chunks.  Each grid must give the oracle's forces, thermo record and
+trajectories at the usual tolerances, and a change of grid between runs must
+rebuild the list and carry on.
 """
 import numpy as np
 import pytest
@@ -31,7 +30,7 @@ def _min_image(d, box):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("grid", [1, 2, 9, 10, 33])
+@pytest.mark.parametrize("grid", [1, 10, 11, 33, 76])
 def test_forces_on_small_grids(orc, precision, grid):
     wl = inputs.workload("mix2k", lambda3=2.0, n=3001, density=0.5, seed=4)
     s = make_gpu(wl, precision)
@@ -42,7 +41,7 @@ def test_forces_on_small_grids(orc, precision, grid):
     assert_thermo_match(s.thermo(), ref, TOL[precision], f"grid={grid}")
 
 
-@pytest.mark.parametrize("grid", [1, 4])
+@pytest.mark.parametrize("grid", [10, 17])
 def test_trajectory_with_rebuilds_on_small_grids(orc, grid):
     wl = inputs.workload("mix2k", lambda3=1.0, n=1500, density=0.3, seed=2, shift=1)
     wl["v"] = inputs.maxwell_velocities(1500, 1.0, 1.0, seed=9)
@@ -61,12 +60,12 @@ def test_trajectory_with_rebuilds_on_small_grids(orc, grid):
     assert th["K"] == pytest.approx(tho[-1, 2], rel=1e-10)
 
 
-def test_dumbbell_single_block_matches_full_grid():
-    """The paper's timing system (n = 100 dumbbells) on one block and on every
+def test_dumbbell_small_grid_matches_full_grid():
+    """The paper's timing system (n = 100 dumbbells) on ten blocks and on every
     SM: the same trajectory up to the order of floating-point sums."""
     wl = inputs.dumbbell_workload(seed=3, kT=0.03, n_a=600, n_b=400, rcut=1.15)
     out = []
-    for grid in (1, 0):
+    for grid in (10, 0):
         s = make_gpu(wl, "fp64")
         s.set_grid(grid)
         s.run(400, 0.001, 0.03, 1.0)
@@ -86,7 +85,7 @@ def test_grid_change_between_runs(orc):
     a.run(60, 0.001, 0.1, 1.0)
     b = make_gpu(wl, "fp64")
     b.run(25, 0.001, 0.1, 1.0)
-    b.set_grid(3)
+    b.set_grid(12)
     b.run(35, 0.001, 0.1, 1.0)
     xa, va, ia = a.state()
     xb, vb, ib = b.state()

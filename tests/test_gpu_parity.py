@@ -92,6 +92,27 @@ def test_forces_full_size_100k(orc):
     assert_thermo_match(s.thermo(), ref, TOL["fp32"], "100k")
 
 
+@pytest.mark.parametrize("n,density", [(131072, 0.125), (300_000, 0.125)])
+def test_forces_large_boxes_fp32(orc, n, density):
+    # boxes of 102 and 134 sigma: FP32 displacements come from 32-bit box
+    # fractions, so their error does not grow with the coordinates
+    wl = _wl("mix2k", lam=1.0, n=n, density=density, seed=5)
+    assert wl["box"][0] > 100.0
+    s = make_gpu(wl, "fp32")
+    s.compute_forces()
+    ref = _oracle(orc, wl, True)
+    assert_forces_match(s.forces(), ref, TOL["fp32"], f"n={n} L={wl['box'][0]:.1f}")
+    assert_thermo_match(s.thermo(), ref, TOL["fp32"], f"n={n}")
+    rows, counts = s.nlist()
+    assert counts[:, 1].sum() == 2 * len(orc_pairs_within(orc, wl))
+
+
+def orc_pairs_within(orc, wl):
+    """Unordered pairs within the list radius by the oracle's FP32 decisions."""
+    nb = orc.nlist(wl["x"], wl["types"], wl["n_types"], oracle_pairs(orc, wl), wl["box"], wl["skin"], fp32=True)
+    return [(i, j) for i, r in enumerate(nb) for j in r if j > i]
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_shifted_form_and_noncubic_box(orc, precision):
     n = 1500

@@ -229,6 +229,30 @@ def test_oracle_matches_brute_force(orc, seed, fp32, lam, shift):
     assert r["n_bonds"] == b["n_bonds"]
 
 
+def test_fp32_decision_distance_is_accurate_in_large_boxes():
+    """The FP32 decision displacement (32-bit box fractions) is within a few
+    units of 2^-32 L of the exact minimum-image displacement, whatever the
+    coordinates: for a box of 133 sigma and pairs straddling the periodic
+    faces, d2 agrees with the FP64 value to 1e-6 relative."""
+    from brute import _d2_decision
+
+    rng = np.random.default_rng(3)
+    L = float(np.float32(133.7))
+    box = np.array([L, L * 0.9, L * 1.1])
+    box = inputs.f32(box)
+    for k in range(400):
+        xi = rng.random(3) * box
+        if k % 2:  # half of the pairs straddle a face
+            c = k % 3
+            xi[c] = box[c] - rng.uniform(0.0, 1.0)
+        d = rng.normal(size=3)
+        d *= rng.uniform(0.5, 2.0) / np.linalg.norm(d)
+        xj = np.mod(xi + d, box)
+        exact = _d2_decision(xi, xj, box, False)
+        approx = _d2_decision(xi, xj, box, True)
+        assert abs(approx - exact) <= 1e-6 * exact, (approx, exact)
+
+
 def test_oracle_brute_three_types_mixed_coefficients(orc):
     # c2 reading: prefactor sqrt(l_ij e_ij l_ik e_ik); checked only for consistency
     x, ty, box = _small_system(7, n=30, L=5.6, types=3)
