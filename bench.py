@@ -11,6 +11,11 @@ One benchmark step = one launch of the persistent step kernel advancing
 the inputs stay resident in HBM, and L2 is flushed (a 512 MB write) between
 timed launches.
 
+Other workloads (``--workload``): batch256 (256 independent systems in one
+launch), diff20k (force-matching gradient), vitrimer2m (2M-bead bonded
+network), dumbbell (the paper's timing system at ``--particles`` and
+``--rcut``).
+
 Each rank (torchrun, one GPU each) runs its own independent replica: weak
 scaling, no collective on the data path.  ``--impl reference`` times the FP64
 CPU oracle on the same workload (bounded samples) instead.
