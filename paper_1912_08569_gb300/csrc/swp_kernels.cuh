@@ -405,31 +405,25 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
 // ---------------------------------------------------------------------------
 // Block reductions
 
-// Sums the per-thread accumulators over the block into partials[slot][q]:
-// warp shuffles level by level over all quantities at once (independent
-// chains in flight together), then warp q combines the warp sums of
-// quantity q, in the arithmetic precision (at most 1024 terms per block);
-// the block totals are summed over blocks in FP64 (reduce_thermo).  FP64
-// runs at a small fraction of the FP32 rate on this part, so it is kept out
-// of the per-thread work.
+// Sums the per-thread accumulators over the block into partials[slot][q],
+// in the arithmetic precision (at most 1024 terms per block), through a
+// shared staging area of kNQA x blockDim values: ten warps do the sums while
+// the others go on (fewer shuffles than a tree over every warp); the block
+// totals are summed over blocks in FP64 (reduce_thermo).  FP64 runs at a
+// small fraction of the FP32 rate on this part, so it is kept out of the
+// per-thread work.
 template <typename Real>
-__device__ __forceinline__ void block_thermo(const Real* acc, double* out, double* shd)
+__device__ __forceinline__ void block_thermo(const Real* acc, double* out, Real* stage)
 {
-    Real* sh = (Real*)shd;  // kNQA * 32 values
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    Real v[kNQA];
+    // thread t's values go to stage[q * B + t]; warp q then sums quantity q over
+    // the block in a fixed order (32 values per lane, then the lanes)
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, B = blockDim.x;
 #pragma unroll
-    for (int q = 0; q < kNQA; q++) v[q] = acc[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int q = 0; q < kNQA; q++) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < kNQA; q++) sh[q * 32 + warp] = v[q];
+    for (int q = 0; q < kNQA; q++) stage[q * B + t] = acc[q];
     __syncthreads();
     if (warp < kNQA) {
-        Real x = lane < nw ? sh[warp * 32 + lane] : Real(0);
+        Real x = Real(0);
+        for (int k = lane; k < B; k += 32) x += stage[warp * B + k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) out[warp] = (double)x;
@@ -1470,7 +1464,8 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     bs.target = s_ls.bar_target;
     bar_arrive(d.ctl, bs, pub_dst, &s_ls.dmax_bits);
     const int had = s_ls.have_thermo, prev = s_ls.parity;
-    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ, s_red);
+    // the wave buffer is free from the end of the force pass to the next S pass
+    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ, Stage<Real>::w());
     // groups of at least kNQA blocks: one quantity per block, asynchronously;
     // smaller groups reduce every quantity here
     const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
