@@ -201,6 +201,28 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def host_info():
+    """The host the CPU baseline ran on: logical cores and CPU model."""
+    model, arm = None, {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" not in line:
+                    continue
+                key, val = (t.strip() for t in line.split(":", 1))
+                if key.lower() in ("model name", "cpu model") and model is None:
+                    model = val
+                elif key in ("CPU implementer", "CPU part") and key not in arm:
+                    arm[key] = val  # Arm cores name themselves by these codes
+    except OSError:
+        pass
+    if model is None and arm:
+        model = ", ".join(f"{k} {v}" for k, v in arm.items())
+    import platform
+
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
 def _profile_traffic(n, md_steps):
     """DRAM bytes of one step-kernel launch (dram__bytes_read.sum +
     dram__bytes_write.sum) from the committed ncu record, if it was taken on
@@ -298,7 +320,8 @@ def run_reference(a):
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": _config(a, wl["n"], 1),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "host": host_info()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -421,7 +444,7 @@ def run_ours(a):
 
         oracle.build()
         v, steps_done, el = cpu_oracle_sample(wl, a.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"N={n}, {steps_done} BAOAB steps of the FP64 C oracle (explicit triplet "
                          f"loop, cell list every step), {el:.1f} s, 1 thread",
                "accuracy": accuracy_vs_oracle(oracle, s, wl)}
@@ -553,7 +576,7 @@ def run_batch(a):
         oracle.build()
         k = int(np.argsort(ns)[len(ns) // 2])  # the median-size system
         v, steps_done, el = cpu_oracle_sample(wls[k], a.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"system {k} (N={int(ns[k])}), {steps_done} BAOAB steps of the FP64 C oracle, "
                          f"{el:.1f} s, 1 thread"}
     if rank == 0:
@@ -796,7 +819,8 @@ def run_reference_dumbbell(a, oracle):
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": _dumb_config(a, wl["n"], 1), "timesteps_per_s": per / (ms / 1e3),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "host": host_info()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -873,7 +897,7 @@ def run_dumbbell(a):
 
         oracle.build()
         v, steps_done, el = cpu_oracle_sample(wl, a.cpu_seconds, steps_cap=2000)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "timesteps_per_s": v / n,
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(), "timesteps_per_s": v / n,
                "sample": f"N={n}, {steps_done} BAOAB steps of the FP64 C oracle, {el:.1f} s, 1 thread",
                "accuracy": accuracy_vs_oracle(oracle, s, wl)}
     if rank == 0:
