@@ -64,3 +64,19 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_dumbbell_workload_line():
+    """The oracle arm on the paper's timing system prints one complete line
+    (bounded sample; CPU only)."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "dumbbell", "--particles", "512", "--rcut", "1.15", "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["n_particles"] == 512
+    assert d["config"]["r_cut"] == 1.15 and d["timesteps_per_s"] > 0
+    assert d["cpu_baseline"]["cores"] == 1 and d["cpu_baseline"]["host"]["nproc"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
