@@ -35,6 +35,15 @@ namespace single {
 #endif
 
 constexpr bool kBatched = SWP_BATCHED != 0;
+// The list rebuild is kept out of line in the batched kernel: inlined, its
+// register needs spread into the step loop (whose per-system descriptors come
+// from shared memory there, not the parameter bank) and cost spills.
+#undef SWP_COLD
+#if SWP_BATCHED
+#define SWP_COLD __noinline__
+#else
+#define SWP_COLD
+#endif
 // Threads per block.  The batched kernel reads every system's descriptors from
 // shared memory rather than the constant bank, so at 64 registers per thread
 // it spills; 512-thread blocks at 128 registers run without spilling but were
@@ -1282,7 +1291,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, long long timeout_ns, int
 
 // 0: ok; 1: the list overflowed its capacity; 2: a wait timed out.
 template <typename Real>
-__device__ int run_rebuild(const Dev<Real>& d, const RunArgs& a)
+__device__ SWP_COLD int run_rebuild(const Dev<Real>& d, const RunArgs& a)
 {
     Ctl* ctl = d.ctl;
     const int gt = g_rank() * blockDim.x + threadIdx.x, gn = g_size() * blockDim.x;
