@@ -62,8 +62,12 @@ extern "C" {
 #define SWP_ERR_STATE (-5)           /* call out of order (nothing bound / no state set) */
 #define SWP_ERR_NONFINITE (-6)       /* a non-finite force was produced */
 
-/* Arithmetic precision of a context. */
-#define SWP_FP32 0 /* FP32 pair/three-body arithmetic, FP64 reductions, 64-bit fixed-point positions */
+/* Arithmetic precision of a context.  SWP_FP32: pair and three-body arithmetic
+ * and per-block sums in FP32, sums over blocks in FP64, positions accumulated
+ * in 64-bit fixed point; distances come from 32-bit fractions of the box
+ * edges (the minimum image is the wrap-around difference), so their error does
+ * not grow with the box. */
+#define SWP_FP32 0
 #define SWP_FP64 1 /* FP64 everywhere (parity and validation) */
 
 /* Kinds of type pairs. */
