@@ -57,6 +57,8 @@ def _args():
     ap.add_argument("--rcut", type=float, default=1.3, help="A-B cut-off of the dumbbell workload")
     ap.add_argument("--grid", type=int, default=0, help="step-kernel blocks (0: every SM)")
     ap.add_argument("--bps", type=int, default=0)
+    ap.add_argument("--no-resident", action="store_true",
+                    help="forbid the resident mode (one barrier per step): the two-barrier step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -353,6 +355,8 @@ def run_ours(a):
     s.set_state(wl["x"], wl["v"], wl["types"], wl["mass"])
     if a.grid:
         s.set_grid(a.grid)
+    if a.no_resident:
+        s.set_resident(False)
     s.compute_forces()
     _, counts = s.nlist()
     nn = float(counts[:, 1].mean())
@@ -456,6 +460,7 @@ def run_ours(a):
                "config": _config(a, n, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": a.steps, "clocks": clk, "wall_s_timed": t_wall,
                "kernel_digest": _kernel_digest(),
+               "resident_steps_last_launch": th1["resident_steps"],
                "thermo_last": {"U2": th1["U2"], "U3": th1["U3"], "K": th1["K"],
                                "n_bonds": th1["n_bonds"]}}
         print(json.dumps(out), flush=True)

@@ -51,7 +51,7 @@ extern "C" {
 #define SWP_API
 #endif
 
-#define SWP_ABI_VERSION 1
+#define SWP_ABI_VERSION 2
 
 /* Status codes. */
 #define SWP_OK 0
@@ -63,10 +63,12 @@ extern "C" {
 #define SWP_ERR_NONFINITE (-6)       /* a non-finite force was produced */
 
 /* Arithmetic precision of a context.  SWP_FP32: pair and three-body arithmetic
- * and per-block sums in FP32, sums over blocks in FP64, positions accumulated
- * in 64-bit fixed point; distances come from 32-bit fractions of the box
- * edges (the minimum image is the wrap-around difference), so their error does
- * not grow with the box. */
+ * in FP32, per-thread energy/virial terms of at most one block sub-chunk in
+ * FP32, block sums compensated (double-float, as accurate as FP64 sums of the
+ * FP32 terms), sums over blocks in FP64, positions accumulated in 64-bit fixed
+ * point; distances come from 32-bit fractions of the box edges (the minimum
+ * image is the wrap-around difference), so their error does not grow with the
+ * box. */
 #define SWP_FP32 0
 #define SWP_FP64 1 /* FP64 everywhere (parity and validation) */
 
@@ -93,6 +95,9 @@ typedef struct {
     int64_t steps_done;  /* steps completed by the last step call */
     int32_t max_row;     /* longest neighbour row of the last build */
     int32_t state;       /* 0: forces current; 1: forces stale; 2: inside a step (after overflow) */
+    int32_t resident_steps; /* steps of the last step call taken in the resident mode
+                               (see swp_set_resident) */
+    int32_t reserved;
 } swp_thermo;
 
 /* ABI version (SWP_ABI_VERSION); needs no device. */
@@ -263,13 +268,43 @@ SWP_API int swp_set_grid(swp_ctx* ctx, int blocks);
 /* Bound, in nanoseconds, on every device-side wait (default 2 s). */
 SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);
 
+/* Resident mode of the FP32 step (enable: 1, the default; 0: off).  When a
+ * run has one system in FP32 without bonds and every block of the step kernel
+ * owns at most one sub-chunk of particles (n up to blockDim x grid, 155,648
+ * on a 152-SM part), each block keeps in shared memory, between list builds,
+ * its own rows and the reactive rows of its halo (the partners of its particles
+ * that other blocks own) with partners as local indices; a step then copies
+ * the halo's new positions in once, forms S (Eq. 3bp via S_i) for its own
+ * particles and the reactive halo itself, and the forces and the integrator
+ * from shared memory, with one grid barrier per step instead of two.  Blocks
+ * whose structures exceed the shared-memory capacity (3,072 local particles,
+ * 16,384 local entries, rows of 255 entries) make the whole run fall back to
+ * the two-barrier path until the next list build.  Forces and trajectories are
+ * the same bit for bit either way (same operations, same summation orders);
+ * the energy and virial sums are grouped differently (equal within their
+ * rounding).  thermo.resident_steps reports how many steps ran resident.
+ * enable not 0 or 1: SWP_ERR_INVALID. */
+SWP_API int swp_set_resident(swp_ctx* ctx, int enable);
+
+/* Failure-detection test hook (the paper has no counterpart).  With on = 1 the
+ * next step-kernel launch of ctx withholds one block's arrival at its first
+ * grid barrier, so that every other block's bounded wait runs out after the
+ * timeout of swp_set_timeout: the launch ends early with every block returned,
+ * and the next swp_sync / swp_read_* reports SWP_ERR_TIMEOUT (the state is then
+ * lost: set it again).  Nothing faults and no wait is unbounded; it exercises
+ * the path a real stall (a block starved by other work, a lost arrival) takes.
+ * The request is consumed by that one launch.  on not 0 or 1: SWP_ERR_INVALID. */
+SWP_API int swp_set_withhold_arrival(swp_ctx* ctx, int on);
+
 /* Forces without any device allocation.  The paper has no counterpart: this
  * serves callers that cannot allocate device memory when they need forces --
  * code running inside a host framework whose memory pool has reserved the
- * device and forbids side allocations, code driven from inside a stream
- * capture, or a latency-bound loop that cannot afford the device-wide
- * synchronisation of cudaMalloc / cudaFree.  It neither allocates nor frees
- * anything and needs no bound workspace or list buffer.
+ * device and forbids side allocations, or a latency-bound loop that cannot
+ * afford the device-wide synchronisation of cudaMalloc / cudaFree.  It neither
+ * allocates nor frees anything and needs no bound workspace or list buffer.
+ * The call synchronises cuda_stream and copies small parameter blocks from
+ * pageable host memory, so it cannot be recorded into a CUDA graph by stream
+ * capture; call it outside any capture.
  *
  * Uses the coefficients, skin, max_nn and launch shape of ctx.  Inputs: x_dev
  * [n][3] positions and type_dev [n] types (NULL: all 0), device pointers.
@@ -286,10 +321,11 @@ SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);
  * re-initialises what must start at zero), so calls that overlap on the GPU
  * -- from two streams, threads or contexts at once -- race and corrupt each
  * other: serialise them.  The first call on each device looks up the array's
- * device address (with that device current); make that first call before
- * any stream capture.  Enqueues on cuda_stream and returns after
- * synchronising it.  Errors: as swp_compute_forces (row overflow:
- * SWP_ERR_NLIST_OVERFLOW, grow max_nn with swp_set_nlist). */
+ * device address (with that device current).  The current device must be the
+ * one ctx was created on (else SWP_ERR_INVALID).  Enqueues on cuda_stream and
+ * returns after synchronising it.  Errors: as swp_compute_forces (row
+ * overflow: SWP_ERR_NLIST_OVERFLOW, grow max_nn with swp_set_nlist; the next
+ * call starts clean). */
 #define SWP_STATIC_SCRATCH_BYTES (8u << 20)
 SWP_API int swp_compute_forces_static(swp_ctx* ctx, const double* x_dev, const int32_t* type_dev,
                                       double* f_dev, double* thermo_dev, void* cuda_stream);

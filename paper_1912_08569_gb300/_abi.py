@@ -48,7 +48,8 @@ EXPORTS = (
     "swp_build_nlist", "swp_compute_forces", "swp_step_nve", "swp_step_nvt", "swp_sync",
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch", "swp_set_grid",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
-    "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds",
+    "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds", "swp_set_resident",
+    "swp_set_withhold_arrival",
 )
 
 
@@ -70,6 +71,8 @@ class swp_thermo(ctypes.Structure):
         ("steps_done", ctypes.c_int64),
         ("max_row", ctypes.c_int32),
         ("state", ctypes.c_int32),
+        ("resident_steps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -111,6 +114,8 @@ def load_library(path: str = LIB_PATH):
         "swp_set_launch": ([c_void_p, c_int], c_int),
         "swp_set_grid": ([c_void_p, c_int], c_int),
         "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
+        "swp_set_resident": ([c_void_p, c_int], c_int),
+        "swp_set_withhold_arrival": ([c_void_p, c_int], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
         "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
@@ -255,6 +260,14 @@ def swp_set_grid(ctx, blocks: int = 0):
 
 def swp_set_timeout(ctx, ns: int):
     return _check(ctx, load_library().swp_set_timeout(ctx, int(ns)), "swp_set_timeout")
+
+
+def swp_set_resident(ctx, enable: int):
+    return _check(ctx, load_library().swp_set_resident(ctx, int(enable)), "swp_set_resident")
+
+
+def swp_set_withhold_arrival(ctx, on: int):
+    return _check(ctx, load_library().swp_set_withhold_arrival(ctx, int(on)), "swp_set_withhold_arrival")
 
 
 def swp_last_error(ctx) -> str:

@@ -47,6 +47,8 @@ struct swp_ctx {
     int device = 0, num_sms = 0;
     int bps_req = 0, grid_req = 0, grid = 0, max_blocks = 0;
     long long timeout_ns = 2000000000LL;
+    int resident = 1;  // the FP32 step may keep each block's neighbourhood in shared memory
+    int withhold = 0;  // test hook: the next launch withholds one barrier arrival
     void* ws = nullptr;
     size_t ws_bytes = 0;
     void* nl = nullptr;
@@ -195,7 +197,7 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     int* perm = (int*)take(sizeof(int) * n);
     int* bsum = (int*)take(sizeof(int) * c->max_blocks);
     // thermo partials of the step kernel; also the scratch of the parameter derivatives (4 * 512 + 4)
-    double* partials = (double*)take(sizeof(double) * std::max<size_t>(2 * c->max_blocks * kNQ, 4 * 512 + 4));
+    double* partials = (double*)take(sizeof(double) * std::max<size_t>((size_t)kParities * c->max_blocks * kNQ, 4 * 512 + 4));
     double* io = (double*)take(sizeof(double) * 7 * n);
     int* io_int = (int*)take(sizeof(int) * 4 * n);
     int* bond_tag = (int*)take(sizeof(int) * kMaxBonds * n);
@@ -255,11 +257,12 @@ size_t workspace_bytes(swp_ctx* c)
                                     : layout<float>(c, nullptr, nullptr);
 }
 
+// Every type pair's device coefficients (precomputed in double, stored in the
+// run's precision): the one place the table is derived from the context.
 template <typename Real>
-void build_table(swp_ctx* c)
+void fill_pair_table(const swp_ctx* c, PairP<Real>* t)
 {
-    c->table_host.assign(sizeof(PairP<Real>) * kMaxTypes * kMaxTypes, 0);
-    PairP<Real>* t = (PairP<Real>*)c->table_host.data();
+    std::memset(t, 0, sizeof(PairP<Real>) * kMaxTypes * kMaxTypes);
     for (int k = 0; k < c->ntypes * c->ntypes; k++) {
         const PairHost& p = c->pairs[k];
         PairP<Real> e;
@@ -293,6 +296,13 @@ void build_table(swp_ctx* c)
         }
         t[k] = e;
     }
+}
+
+template <typename Real>
+void build_table(swp_ctx* c)
+{
+    c->table_host.assign(sizeof(PairP<Real>) * kMaxTypes * kMaxTypes, 0);
+    fill_pair_table<Real>(c, (PairP<Real>*)c->table_host.data());
 }
 
 template <typename Real>
@@ -464,6 +474,9 @@ int run(swp_ctx* c, RunArgs a)
     c->grid = step_grid(c, bps);
     int rc = prepare_args<Real>(c, a);
     if (rc) return rc;
+    a.resident = c->resident;
+    a.withhold = c->withhold;
+    c->withhold = 0;  // one launch consumes the request
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
     SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
     return SWP_OK;
@@ -1027,6 +1040,7 @@ int swp_read_thermo(swp_ctx* c, swp_thermo* out)
     out->steps_done = h.steps_done;
     out->max_row = h.max_row;
     out->state = h.state;
+    out->resident_steps = h.resident_steps;
     return rc;
 }
 
@@ -1158,6 +1172,22 @@ int swp_set_timeout(swp_ctx* c, int64_t ns)
     return SWP_OK;
 }
 
+int swp_set_resident(swp_ctx* c, int enable)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (enable != 0 && enable != 1) return fail(c, SWP_ERR_INVALID, "enable must be 0 or 1");
+    c->resident = enable;
+    return SWP_OK;
+}
+
+int swp_set_withhold_arrival(swp_ctx* c, int on)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (on != 0 && on != 1) return fail(c, SWP_ERR_INVALID, "on must be 0 or 1");
+    c->withhold = on;
+    return SWP_OK;
+}
+
 const char* swp_last_error(const swp_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int swp_destroy(swp_ctx* c)
@@ -1173,12 +1203,13 @@ int swp_destroy(swp_ctx* c)
 //
 // Some callers cannot allocate device memory at the moment they need forces:
 // code embedded in a host framework whose memory pool has reserved the
-// device's memory and forbids side allocations, code driven from inside a
-// stream capture, or a latency-bound loop that cannot afford the implicit
-// device synchronisation of cudaMalloc/cudaFree.  swp_compute_forces_static
-// serves them: its scratch (state copy, cell list, neighbour list, partial
-// sums) lives in the fixed-size array below, which the library's module
-// reserves on every GPU that loads it, for the life of the process.
+// device's memory and forbids side allocations, or a latency-bound loop that
+// cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
+// swp_compute_forces_static serves them: its scratch (state copy, cell list,
+// neighbour list, partial sums) lives in the fixed-size array below, which the
+// library's module reserves on every GPU that loads it, for the life of the
+// process.  The call synchronises its stream and uploads small parameter
+// blocks from pageable host memory, so it is not for stream capture.
 
 namespace {
 
@@ -1205,48 +1236,13 @@ __global__ void k_static_stage(const double* x, const int32_t* type, double* io,
 }
 
 template <typename Real>
-void static_table(const swp_ctx* c, PairP<Real>* t)
-{
-    std::memset(t, 0, sizeof(PairP<Real>) * kMaxTypes * kMaxTypes);
-    for (int k = 0; k < c->ntypes * c->ntypes; k++) {
-        const PairHost& p = c->pairs[k];
-        PairP<Real>& e = t[k];
-        e.kind = p.kind;
-        e.nhalf = p.n / 2;
-        e.odd = p.n & 1;
-        e.four_eps = (Real)(4.0 * p.eps);
-        e.n_real = (Real)p.n;
-        e.sig2 = (Real)(p.sigma * p.sigma);
-        const double rmin = p.sigma * std::pow(2.0, 1.0 / p.n);
-        e.rmin2 = (Real)(rmin * rmin);
-        e.rlist2 = (Real)(-1.0);
-        if (p.kind == KIND_WCA) {
-            e.rc2 = (Real)(rmin * rmin);
-            e.ushift = (Real)p.eps;
-            e.inv_epshat = (Real)(1.0 / p.eps);
-            e.rlist2 = (Real)((rmin + c->skin) * (rmin + c->skin));
-            e.rbond2 = (Real)(-1.0);
-        } else if (p.kind == KIND_SWAP) {
-            const double vc = p.shift ? lj(p.rcut, p.eps, p.sigma, p.n) : 0.0;
-            e.rc2 = (Real)(p.rcut * p.rcut);
-            e.a = (Real)std::sqrt(p.lambda3 * p.eps);
-            e.inv_epshat = (Real)(1.0 / (p.eps + vc));
-            e.vshift = (Real)vc;
-            e.ushift = (Real)(-vc);
-            e.rlist2 = (Real)((p.rcut + c->skin) * (p.rcut + c->skin));
-            double rb = p.rbond > 0.0 ? p.rbond
-                                      : p.sigma * std::pow((1.0 - std::sqrt(0.5)) / 2.0, -1.0 / p.n);
-            e.rbond2 = (Real)(rb * rb);
-        }
-    }
-}
-
-template <typename Real>
 int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, double* thermo,
                   cudaStream_t s)
 {
     int dev = 0;
     SWP_CUDA(c, cudaGetDevice(&dev));
+    if (dev != c->device)
+        return fail(c, SWP_ERR_INVALID, "the current device is not the one the context was created on");
     if (dev < 0 || dev >= kMaxStaticDevices) return fail(c, SWP_ERR_INVALID, "device index too large");
     if (!g_static_addr[dev]) {
         void* p = nullptr;
@@ -1270,7 +1266,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
     set_list(c, base + ws, &d);
 
     PairP<Real> tab[kMaxTypes * kMaxTypes];
-    static_table<Real>(c, tab);
+    fill_pair_table<Real>(c, tab);
     SWP_CUDA(c, cudaMemcpyAsync((void*)d.table, tab, sizeof(tab), cudaMemcpyHostToDevice, s));
     SWP_CUDA(c, cudaMemcpyAsync((void*)d.cell_rank, c->cell_rank.data(), sizeof(int) * 2 * c->ncell,
                                 cudaMemcpyHostToDevice, s));

@@ -20,6 +20,7 @@ constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays c
 // Thermo quantities, in the order of the per-block partials.
 enum { Q_U2 = 0, Q_U3 = 1, Q_K = 2, Q_W0 = 3, Q_BONDS = 9, Q_SPARE0 = 10, Q_SPARE1 = 11 };
 constexpr int kNQA = 10;  // quantities accumulated per thread (Q_U2 .. Q_BONDS)
+constexpr int kParities = 3;  // thermo partial buffers in rotation (see f_barrier)
 
 // Fixed-point position unit: positions are int64 multiples of 2^-48 sigma.
 constexpr double kFix = 281474976710656.0;          // 2^48
@@ -67,6 +68,10 @@ struct Ctl {
     long long steps_done;        // steps completed by the last run call
     long long timeout_at;        // diagnostic: phase id where a wait gave up
     double thermo[kNQ];          // last reduced thermo record
+    int rfail[2];                // resident-mode agreement: a block whose local structures do not
+                                 // fit sets its round's word (rounds alternate; cleared on device)
+    int resident_steps;          // steps of the last run call taken in the resident mode
+    int pad_;
 };
 
 // Status bits latched on the device.
@@ -140,7 +145,7 @@ struct Dev {
     int* cell_fill;    // [ncell]
     int* perm;         // [n] new slot -> old slot
     int* bsum;         // [max_blocks] per-block cell-count sums (scan)
-    double* partials;  // [2][max_blocks][kNQ]
+    double* partials;  // [kParities][max_blocks][kNQ]
     Ctl* ctl;
     double* io;        // host-exchange staging: [3n] x, [3n] v, [n] mass
     int* io_int;       // staging: [n] types, [3n] images
@@ -167,6 +172,8 @@ struct RunArgs {
     unsigned long long seed;
     long long timeout_ns;  // bound on every device-side wait
     int max_blocks;     // partials stride
+    int resident;       // 1: an FP32 single-system run may keep each block's neighbourhood in shared memory
+    int withhold;       // test hook: block 0 withholds its arrival at the launch's first grid barrier
     int uni;            // 1: uniform coefficients (see uni_swap / uni_other)
     int uni_swap;       // table index of the reactive pair coefficients (UNI)
     int uni_other;      // table index of the other pairs' coefficients (UNI)

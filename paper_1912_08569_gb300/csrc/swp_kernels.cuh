@@ -353,6 +353,10 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
     return v;
 }
 
+// Set (thread 0 of one block) when the launch must withhold that block's
+// arrival at its first grid barrier (a test of the bounded waits).
+static __shared__ int s_withhold;
+
 // Arrival: the block's writes are ordered before a release add on the
 // counter (after the block-wide __syncthreads, thread 0's release is
 // cumulative over them).  Generation g completes at count g * (group size).
@@ -371,7 +375,10 @@ __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_
         }
         if (kBatched && g_size() == 1) return;  // a group of one block: __syncthreads is the barrier
         b.target += g_size();
-        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
+        if (s_withhold)
+            s_withhold = 0;  // this arrival is withheld: every wait of the barrier runs out
+        else
+            asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&ctl->barrier), "l"(1ull) : "memory");
     }
 }
 
@@ -414,29 +421,76 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
 // ---------------------------------------------------------------------------
 // Block reductions
 
-// Sums the per-thread accumulators over the block into partials[slot][q],
-// in the arithmetic precision (at most 1024 terms per block), through a
-// shared staging area of kNQA x blockDim values: ten warps do the sums while
-// the others go on (fewer shuffles than a tree over every warp); the block
-// totals are summed over blocks in FP64 (reduce_thermo).  FP64 runs at a
-// small fraction of the FP32 rate on this part, so it is kept out of the
-// per-thread work.
-template <typename Real>
-__device__ __forceinline__ void block_thermo(const Real* acc, double* out, Real* stage)
+// Compensated FP32 summation (Knuth's TwoSum; the double-float addition of
+// Dekker and Bailey): a pair (hi, lo) carries about 44 significant bits, so
+// the block sums below lose nothing beyond the per-thread FP32 terms.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    // thread t's values go to stage[q * B + t]; warp q then sums quantity q over
-    // the block in a fixed order (32 values per lane, then the lanes)
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
+{
+    float s, e;
+    two_sum(hi, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// Sums the per-thread accumulators over the block, through a shared staging
+// area of kNQA x blockDim values: thread t's values go to stage[q * B + t],
+// then warp q sums quantity q in a fixed order (32 values per lane, then the
+// lanes) while the other warps go on.  FP32 runs: compensated (double-float)
+// sums, so the block total is as accurate as an FP64 sum of the FP32 thread
+// values; FP64 runs: plain FP64 sums.  The total is added to the block's FP64
+// running sum blk[q]; with out given, blk[q] is then written to out[q] (the
+// block's partial of the pass) and cleared.  Each thread holds the terms of one
+// sub-chunk at most (multi-chunk passes flush after every sub-chunk), so the
+// error does not grow with the system size; block partials are summed over
+// blocks in FP64 (run_reduce_thermo / reduce_finish).
+__device__ __forceinline__ double warp_total(int lane, const float* row, int B)
+{
+    float hi = 0.0f, lo = 0.0f;
+    for (int k = lane; k < B; k += 32) df_add(hi, lo, row[k], 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        df_add(hi, lo, h2, l2);
+    }
+    return (double)hi + (double)lo;
+}
+
+__device__ __forceinline__ double warp_total(int lane, const double* row, int B)
+{
+    double s = 0.0;
+    for (int k = lane; k < B; k += 32) s += row[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+template <typename Real>
+__device__ __forceinline__ void block_sums(const Real* acc, Real* stage, double* blk, double* out)
+{
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, B = blockDim.x;
 #pragma unroll
     for (int q = 0; q < kNQA; q++) stage[q * B + t] = acc[q];
     __syncthreads();
     if (warp < kNQA) {
-        Real x = Real(0);
-        for (int k = lane; k < B; k += 32) x += stage[warp * B + k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) out[warp] = (double)x;
-    } else if (warp == kNQA && lane < kNQ - kNQA) {
+        const double tot = blk[warp] + warp_total(lane, stage + warp * B, B);
+        if (lane == 0) {
+            if (out) {
+                out[warp] = tot;
+                blk[warp] = 0.0;
+            } else {
+                blk[warp] = tot;
+            }
+        }
+    } else if (out && warp == kNQA && lane < kNQ - kNQA) {
         out[kNQA + lane] = 0.0;
     }
     __syncthreads();
@@ -870,6 +924,21 @@ __device__ __forceinline__ void cp_async_r4(R4* smem, const R4* gmem)
 // ---------------------------------------------------------------------------
 // S pass: S_i = sum over reactive partners k inside r_cut of a vh(r_ik).
 
+// One reactive entry's term of S_i: a vh(r_ij) inside r_cut, else 0 (evaluated
+// for every listed pair and selected by the cut-off decision, see entry_force).
+template <typename Real, bool UNI>
+__device__ __forceinline__ Real s_term(const Dev<Real>& d, const PairP<Real>* tab, const PairP<Real>& ps,
+                                       const typename Dev<Real>::P4& pi, const typename Dev<Real>::P4& pj)
+{
+    const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(pj), d.ntypes, ps);
+    Real dx, dy, dz;
+    const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+    Real v, f;
+    lj_eval(p, r2, v, f);
+    const Real vh = r2 > p.rmin2 ? (p.vshift - v) * p.inv_epshat : Real(1);
+    return r2 < p.rc2 ? mul_rn(p.a, vh) : Real(0);
+}
+
 // staged: the block has one sub-chunk and the shared copies of its positions
 // and list ranges are current (kept by the previous force pass), so they are
 // not loaded again.  With one sub-chunk the block's S values also stay in
@@ -915,15 +984,7 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
                     j_n = d.ent_j[e + B];
                     o_n = d.ent_o[e + B];
                 }
-                const P4 pi = SM::pos()[o_c];
-                const PairP<Real>& p = pair_of<Real, UNI>(tab, type_of(pi), type_of(p_c), d.ntypes, ps);
-                Real dx, dy, dz;
-                const Real r2 = dist2_listed(pi, p_c, d, dx, dy, dz);
-                // selected, not branched (see entry_force)
-                Real v, f;
-                lj_eval(p, r2, v, f);
-                const Real vh = r2 > p.rmin2 ? (p.vshift - v) * p.inv_epshat : Real(1);
-                SM::w()[e - wb] = r2 < p.rc2 ? p.a * vh : Real(0);
+                SM::w()[e - wb] = s_term<Real, UNI>(d, tab, ps, SM::pos()[o_c], p_c);
                 e += B;
                 j_c = j_n;
                 o_c = o_n;
@@ -979,37 +1040,35 @@ __device__ __forceinline__ void load_pstate(const Dev<Real>& d, int ac, int i, i
     }
 }
 
-// Adds a displacement to one fixed-point coordinate, wraps it into the box
-// (counting the image) and returns the new fixed-point coordinate.
-template <typename Real>
-__device__ __forceinline__ long long advance_fix(const Dev<Real>& d, int ac, int i, int c, long long q0,
-                                                 Real dx)
+// Adds a displacement to one fixed-point coordinate and wraps it into the box;
+// w gets the change of the image count (-1, 0 or +1).
+__device__ __forceinline__ long long advance_fix(long long q0, long long Lq, long long dq, int& w)
 {
-    const int n = d.n;
-    long long q = q0 + real_to_fix(dx);
-    const long long Lq = d.Lq[c];
+    const long long q = q0 + dq;
     if (q >= Lq) {
-        q -= Lq;
-        d.img[ac][c * n + i] += 1;
-    } else if (q < 0) {
-        q += Lq;
-        d.img[ac][c * n + i] -= 1;
+        w = 1;
+        return q - Lq;
     }
-    d.xq[ac][c * n + i] = q;
+    if (q < 0) {
+        w = -1;
+        return q + Lq;
+    }
+    w = 0;
     return q;
 }
 
-// Advances particle i given its force.  Returns the squared displacement of
-// this step's drift (0 when not opening).
+// The integrator on one particle's registers: the closing half kick of the
+// step that ends, the kinetic energy, and (opening) the half kick, half drift,
+// Langevin O step and half drift of the next (BAOAB; velocity Verlet without
+// O).  q[] (fixed point) and v are advanced in place, w[] gets the image
+// changes, np the new snapshot.  Returns the squared displacement of the drift
+// (0 when not opening).
 template <typename Real>
-__device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs& a, int pc,
-                                               int ac, int i, Real fx, Real fy, Real fz,
-                                               int flags, long long step, PState<Real>& st,
-                                               int wbits, Real& kin, typename Dev<Real>::P4* keep)
+__device__ __forceinline__ float advance_particle(const Dev<Real>& d, const RunArgs& a, Real fx, Real fy, Real fz,
+                                                  int flags, long long step, int wbits,
+                                                  typename Dev<Real>::R4& v, long long q[3], int w[3], Real& kin,
+                                                  typename Dev<Real>::P4& np)
 {
-    typedef typename Dev<Real>::R4 R4;
-    typedef typename Dev<Real>::P4 P4;
-    R4 v = st.v;
     const Real im = v.w;
     const Real hdt = pick(Real(0), a.hdt_f, a.hdt_d);
     if (flags & F_CLOSING) {
@@ -1019,6 +1078,7 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
     }
     kin += Real(0.5) * (v.x * v.x + v.y * v.y + v.z * v.z) * recip(im);
     float disp2 = 0.0f;
+    w[0] = w[1] = w[2] = 0;
     if (flags & F_OPENING) {
         v.x += hdt * fx * im;
         v.y += hdt * fy * im;
@@ -1037,11 +1097,37 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         ddy += hdt * v.y;
         ddz += hdt * v.z;
         disp2 = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
-        P4 np;
-        np.x = snap_coord(advance_fix(d, ac, i, 0, st.q[0], ddx), 0, d);
-        np.y = snap_coord(advance_fix(d, ac, i, 1, st.q[1], ddy), 1, d);
-        np.z = snap_coord(advance_fix(d, ac, i, 2, st.q[2], ddz), 2, d);
+        q[0] = advance_fix(q[0], d.Lq[0], real_to_fix(ddx), w[0]);
+        q[1] = advance_fix(q[1], d.Lq[1], real_to_fix(ddy), w[1]);
+        q[2] = advance_fix(q[2], d.Lq[2], real_to_fix(ddz), w[2]);
+        np.x = snap_coord(q[0], 0, d);
+        np.y = snap_coord(q[1], 1, d);
+        np.z = snap_coord(q[2], 2, d);
         np.w = snap_bits(wbits, d);
+    }
+    return disp2;
+}
+
+// Advances particle i given its force (state from global memory, written
+// back there; the image count is touched only when the particle wraps).
+// Returns the squared displacement of this step's drift (0 when not opening).
+template <typename Real>
+__device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs& a, int pc,
+                                               int ac, int i, Real fx, Real fy, Real fz,
+                                               int flags, long long step, PState<Real>& st,
+                                               int wbits, Real& kin, typename Dev<Real>::P4* keep)
+{
+    typename Dev<Real>::R4 v = st.v;
+    typename Dev<Real>::P4 np;
+    int w[3];
+    const float disp2 = advance_particle(d, a, fx, fy, fz, flags, step, wbits, v, st.q, w, kin, np);
+    if (flags & F_OPENING) {
+        const int n = d.n;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            d.xq[ac][c * n + i] = st.q[c];
+            if (w[c]) d.img[ac][c * n + i] += w[c];
+        }
         d.pos[pc ^ 1][i] = np;
         if (keep) *keep = np;
     }
@@ -1111,7 +1197,7 @@ __device__ __forceinline__ void sum_run(const R4* w, int wb, int k0, int k1, Rea
 template <typename Real, bool UNI, bool BONDS>
 __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const RunArgs& a, int pc,
                               int ac, int flags, long long step, Acc<Real>& acc,
-                              const PairP<Real>& ps, const PairP<Real>& pw)
+                              const PairP<Real>& ps, const PairP<Real>& pw, double* blk)
 {
     typedef Stage<Real> SM;
     typedef typename Dev<Real>::R4 R4;
@@ -1229,6 +1315,13 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             for (int q = 0; q < kNQA; q++) acc.q[q] = SM::w()[q * blockDim.x + t];
         acc.q[Q_K] += kin;
         __syncthreads();
+        if (!single) {
+            // several sub-chunks: fold this one's terms into the block's FP64
+            // running sums, so no thread accumulates more than one sub-chunk
+            block_sums(acc.q, SM::w(), blk, (double*)nullptr);
+#pragma unroll
+            for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
+        }
     }
     return dmax;
 }
@@ -1268,11 +1361,20 @@ struct LoopState {
     unsigned dmax_bits;  // the block's largest squared step displacement (float bits)
     int own_ok;          // shared positions and list ranges of the block's particles are current
     int red_pending;     // a thermo reduction's copies are in flight into s_rbuf
+    // resident mode (section below)
+    int r_try;           // build the resident structures before the next step
+    int r_valid;         // every block's resident structures are built and current
+    int r_gathered;      // the next step's copies were issued after the last barrier
+    int r_round;         // agreement round (selects ctl->rfail[round & 1])
+    int r_fail;          // this block's structures do not fit
+    int r_np, r_nh, r_nhr;  // own particles, halo particles, halo rows of S
+    int r_steps;         // steps this launch took in the resident mode
 };
 
 static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
 static __shared__ double s_red[kNQ * 32];
 static __shared__ double s_rbuf[kMaxGrid];
+static __shared__ double s_blk[kNQ];  // the block's FP64 running thermo sums of the current pass
 static __shared__ int s_int[64];
 static __shared__ LoopState s_ls;
 
@@ -1369,7 +1471,7 @@ __device__ __forceinline__ void run_f_pass(const Dev<Real>& d, const RunArgs& a,
 #pragma unroll
     for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
     const float dmax = f_pass_block<Real, UNI, BONDS>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
-                                               uni_params(a, Real(0))[0], uni_params(a, Real(0))[1]);
+                                                      uni_params(a, Real(0))[0], uni_params(a, Real(0))[1], s_blk);
     if (flags & F_OPENING) warp_max_disp(dmax);
 }
 
@@ -1426,10 +1528,11 @@ __device__ __forceinline__ void reduce_small(const Dev<Real>& d, const RunArgs& 
 
 // The same reduction in two halves, kept off the blocks' critical path: at a
 // force-pass barrier block q (< kNQA) starts asynchronous copies of quantity
-// q of every block's partials of the previous pass into s_rbuf; before it
-// arrives at the next S-pass barrier it waits for them (so nothing is still
-// reading the partials when the next force pass overwrites that buffer), and
-// while waiting at that barrier it sums them in a fixed order.
+// q of every block's partials of the previous pass into s_rbuf; the copies are
+// waited for before the block's next barrier arrival (so the buffer may be
+// written again from that barrier on: the partials rotate over kParities
+// buffers, and the buffer read here is written next two passes later), and the
+// sum is formed in a fixed order after that arrival.
 template <typename Real>
 __device__ __forceinline__ void reduce_issue(const Dev<Real>& d, const RunArgs& a, int par)
 {
@@ -1461,26 +1564,31 @@ __device__ __forceinline__ void reduce_finish(const Dev<Real>& d)
 
 // The barrier that ends a force pass.  After arriving (and publishing the
 // block's displacement maximum when the pass drifted), while the other blocks
-// finish, the block sums its thermo accumulators of this pass into its
-// partials, and the blocks that own a quantity start the reduction of the
-// previous pass's partials: every block wrote those before arriving at the
-// barrier that followed that pass, which this block has passed.
+// finish, the block completes a reduction still pending from the previous
+// barrier, sums its thermo accumulators of this pass into its partials (stage:
+// kNQA x blockDim values of free shared memory), and the blocks that own a
+// quantity start the reduction of the previous pass's partials: every block
+// wrote those before arriving at the barrier that followed that pass, which
+// this block has passed.
 template <typename Real>
 __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, const Acc<Real>& acc,
-                                          int par, unsigned* pub_dst, int where)
+                                          int par, unsigned* pub_dst, int where, Real* stage)
 {
     BarState bs;
     bs.target = s_ls.bar_target;
     bar_arrive(d.ctl, bs, pub_dst, &s_ls.dmax_bits);
     const int had = s_ls.have_thermo, prev = s_ls.parity;
-    // the wave buffer is free from the end of the force pass to the next S pass
-    block_thermo(acc.q, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ, Stage<Real>::w());
+    if (s_ls.red_pending) {
+        cp_async_wait_all();  // each thread's own copy into s_rbuf
+        reduce_finish(d);
+    }
+    block_sums(acc.q, stage, s_blk, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ);
     // groups of at least kNQA blocks: one quantity per block, asynchronously;
     // smaller groups reduce every quantity here
     const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
     if (red) reduce_issue(d, a, prev);
     if (kBatched && had && g_size() < kNQA) reduce_small(d, a, prev);
-    if (threadIdx.x == 0) {  // every thread read the old values before block_thermo's barriers
+    if (threadIdx.x == 0) {  // every thread read the old values before block_sums' barriers
         s_ls.bar_target = bs.target;
         s_ls.parity = par;
         s_ls.have_thermo = 1;
@@ -1496,17 +1604,411 @@ __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
     __syncthreads();
 }
 
+#if !SWP_BATCHED
+// ---------------------------------------------------------------------------
+// Resident mode: one system, FP32, no bonds, every block's particles in one
+// sub-chunk (up to blockDim x grid particles).
+//
+// After each list build every block copies into shared memory what its steps
+// need: the snapshots of its own particles and of its halo -- every particle
+// outside the block that is a list partner of an own particle, plus every
+// reactive partner of those that are reactive partners of an own particle --
+// the own rows, and the reactive rows of that first halo shell (each the
+// owner's row, in the owner's order), all with partners as 16-bit local
+// indices.  A step then copies the halo's new snapshots in once (one bulk
+// asynchronous copy), forms S for the own particles and for the reactive halo
+// from shared memory (a halo row is its owner's row, evaluated in the same
+// order with the same operations, so both blocks hold bit-identical S), and
+// the pair forces and the integrator with no further global gather: one grid
+// barrier per step instead of two, and no chains of dependent L2 round trips
+// inside a step.  Forces and trajectories are bit-identical to the two-barrier
+// path (same per-entry operations, same summation orders); only the thermo
+// partials are grouped differently.
+
+struct RStage {
+    static constexpr int kL = 3 * kBlock;   // local particles: own (<= kBlock), then halo
+    static constexpr int kH = kL - kBlock;  // halo particles; also the bound on halo rows of S
+    static constexpr int kE = 16384;        // local entries (16-bit partner indices)
+    static constexpr int kHash = 4096;      // open-addressing table of halo slots (while building)
+    static constexpr size_t O_LPOS = 0;                            // [kL] int4 snapshots
+    static constexpr size_t O_LS = O_LPOS + (size_t)kL * 16;       // [kL] float S
+    static constexpr size_t O_HSLOT = O_LS + (size_t)kL * 4;       // [kH] int global slots of the halo
+    static constexpr size_t O_ENT = O_HSLOT + (size_t)kH * 4;      // [kE] u16 local partner indices
+    static constexpr size_t O_OROW = O_ENT + (size_t)kE * 2;       // [kBlock] own rows: first | nr << 16 | nw << 24
+    static constexpr size_t O_SROW = O_OROW + (size_t)kBlock * 4;  // [kH] int2 halo S rows: (first | n << 16, centre)
+    static constexpr size_t O_VEL = O_SROW + (size_t)kH * 8;       // [kBlock] float4 staged velocities
+    static constexpr size_t O_XQ = O_VEL + (size_t)kBlock * 16;    // [3 kBlock] staged fixed-point positions
+    static constexpr size_t O_IMG = O_XQ + (size_t)kBlock * 24;    // [3 kBlock] staged image counts
+    static constexpr size_t kBytes = O_IMG + (size_t)kBlock * 12;
+    // the thermo staging (kNQA x kBlock floats) and the build's hash table
+    // (2 x kHash ints) reuse the staging area from O_VEL on
+    static_assert((size_t)kNQA * kBlock * 4 <= kBytes - O_VEL, "thermo staging");
+    static_assert((size_t)2 * kHash * 4 <= kBytes - O_VEL, "hash table");
+    static_assert(kE <= 65536 && kL <= 65536, "16-bit local indices");
+    static_assert(kHash % kBlock == 0 && kH % kBlock == 0, "whole rounds per thread");
+
+    static __device__ __forceinline__ int4* lpos() { return (int4*)(g_dyn + O_LPOS); }
+    static __device__ __forceinline__ float* lS() { return (float*)(g_dyn + O_LS); }
+    static __device__ __forceinline__ int* hslot() { return (int*)(g_dyn + O_HSLOT); }
+    static __device__ __forceinline__ unsigned short* ent() { return (unsigned short*)(g_dyn + O_ENT); }
+    static __device__ __forceinline__ unsigned* orow() { return (unsigned*)(g_dyn + O_OROW); }
+    static __device__ __forceinline__ int2* srow() { return (int2*)(g_dyn + O_SROW); }
+    static __device__ __forceinline__ float4* vel() { return (float4*)(g_dyn + O_VEL); }
+    static __device__ __forceinline__ long long* xq() { return (long long*)(g_dyn + O_XQ); }
+    static __device__ __forceinline__ int* img() { return (int*)(g_dyn + O_IMG); }
+    static __device__ __forceinline__ float* stage() { return (float*)(g_dyn + O_VEL); }
+};
+static_assert(RStage::kBytes <= Stage<float>::kBytes, "the resident layout reuses the staging buffer");
+
+__device__ __forceinline__ void cp_async_cg16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ unsigned r_hash(int q) { return ((unsigned)q * 2654435761u) >> 20; }
+
+// Inserts slot q into the table (if absent); its index, or -1 when full.
+__device__ __forceinline__ int r_insert(int* key, int q)
+{
+    unsigned h = r_hash(q) & (RStage::kHash - 1);
+    for (int probe = 0; probe < RStage::kHash; probe++) {
+        const int old = atomicCAS(&key[h], -1, q);
+        if (old == -1 || old == q) return (int)h;
+        h = (h + 1) & (RStage::kHash - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int r_find(const int* key, int q)
+{
+    unsigned h = r_hash(q) & (RStage::kHash - 1);
+    for (int probe = 0; probe < RStage::kHash; probe++) {
+        const int k = key[h];
+        if (k == q) return (int)h;
+        if (k == -1) return -1;
+        h = (h + 1) & (RStage::kHash - 1);
+    }
+    return -1;
+}
+
+// Local index of global slot q: own particles first (q - b0), then the halo
+// (P + compact rank, kept in val >> 1).
+__device__ __forceinline__ int r_lid(const int* key, const int* val, int q, int b0, int b1, int P, int& fail)
+{
+    if (q >= b0 && q < b1) return q - b0;
+    const int h = r_find(key, q);
+    if (h < 0) {
+        fail = 1;
+        return 0;
+    }
+    return P + (val[h] >> 1);
+}
+
+// Builds the block's resident structures from the global list and the
+// snapshots pos[pc].  Returns 1 when they fit (the same answer in every
+// thread of the block); 0 leaves nothing the step relies on.
+static __device__ int r_localize(const Dev<float>& d, int pc)
+{
+    typedef RStage RS;
+    constexpr int PER = RS::kHash / kBlock, RR = RS::kH / kBlock;
+    int4* lpos = RS::lpos();
+    int* hslot = RS::hslot();
+    unsigned short* ent = RS::ent();
+    int2* srow = RS::srow();
+    int* key = (int*)RS::stage();
+    int* val = key + RS::kHash;  // bit 0: reactive partner of an own particle; then the compact rank << 1
+    const int t = threadIdx.x, B = blockDim.x;
+    int b0, b1;
+    block_range(d, b0, b1);
+    const int P = b1 - b0;
+    if (B != kBlock || P > B) return 0;
+    for (int h = t; h < RS::kHash; h += B) {
+        key[h] = -1;
+        val[h] = 0;
+    }
+    __syncthreads();
+    int fail = 0;
+    int e_beg = 0, e_rend = 0, e_end = 0;
+    if (P > 0) {
+        const int4 f0 = d.pinfo[b0], f1 = d.pinfo[b1 - 1];
+        e_beg = f0.x;
+        e_rend = f1.x + f1.y;
+        e_end = f1.z + f1.w;
+    }
+    // 1. first shell: the partners of the own rows outside the block
+    for (int e = e_beg + t; e < e_end; e += B) {
+        const int q = d.ent_j[e];
+        if (q < b0 || q >= b1) {
+            const int h = r_insert(key, q);
+            if (h < 0) fail = 1;
+            else if (e < e_rend) atomicOr(&val[h], 1);
+        }
+    }
+    if (__syncthreads_or(fail)) return 0;
+    // 2. its reactive part (their S is formed here too), in table order
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < PER; k++) c += val[t * PER + k] & 1;
+    int Hr;
+    int off = block_excl_scan(c, s_int, &Hr);
+    if (Hr > RS::kH) return 0;  // Hr is the same in every thread
+#pragma unroll
+    for (int k = 0; k < PER; k++)
+        if (val[t * PER + k] & 1) srow[off++].y = t * PER + k;  // table index, for now
+    __syncthreads();
+    // 3. second shell: the reactive partners of the reactive first shell
+    for (int k = t; k < Hr; k += B) {
+        const int4 fi = d.pinfo[key[srow[k].y]];
+        for (int e = fi.x; e < fi.x + fi.y; e++) {
+            const int q = d.ent_j[e];
+            if ((q < b0 || q >= b1) && r_insert(key, q) < 0) fail = 1;
+        }
+    }
+    if (__syncthreads_or(fail)) return 0;
+    // 4. compact the table: halo particle of rank r has local index P + r
+    c = 0;
+#pragma unroll
+    for (int k = 0; k < PER; k++) c += key[t * PER + k] != -1;
+    int H;
+    off = block_excl_scan(c, s_int, &H);
+    if (H > RS::kH || P + H > RS::kL) return 0;
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const int h = t * PER + k;
+        if (key[h] != -1) {
+            hslot[off] = key[h];
+            val[h] = (val[h] & 1) | (off << 1);
+            off++;
+        }
+    }
+    // 5. entry offsets: the own rows, then the halo rows of S
+    int4 inf = make_int4(0, 0, 0, 0);
+    if (t < P) inf = d.pinfo[b0 + t];
+    if (inf.y > 255 || inf.w > 255) fail = 1;
+    int Eo;
+    const int st_own = block_excl_scan(inf.y + inf.w, s_int, &Eo);
+    int st_h[RR], cnt_h[RR], cen_h[RR];
+    int base = Eo;
+#pragma unroll
+    for (int r = 0; r < RR; r++) {
+        const int k = t + r * B;
+        int cn = 0, h = 0;
+        if (k < Hr) {
+            h = srow[k].y;
+            cn = d.pinfo[key[h]].y;
+        }
+        int tot;
+        st_h[r] = base + block_excl_scan(cn, s_int, &tot);
+        base += tot;
+        cnt_h[r] = cn;
+        cen_h[r] = h;
+    }
+    if (base > RS::kE) fail = 1;
+    if (__syncthreads_or(fail)) return 0;
+    // 6. the rows, partners as local indices, and the own snapshots
+    if (t < P) {
+        for (int k = 0; k < inf.y; k++)
+            ent[st_own + k] = (unsigned short)r_lid(key, val, d.ent_j[inf.x + k], b0, b1, P, fail);
+        for (int k = 0; k < inf.w; k++)
+            ent[st_own + inf.y + k] = (unsigned short)r_lid(key, val, d.ent_j[inf.z + k], b0, b1, P, fail);
+        RS::orow()[t] = (unsigned)st_own | ((unsigned)inf.y << 16) | ((unsigned)inf.w << 24);
+        lpos[t] = d.pos[pc][b0 + t];
+    }
+#pragma unroll
+    for (int r = 0; r < RR; r++) {
+        const int k = t + r * B;
+        if (k < Hr) {
+            const int h = cen_h[r];
+            const int4 fi = d.pinfo[key[h]];
+            for (int m = 0; m < cnt_h[r]; m++)
+                ent[st_h[r] + m] = (unsigned short)r_lid(key, val, d.ent_j[fi.x + m], b0, b1, P, fail);
+            srow[k] = make_int2(st_h[r] | (cnt_h[r] << 16), P + (val[h] >> 1));
+        }
+    }
+    if (t == 0) {
+        s_ls.r_np = P;
+        s_ls.r_nh = H;
+        s_ls.r_nhr = Hr;
+    }
+    return __syncthreads_or(fail) ? 0 : 1;
+}
+
+// Issues a step's copies: the halo's snapshots pos[pc] (L2 only: other blocks
+// wrote them) and the own particles' velocities, fixed-point positions and
+// image counts (set ac).
+__device__ __forceinline__ void r_gather(const Dev<float>& d, int pc, int ac)
+{
+    typedef RStage RS;
+    const int t = threadIdx.x, B = blockDim.x, P = s_ls.r_np, H = s_ls.r_nh, n = d.n;
+    int b0, b1;
+    block_range(d, b0, b1);
+    int4* lpos = RS::lpos();
+    const int* hslot = RS::hslot();
+    const int4* pos = d.pos[pc];
+    for (int h = t; h < H; h += B) cp_async_cg16(&lpos[P + h], &pos[hslot[h]]);
+    if (t < P) {
+        const int i = b0 + t;
+        cp_async_cg16(&RS::vel()[t], &d.vel[ac][i]);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            cp_async(&RS::xq()[3 * t + c], &d.xq[ac][c * n + i], 8);
+            cp_async(&RS::img()[3 * t + c], &d.img[ac][c * n + i], 4);
+        }
+    }
+    cp_async_commit();
+}
+
+// S of one row (first..first+cnt of ent) with the two-barrier path's order of
+// additions (groups of four, then one by one).
+template <bool UNI>
+__device__ __forceinline__ float r_row_s(const Dev<float>& d, const PairP<float>* tab, const PairP<float>& ps,
+                                         const int4* lpos, const unsigned short* e, int cnt, const int4& pi)
+{
+    float s = 0.0f;
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {
+        const float w0 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k]]);
+        const float w1 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k + 1]]);
+        const float w2 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k + 2]]);
+        const float w3 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k + 3]]);
+        s += (w0 + w1) + (w2 + w3);
+    }
+    for (; k < cnt; k++) s += s_term<float, UNI>(d, tab, ps, pi, lpos[e[k]]);
+    return s;
+}
+
+// One resident step: S of the own particles and the reactive halo, the pair
+// forces of the own rows (entry order: reactive, then the others), the
+// integrator.  Returns the thread's squared drift displacement.
+template <bool UNI>
+__device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long long step, Acc<float>& acc)
+{
+    typedef RStage RS;
+    const int t = threadIdx.x, B = blockDim.x, n = d.n;
+    const int P = s_ls.r_np, nS = P + s_ls.r_nhr;
+    const int pc = s_ls.pc, ac = s_ls.ac;
+    int b0, b1;
+    block_range(d, b0, b1);
+    if (!s_ls.r_gathered) r_gather(d, pc, ac);
+    cp_async_wait_all();
+    __syncthreads();
+    const PairP<float>* tab = stab<float>();
+    const PairP<float>& ps = a.uf[0];
+    const PairP<float>& pw = a.uf[1];
+    int4* lpos = RS::lpos();
+    float* lS = RS::lS();
+    const unsigned short* ent = RS::ent();
+    for (int r = t; r < nS; r += B) {
+        int first, cnt, lid;
+        if (r < P) {
+            const unsigned o = RS::orow()[r];
+            first = (int)(o & 0xffffu);
+            cnt = (int)((o >> 16) & 0xffu);
+            lid = r;
+        } else {
+            const int2 sr = RS::srow()[r - P];
+            first = sr.x & 0xffff;
+            cnt = (int)((unsigned)sr.x >> 16);
+            lid = sr.y;
+        }
+        lS[lid] = r_row_s<UNI>(d, tab, ps, lpos, ent + first, cnt, lpos[lid]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kNQA; q++) acc.q[q] = 0.0f;
+    float dmax = 0.0f, kin = 0.0f;
+    int4 np = make_int4(0, 0, 0, 0);
+    if (t < P) {
+        const unsigned o = RS::orow()[t];
+        const int first = (int)(o & 0xffffu), nr = (int)((o >> 16) & 0xffu), nw = (int)(o >> 24);
+        const int4 pi = lpos[t];
+        const float Si = lS[t];
+        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+        for (int k = 0; k < nr; k++) {
+            const int j = ent[first + k];
+            float ex, ey, ez;
+            entry_force<float, UNI, true>(d, tab, pi, lpos[j], Si, lS[j], ps, acc, ex, ey, ez);
+            fx = __fadd_rn(fx, ex);
+            fy = __fadd_rn(fy, ey);
+            fz = __fadd_rn(fz, ez);
+        }
+        for (int k = nr; k < nr + nw; k++) {
+            const int j = ent[first + k];
+            float ex, ey, ez;
+            entry_force<float, UNI, false>(d, tab, pi, lpos[j], 0.0f, 0.0f, pw, acc, ex, ey, ez);
+            fx = __fadd_rn(fx, ex);
+            fy = __fadd_rn(fy, ey);
+            fz = __fadd_rn(fz, ez);
+        }
+        const int i = b0 + t;
+        if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&d.ctl->status, kStatusNonfinite);
+        if (flags & F_STORE) d.force[i] = make_float4(fx, fy, fz, 0.0f);
+        float4 v = RS::vel()[t];
+        long long q[3];
+        int w[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) q[c] = RS::xq()[3 * t + c];
+        dmax = advance_particle(d, a, fx, fy, fz, flags, step, pi.w, v, q, w, kin, np);
+        if (flags & F_OPENING) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                d.xq[ac][c * n + i] = q[c];
+                if (w[c]) d.img[ac][c * n + i] = RS::img()[3 * t + c] + w[c];
+            }
+            d.pos[pc ^ 1][i] = np;
+        }
+        d.vel[ac][i] = v;
+    }
+    acc.q[Q_K] += kin;
+    __syncthreads();  // every row has read the old snapshots
+    if (t < P && (flags & F_OPENING)) lpos[t] = np;
+    if (t == 0) {
+        s_ls.r_gathered = 0;
+        s_ls.r_steps++;
+        s_ls.own_ok = 0;
+    }
+    return dmax;
+}
+
+// Builds every block's resident structures and agrees on the mode: the step
+// runs resident only if every block's structures fit.
+static __device__ bool r_enter(const Dev<float>& d, const RunArgs& a)
+{
+    const int ok = r_localize(d, s_ls.pc);
+    const int round = s_ls.r_round;
+    if (threadIdx.x == 0 && !ok) atomicOr(&d.ctl->rfail[round & 1], 1);
+    if (!grid_barrier(d.ctl, a.timeout_ns, 8)) return false;
+    if (threadIdx.x == 0) {
+        s_ls.r_valid = ld_relaxed(&d.ctl->rfail[round & 1]) == 0;
+        s_ls.r_try = 0;  // tried again after the next list build
+        s_ls.r_round = round + 1;
+        s_ls.r_gathered = 0;
+        s_ls.own_ok = 0;  // the build overwrote the two-barrier path's staging
+        // the next round's word: every block reads this round's word before it
+        // arrives at the next barrier, and the next round comes after it
+        if (g_rank() == 0) d.ctl->rfail[(round + 1) & 1] = 0;
+    }
+    __syncthreads();
+    return true;
+}
+#endif  // !SWP_BATCHED
+
 // One system advanced by the group of blocks this block belongs to (g_rank /
 // g_size set by the caller).  Returns false when a wait timed out (the status
 // word says so).
 template <typename Real, bool UNI, bool BONDS>
 __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 {
+    // the resident mode exists for one FP32 system without bonds
+    constexpr bool kRes = !kBatched && sizeof(Real) == 4 && !BONDS;
     Ctl* ctl = d.ctl;
     PairP<Real>* tab = (PairP<Real>*)s_tab_raw;
     const int ntt = d.ntypes * d.ntypes;
     for (int t = threadIdx.x; t < ntt; t += blockDim.x) tab[t] = d.table[t];
+    if (threadIdx.x < kNQ) s_blk[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
+        s_withhold = a.withhold && g_rank() == 0;
         s_ls.bar_target = 0;
         s_ls.step = ctl->step;
         s_ls.rebuilds = 0;
@@ -1525,6 +2027,18 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         s_ls.dmax_bits = 0u;
         s_ls.own_ok = 0;
         s_ls.red_pending = 0;
+        s_ls.r_try = (kRes && a.resident && single_chunk(d)) ? 1 : 0;
+        s_ls.r_valid = 0;
+        s_ls.r_gathered = 0;
+        s_ls.r_round = 0;
+        s_ls.r_fail = 0;
+        s_ls.r_np = s_ls.r_nh = s_ls.r_nhr = 0;
+        s_ls.r_steps = 0;
+        // both agreement words start clear: every round comes after a barrier
+        if (kRes && g_rank() == 0) {
+            ctl->rfail[0] = 0;
+            ctl->rfail[1] = 0;
+        }
     }
     __syncthreads();
     const float skin_eff = (float)a.skin_eff;
@@ -1551,11 +2065,11 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             if (s_ls.rc == 0) {
                 run_s_pass<Real, UNI>(d, a);
                 if (!grid_barrier(ctl, a.timeout_ns, 10)) return false;
-                const int par = (int)(s_ls.step & 1);
+                const int par = (int)(s_ls.step % kParities);
                 Acc<Real> acc;
                 run_f_pass<Real, UNI, BONDS>(d, a, F_STORE, s_ls.step, acc);
                 if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
-                if (!f_barrier(d, a, acc, par, nullptr, 11)) return false;
+                if (!f_barrier(d, a, acc, par, nullptr, 11, Stage<Real>::w())) return false;
             }
         }
         if (s_ls.rc == 0 && s_ls.remaining > 0 && s_ls.state == 0) {
@@ -1576,38 +2090,70 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             const long long stp = s_ls.step;
             if (threadIdx.x == 0 && g_rank() == 0) ctl->dmax2[(stp + 1) & 1] = 0u;
             if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
+                // a resident gather issued for this step lands in memory the rebuild reuses
+                cp_async_wait_all();
                 const int rc = run_rebuild(d, a);
                 if (rc == 2) return false;
                 if (threadIdx.x == 0) {
                     s_ls.need_rb = rc;
                     s_ls.rc = rc;
+                    s_ls.r_valid = 0;
+                    s_ls.r_gathered = 0;
+                    s_ls.r_try = (kRes && a.resident && single_chunk(d)) ? 1 : 0;
                 }
                 __syncthreads();
                 if (rc) break;
             }
             const bool more = s_ls.remaining > 1;
-            run_s_pass<Real, UNI>(d, a);
-            const bool fin = s_ls.red_pending;
-            if (fin) cp_async_wait_all();
-            {
-                BarState bs;
-                bs.target = s_ls.bar_target;
-                bar_arrive(ctl, bs);
-                if (fin) reduce_finish(d);
-                if (threadIdx.x == 0) s_ls.bar_target = bs.target;
-                if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return false;
-            }
-            const int par = (int)((stp + 1) & 1);
+            const int par = (int)((stp + 1) % kParities);
+            const int flags = F_CLOSING | (more ? F_OPENING : F_STORE);
             Acc<Real> acc;
-            run_f_pass<Real, UNI, BONDS>(d, a, F_CLOSING | (more ? F_OPENING : F_STORE), stp + 1, acc);
+            Real* stage = Stage<Real>::w();
+            bool resident = false;
+#if !SWP_BATCHED
+            if constexpr (kRes) {
+                if (s_ls.r_try)
+                    if (!r_enter(d, a)) return false;
+                if (s_ls.r_valid) {
+                    const float dmax = r_step<UNI>(d, a, flags, stp + 1, acc);
+                    if (more) warp_max_disp(dmax);
+                    stage = (Real*)RStage::stage();
+                    resident = true;
+                }
+            }
+#endif
+            if (!resident) {
+                run_s_pass<Real, UNI>(d, a);
+                const bool fin = s_ls.red_pending;
+                if (fin) cp_async_wait_all();
+                {
+                    BarState bs;
+                    bs.target = s_ls.bar_target;
+                    bar_arrive(ctl, bs);
+                    if (fin) reduce_finish(d);
+                    if (threadIdx.x == 0) s_ls.bar_target = bs.target;
+                    if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return false;
+                }
+                run_f_pass<Real, UNI, BONDS>(d, a, flags, stp + 1, acc);
+            }
             if (threadIdx.x == 0) {  // every thread read `remaining` before the pass's barriers
                 s_ls.step = stp + 1;
                 s_ls.remaining--;
                 s_ls.done++;
             }
-            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21)) return false;
+            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21, stage)) return false;
             if (more) {
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
+                __syncthreads();
+#if !SWP_BATCHED
+                if constexpr (kRes) {
+                    // the next step's copies overlap the displacement read
+                    if (s_ls.r_valid) {
+                        r_gather(d, s_ls.pc, s_ls.ac);
+                        if (threadIdx.x == 0) s_ls.r_gathered = 1;
+                    }
+                }
+#endif
                 add_disp(ctl, stp + 1);
             } else {
                 if (threadIdx.x == 0) s_ls.state = 0;
@@ -1633,6 +2179,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         ctl->n_rebuilds += s_ls.rebuilds;
         ctl->steps_done = s_ls.done;
         ctl->need_rebuild = s_ls.need_rb;
+        ctl->resident_steps = s_ls.r_steps;
         if (s_ls.rebuilds > 0) {
             ctl->list_grid = s_ls.rc == 0 ? g_size() : -1;
             ctl->list_chunk = blockDim.x;

@@ -83,6 +83,10 @@ class SwapSystem:
     def set_timeout(self, ns: int):
         A.swp_set_timeout(self.ctx, ns)
 
+    def set_resident(self, enable: bool = True):
+        """Allow (default) or forbid the resident mode of the FP32 step."""
+        A.swp_set_resident(self.ctx, 1 if enable else 0)
+
     # -- state --------------------------------------------------------------
     def set_state(self, x, v=None, types=None, mass=None, img=None):
         """Host arrays (numpy) or device tensors (torch, cuda) in user order."""
@@ -157,7 +161,7 @@ class SwapSystem:
         t = A.swp_read_thermo(self.ctx)
         return dict(U2=t.U2, U3=t.U3, K=t.K, W=np.array(list(t.W)), n_bonds=int(t.n_bonds),
                     step=int(t.step), n_rebuilds=int(t.n_rebuilds), steps_done=int(t.steps_done),
-                    max_row=int(t.max_row), state=int(t.state))
+                    max_row=int(t.max_row), state=int(t.state), resident_steps=int(t.resident_steps))
 
     def forces(self) -> np.ndarray:
         f = np.zeros((max(self.n, 1), 3))

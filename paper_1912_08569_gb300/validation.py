@@ -78,11 +78,13 @@ def fit_tau(t, c, cmin=0.05):
 
 
 def run(kT=0.03, replicas=8, t_equil=20.0, t_max=400.0, sample_dt=1.0, seed=1, precision="fp32", split=1e9,
-        light_mass=None):
+        light_mass=None, keep_final=False):
     """Advances `replicas` independent dumbbell systems together (one batched
     launch per sample interval) and returns the bond statistics.  light_mass:
     give half of the A particles (seeded choice) this mass and also return the
-    statistics of the light-A and heavy-A bonds separately."""
+    statistics of the light-A and heavy-A bonds separately.  keep_final: also
+    return every replica's last positions with the kernel's bond count of that
+    step ("final": list of dicts x, types, box, pairs, n_bonds)."""
     from .system import SwapBatch, SwapSystem
 
     wls = [inputs.dumbbell_workload(seed=seed + 17 * r, kT=kT) for r in range(replicas)]
@@ -135,12 +137,17 @@ def run(kT=0.03, replicas=8, t_equil=20.0, t_max=400.0, sample_dt=1.0, seed=1, p
     th = [s.thermo() for s in systems]
     # the kernel's own bond count of the last step against the host count
     bond_count_diff = max(abs(int(h["n_bonds"]) - len(sr[-1])) for h, sr in zip(th, sets))
+    final = []
+    if keep_final:
+        for s, wl, h in zip(systems, wls, th):
+            x, _, _ = s.state()
+            final.append(dict(x=x, types=wl["types"], box=wl["box"], pairs=wl["pairs"], n_bonds=int(h["n_bonds"])))
     for s in systems:
         s.close()
     return dict(kT=kT, replicas=replicas, t_max=t_max, sample_dt=sample_dt, t=t.tolist(), c=c.tolist(), tau=tau,
                 fit_r2=r2, bonded_fraction_min=bonded_min, max_bonds_per_particle=multi_max,
                 n_bonds_mean=float(np.mean([h["n_bonds"] for h in th])), bond_count_diff=bond_count_diff,
-                mass_split=split_stats)
+                mass_split=split_stats, final=final)
 
 
 def main(argv=None):
@@ -156,6 +163,7 @@ def main(argv=None):
     for kT in a.kT:
         r = run(kT=kT, replicas=a.replicas, t_max=a.t_max, light_mass=a.light_mass)
         r.pop("t")
+        r.pop("final")
         r["c"] = [round(v, 4) for v in r["c"][::10]]
         for v in r["mass_split"].values():
             v["c"] = [round(x, 4) for x in v["c"][::10]]

@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_abi_version_needs_no_device(lib):
     from paper_1912_08569_gb300 import _abi
 
-    assert _abi.swp_abi_version() == 1
+    assert _abi.swp_abi_version() == 2
 
 
 def test_header_compiles_as_plain_c(tmp_path):
@@ -61,8 +61,28 @@ def test_thermo_struct_layout_matches_binding():
 
     from paper_1912_08569_gb300 import _abi
 
-    # 9 doubles + 4 int64 + 2 int32
-    assert ctypes.sizeof(_abi.swp_thermo) == 9 * 8 + 4 * 8 + 2 * 4
+    # 9 doubles + 4 int64 + 4 int32
+    assert ctypes.sizeof(_abi.swp_thermo) == 9 * 8 + 4 * 8 + 4 * 4
+    assert _abi.swp_thermo.resident_steps.offset == 9 * 8 + 4 * 8 + 2 * 4
+
+
+def test_thermo_struct_layout_matches_c(tmp_path):
+    """The C compiler's layout of swp_thermo equals the binding's."""
+    import ctypes
+
+    from paper_1912_08569_gb300 import _abi
+
+    c = tmp_path / "lay.c"
+    c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "swapmd.h"\n'
+                 'int main(void){ printf("%zu %zu %zu\\n", sizeof(swp_thermo), '
+                 'offsetof(swp_thermo, state), offsetof(swp_thermo, resident_steps)); return 0; }\n')
+    exe = tmp_path / "lay"
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()
+    assert [int(v) for v in out] == [ctypes.sizeof(_abi.swp_thermo), _abi.swp_thermo.state.offset,
+                                     _abi.swp_thermo.resident_steps.offset]
 
 
 def _py_files(d):

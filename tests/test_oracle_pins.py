@@ -479,6 +479,41 @@ def test_nvt_equipartition(orc):
     assert K == pytest.approx(1.5 * n * kT, rel=0.03)
 
 
+@pytest.mark.parametrize("gamma", [1.0, 4.0])
+def test_langevin_friction_rate(orc, gamma):
+    """The friction of the Langevin dynamics ("canonical Langevin", section
+    "Self-assembly pitfalls"; Ornstein-Uhlenbeck velocity process): for a
+    force-free particle dv = -gamma v dt + sqrt(2 gamma kT/m) dW, so the mean
+    velocity from v(0) decays as exp(-gamma t) and the stationary variance is
+    kT/m.  BAOAB (Leimkuhler & Matthews 2013) reproduces the decay exactly per
+    step (B and A leave v alone without forces; O multiplies the mean by
+    exp(-gamma dt)), so the sample mean over 3n components must equal
+    exp(-gamma k dt) within its sampling error at every k.  A friction factor
+    read as exp(-gamma dt / 2), or applied twice per step, fails by tens of
+    standard errors.  Equipartition alone cannot tell: any factor keeps the
+    Maxwell distribution stationary."""
+    n, kT, dt = 2000, 0.05, 0.001
+    box = np.array([50.0, 50.0, 50.0])
+    x = inputs.rsa_positions(n, box, 0.9, seed=4)
+    ty = np.zeros(n, dtype=np.int32)
+    tab = orc.pair_table(1, {})  # no interaction at all
+    tags = np.arange(n, dtype=np.uint32)
+    v0 = np.ones((n, 3))
+    for k in (50, 200, 500):
+        _, v, _, th = orc.run(x, v0, ty, np.ones(n), tags, 1, tab, box, dt, k, kT=kT, gamma=gamma, seed=11)
+        decay = math.exp(-gamma * k * dt)
+        sem = math.sqrt((1.0 - decay ** 2) * kT / (3 * n))
+        assert abs(v.mean() - decay) < 5.0 * sem, (k, v.mean(), decay, sem)
+        # the variance about the mean: (1 - exp(-2 gamma t)) kT / m
+        var = (1.0 - decay ** 2) * kT
+        assert v.var() == pytest.approx(var, rel=0.1)
+        assert np.all(th[:, 0] == 0.0) and np.all(th[:, 1] == 0.0)
+    # long after the start: the stationary velocity variance kT / m
+    _, v, _, _ = orc.run(x, v0, ty, np.ones(n), tags, 1, tab, box, dt, int(round(6.0 / (gamma * dt))),
+                         kT=kT, gamma=gamma, seed=12)
+    assert v.var() == pytest.approx(kT, rel=0.06)
+
+
 def test_nvt_uses_tag_keyed_noise(orc):
     # the Langevin noise depends on (seed, step, tag) only: permuting storage order
     # with the tags permuted alongside gives the same trajectory
