@@ -256,20 +256,43 @@ def algorithmic_bytes(n, md_steps, nn, nn_r, rebuilds):
 
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_sample(wl, seconds, steps_cap=200):
-    """Times the FP64 oracle on the same workload for a bounded number of steps."""
+def cpu_oracle_sample(wl, seconds, steps_cap=200, threaded=False):
+    """Times the FP64 oracle on the same workload for a bounded number of steps
+    (threaded: its OpenMP build on every host core)."""
     import oracle
 
     tab = oracle.pair_table(wl["n_types"], wl["pairs"])
     t0 = time.perf_counter()
-    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True)
+    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True, threaded=threaded)
     t_force = time.perf_counter() - t0
     nsteps = int(max(2, min(steps_cap, seconds / max(t_force, 1e-6))))
     t0 = time.perf_counter()
     oracle.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], wl["n_types"], tab, wl["box"],
-               wl["dt"], nsteps, kT=wl["kT"], gamma=wl["gamma"], seed=wl["seed"], fp32=True)
+               wl["dt"], nsteps, kT=wl["kT"], gamma=wl["gamma"], seed=wl["seed"], fp32=True, threaded=threaded)
     el = time.perf_counter() - t0
     return wl["n"] * nsteps / el, nsteps, el
+
+
+def cpu_baseline(wl, seconds, n_label):
+    """The oracle on the host: on every core (its OpenMP build; the headline
+    figure) and on one thread, each a bounded sample of the workload."""
+    import oracle
+
+    oracle.build()
+    v1, s1, e1 = cpu_oracle_sample(wl, seconds)
+    one = {"value": v1, "cores": 1,
+           "sample": f"N={n_label}, {s1} BAOAB steps of the FP64 C oracle (explicit triplet loop, cell list "
+                     f"every step), {e1:.1f} s, 1 thread"}
+    try:
+        oracle.build(openmp=True)
+        nt = oracle.threads(True)
+        vN, sN, eN = cpu_oracle_sample(wl, seconds, threaded=True)
+    except Exception as e:  # no OpenMP runtime on this host: the one-thread figure is the baseline
+        return dict(one, unit=UNIT, kind="oracle", host=host_info(), all_cores=f"unavailable: {e}")
+    return {"value": vN, "unit": UNIT, "cores": nt, "kind": "oracle", "host": host_info(),
+            "sample": f"N={n_label}, {sN} BAOAB steps of the FP64 C oracle built with OpenMP ({nt} threads: "
+                      f"pair search, pair and triplet sums split over the threads), {eN:.1f} s",
+            "one_thread": one}
 
 
 def accuracy_vs_oracle(oracle, s, wl):
@@ -301,8 +324,14 @@ def run_reference(a):
         return run_reference_dumbbell(a, oracle)
     wl = _workload(a.n, a.lam, 0)
     tab = oracle.pair_table(wl["n_types"], wl["pairs"])
+    # on every host core (the oracle's OpenMP build), else on one thread
+    try:
+        oracle.build(openmp=True)
+        threaded, cores = True, oracle.threads(True)
+    except Exception:
+        threaded, cores = False, 1
     t0 = time.perf_counter()
-    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True)
+    oracle.forces(wl["x"], wl["types"], wl["n_types"], tab, wl["box"], fp32=True, threaded=threaded)
     t_force = time.perf_counter() - t0
     # each step: a bounded sample of the workload (~8 s of CPU work)
     per = int(max(1, min(50, 8.0 / max(t_force, 1e-6))))
@@ -312,17 +341,17 @@ def run_reference(a):
         t0 = time.perf_counter()
         x, v, _, th = oracle.run(x, v, wl["types"], wl["mass"], wl["tags"], wl["n_types"], tab,
                                  wl["box"], wl["dt"], per, kT=wl["kT"], gamma=wl["gamma"],
-                                 seed=wl["seed"], step0=k * per, fp32=True)
+                                 seed=wl["seed"], step0=k * per, fp32=True, threaded=threaded)
         if k >= a.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = wl["n"] * per / (ms / 1e3)
-    sample = f"N={wl['n']}, {per} NVT steps per step of the FP64 C oracle (1 thread)"
+    sample = f"N={wl['n']}, {per} NVT steps per step of the FP64 C oracle ({cores} threads)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": _config(a, wl["n"], 1),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                             "host": host_info()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -447,11 +476,8 @@ def run_ours(a):
         import oracle
 
         oracle.build()
-        v, steps_done, el = cpu_oracle_sample(wl, a.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
-               "sample": f"N={n}, {steps_done} BAOAB steps of the FP64 C oracle (explicit triplet "
-                         f"loop, cell list every step), {el:.1f} s, 1 thread",
-               "accuracy": accuracy_vs_oracle(oracle, s, wl)}
+        cpu = cpu_baseline(wl, a.cpu_seconds, n)
+        cpu["accuracy"] = accuracy_vs_oracle(oracle, s, wl)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

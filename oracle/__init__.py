@@ -24,6 +24,10 @@ follows:
   "canonical Langevin dynamics" of section "Self-assembly pitfalls").
 * ``philox4x32_10`` / ``normals3``: the counter-based generator of Salmon et al.
   (SC'11) and its Box-Muller normals, used for the Langevin noise.
+* ``forces(..., threaded=True)`` / ``run(..., threaded=True)``: the same code
+  built with OpenMP over every host core (OMP_NUM_THREADS), for the
+  benchmark's all-cores CPU baseline; the additions are grouped per thread, so
+  results agree with the one-thread build to rounding, not bit for bit.
 
 Parity pins for every function are in ``tests/test_oracle_*.py``.  The
 mixed-coefficient triplet prefactor sqrt(l_ij e_ij l_ik e_ik) is a reading of
@@ -42,8 +46,12 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "swap_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_swap.so")
+# the same source built with -fopenmp: the all-cores CPU baseline of the
+# benchmark (same terms; the additions are grouped per thread)
+_LIB_OMP = os.path.join(_HERE, "liboracle_swap_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 KIND_NONE, KIND_WCA, KIND_SWAP = 0, 1, 2
 
@@ -62,23 +70,25 @@ PAIR_DTYPE = np.dtype(
 )
 
 
-def build(force: bool = False) -> str:
-    """Compile ``swap_oracle.c`` into ``liboracle_swap.so`` (gcc, FP64, no contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile ``swap_oracle.c`` into ``liboracle_swap.so`` (gcc, FP64, no
+    contraction); with openmp, into ``liboracle_swap_omp.so`` with -fopenmp."""
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+               "-fno-fast-math", *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib)
+    return lib
 
 
-def _load():
-    global _lib
+def _load(threaded: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+        if (_lib_omp if threaded else _lib) is None:
+            path = build(openmp=threaded)
+            lib = ctypes.CDLL(path)
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int)
             up = ctypes.POINTER(ctypes.c_uint32)
@@ -110,8 +120,13 @@ def _load():
             lib.orc_normals3.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                          ctypes.c_uint32, dp]
             lib.orc_normals3.restype = None
-            _lib = lib
-    return _lib
+            lib.orc_threads.argtypes = []
+            lib.orc_threads.restype = ctypes.c_int
+            if threaded:
+                _lib_omp = lib
+            else:
+                _lib = lib
+    return _lib_omp if threaded else _lib
 
 
 def _dp(a):
@@ -174,7 +189,7 @@ def _bond_arrays(bonds):
 
 
 def forces(x, types, ntypes, table, box, fp32: bool = False, bonds=None, kbond: float = 0.0,
-           r0: float = 1.0):
+           r0: float = 1.0, threaded: bool = False):
     """Energies, forces, virial and bond count of a configuration.
 
     Returns a dict with U2, U3, W (6: xx yy zz xy xz yz), n_bonds, F (n x 3),
@@ -192,7 +207,7 @@ def forces(x, types, ntypes, table, box, fp32: bool = False, bonds=None, kbond: 
     out = np.zeros(9)
     sc = np.zeros(3)
     fs = np.zeros(max(n, 1))
-    rc = _load().orc_forces(n, _dp(x), _ip(ty), int(ntypes), tab.ctypes.data, _dp(box),
+    rc = _load(threaded).orc_forces(n, _dp(x), _ip(ty), int(ntypes), tab.ctypes.data, _dp(box),
                             int(bool(fp32)), _dp(F), _dp(out), _dp(sc), _dp(fs))
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
@@ -231,7 +246,7 @@ def nlist(x, types, ntypes, table, box, skin: float, fp32: bool = False, maxn: i
 
 
 def run(x, v, types, mass, tags, ntypes, table, box, dt, nsteps, kT=0.0, gamma=0.0,
-        seed=0, step0=0, fp32=False, img=None, bonds=None, kbond=0.0, r0=1.0):
+        seed=0, step0=0, fp32=False, img=None, bonds=None, kbond=0.0, r0=1.0, threaded=False):
     """Advance (x, v) by nsteps (BAOAB if gamma > 0, else velocity Verlet).
 
     Returns (x, v, img, thermo) with thermo[s] = [U2, U3, K, W(6), n_bonds,
@@ -248,7 +263,7 @@ def run(x, v, types, mass, tags, ntypes, table, box, dt, nsteps, kT=0.0, gamma=0
     tab = np.ascontiguousarray(table, dtype=PAIR_DTYPE)
     th = np.zeros((max(nsteps, 1), 11))
     nb, b = _bond_arrays(bonds)
-    rc = _load().orc_run(n, _dp(x), _dp(v), _ip(im), _ip(ty), _dp(m),
+    rc = _load(threaded).orc_run(n, _dp(x), _dp(v), _ip(im), _ip(ty), _dp(m),
                          tg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), int(ntypes),
                          tab.ctypes.data, _dp(box), int(bool(fp32)), float(dt), int(nsteps),
                          float(kT), float(gamma), int(seed), int(step0), _dp(th), nb, _ip(b), float(kbond),
@@ -256,6 +271,11 @@ def run(x, v, types, mass, tags, ntypes, table, box, dt, nsteps, kT=0.0, gamma=0
     if rc != 0:
         raise MemoryError("oracle: allocation failed")
     return x, v, im, th[:nsteps]
+
+
+def threads(threaded: bool = True) -> int:
+    """Threads the (threaded) build's force sums use."""
+    return int(_load(threaded).orc_threads())
 
 
 def philox4x32_10(ctr, key):

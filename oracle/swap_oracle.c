@@ -62,6 +62,16 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Built as is (gcc, no -fopenmp), every loop runs on one thread in the order
+ * written.  Built a second time with -fopenmp (the benchmark's all-cores CPU
+ * baseline only), the pair search splits the particles, and the force sums
+ * split the pairs and the centres, over the threads in contiguous ranges;
+ * each thread sums into its own buffers, added up in thread order.  The
+ * terms are the same; only the order of the additions differs. */
 
 #define ORC_KIND_NONE 0
 #define ORC_KIND_WCA 1
@@ -306,6 +316,33 @@ static int pv_push(pairvec *v, int i, int j)
     return 0;
 }
 
+/* The pairs (i, j > i) of particle i from the 27 cells around its own,
+ * appended to out.  Returns 0 or -1 (memory). */
+static int cell_pairs(int i, const int *type, int ntypes, const orc_pair *tab, const decider *dc, double extra,
+                      int fp32, const int nc[3], const int *head, const int *next, const int *cid, pairvec *out)
+{
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int cx = (cid[3 * i] + dx + nc[0]) % nc[0];
+                int cy = (cid[3 * i + 1] + dy + nc[1]) % nc[1];
+                int cz = (cid[3 * i + 2] + dz + nc[2]) % nc[2];
+                long c = ((long)cz * nc[1] + cy) * nc[0] + cx;
+                for (int j = head[c]; j >= 0; j = next[j]) {
+                    if (j <= i)
+                        continue;
+                    const orc_pair *p = &tab[type[i] * ntypes + type[j]];
+                    double cut = pair_rcut(p);
+                    if (cut <= 0.0)
+                        continue;
+                    if (decision_d2(dc, i, j) < decision_cut2(cut + extra, fp32))
+                        if (pv_push(out, i, j))
+                            return -1;
+                }
+            }
+    return 0;
+}
+
 /* All unordered pairs i<j whose squared decision distance is below the
  * pair type's cut2 (cut = pair cut-off + extra).  Returns 0 or -1 (memory). */
 static int find_pairs(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
@@ -370,35 +407,36 @@ static int find_pairs(int n, const double *x, const int *type, int ntypes, const
         next[i] = head[c];
         head[c] = i;
     }
-    for (int i = 0; i < n; i++) {
-        for (int dz = -1; dz <= 1; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    int cx = (cid[3 * i] + dx + nc[0]) % nc[0];
-                    int cy = (cid[3 * i + 1] + dy + nc[1]) % nc[1];
-                    int cz = (cid[3 * i + 2] + dz + nc[2]) % nc[2];
-                    long c = ((long)cz * nc[1] + cy) * nc[0] + cx;
-                    for (int j = head[c]; j >= 0; j = next[j]) {
-                        if (j <= i)
-                            continue;
-                        const orc_pair *p = &tab[type[i] * ntypes + type[j]];
-                        double cut = pair_rcut(p);
-                        if (cut <= 0.0)
-                            continue;
-                        if (decision_d2(dc, i, j) < decision_cut2(cut + extra, fp32))
-                            if (pv_push(out, i, j)) {
-                                free(head);
-                                free(next);
-                                free(cid);
-                                return -1;
-                            }
-                    }
-                }
+    int err = 0;
+#ifdef _OPENMP
+    int nt = omp_get_max_threads();
+    pairvec *tv = (pairvec *)calloc((size_t)nt, sizeof(pairvec));
+    if (!tv)
+        err = 1;
+    else {
+#pragma omp parallel num_threads(nt) reduction(| : err)
+        {
+            pairvec *mine = &tv[omp_get_thread_num()];
+#pragma omp for schedule(static)
+            for (int i = 0; i < n; i++)
+                err |= cell_pairs(i, type, ntypes, tab, dc, extra, fp32, nc, head, next, cid, mine);
+        }
+        /* contiguous ranges in thread order: the serial order of the pairs */
+        for (int t = 0; t < nt && !err; t++)
+            for (long q = 0; q < tv[t].n && !err; q++)
+                err |= pv_push(out, tv[t].a[q].i, tv[t].a[q].j);
+        for (int t = 0; t < nt; t++)
+            free(tv[t].a);
+        free(tv);
     }
+#else
+    for (int i = 0; i < n && !err; i++)
+        err = cell_pairs(i, type, ntypes, tab, dc, extra, fp32, nc, head, next, cid, out);
+#endif
     free(head);
     free(next);
     free(cid);
-    return 0;
+    return err ? -1 : 0;
 }
 
 /* ---------------------------------------------------------------------- */
@@ -411,6 +449,164 @@ static int find_pairs(int n, const double *x, const int *type, int ntypes, const
  * acting on the particle of |term| + r |d term/dr| (first-order sensitivity
  * of the term to a relative perturbation of its distances).
  * force (may be NULL): 3n doubles. */
+/* Sums accumulated over the terms of one evaluation. */
+typedef struct {
+    double U2, U3, W[6], sU2, sU3, sW;
+    long nb;
+} orc_sums;
+
+/* The two-body terms of the pair (i, j): energy, forces, virial, error
+ * scales and bond count, added to s, force (may be NULL) and fscale (may be
+ * NULL). */
+static void pair_terms(int i, int j, const double *x, const int *type, int ntypes, const orc_pair *tab,
+                       const double *box, const decider *dc, int fp32, orc_sums *s, double *force,
+                       double *fscale)
+{
+    const orc_pair *p = &tab[type[i] * ntypes + type[j]];
+    double d[3];
+    for (int c = 0; c < 3; c++)
+        d[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]); /* r_ij = x_i - x_j */
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double u, du, d2u;
+    pair_u2(p, r, &u, &du, &d2u);
+    s->U2 += u;
+    s->sU2 += fabs(u) + r * fabs(du);
+    /* F_i = -du/dr * d/r ; F_j = -F_i */
+    double g = -du / r;
+    if (force)
+        for (int c = 0; c < 3; c++) {
+            force[3 * i + c] += g * d[c];
+            force[3 * j + c] -= g * d[c];
+        }
+    s->W[0] += g * d[0] * d[0];
+    s->W[1] += g * d[1] * d[1];
+    s->W[2] += g * d[2] * d[2];
+    s->W[3] += g * d[0] * d[1];
+    s->W[4] += g * d[0] * d[2];
+    s->W[5] += g * d[1] * d[2];
+    s->sW += r * fabs(du) + r * r * fabs(d2u);
+    if (fscale) {
+        double sc = fabs(du) + r * fabs(d2u);
+        fscale[i] += sc;
+        fscale[j] += sc;
+    }
+    if (p->kind == ORC_KIND_SWAP && decision_d2(dc, i, j) < decision_cut2(p->rbond, fp32))
+        s->nb++;
+}
+
+/* Eq. 3bp for centre i: every unordered pair {j, k} of its reactive partners
+ * rpart[rstart[i] .. rstart[i + 1]), one explicit term each, added to s,
+ * force (may be NULL) and fscale (may be NULL). */
+static void centre_terms(int i, const long *rstart, const int *rpart, const double *x, const int *type,
+                         int ntypes, const orc_pair *tab, const double *box, orc_sums *s, double *force,
+                         double *fscale)
+{
+    for (long qa = rstart[i]; qa < rstart[i + 1]; qa++) {
+        for (long qb = qa + 1; qb < rstart[i + 1]; qb++) {
+            int j = rpart[qa], k = rpart[qb];
+            const orc_pair *pj = &tab[type[i] * ntypes + type[j]];
+            const orc_pair *pk = &tab[type[i] * ntypes + type[k]];
+            double dj[3], dk[3];
+            for (int c = 0; c < 3; c++) {
+                dj[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]);
+                dk[c] = wrap_d(x[3 * i + c] - x[3 * k + c], box[c]);
+            }
+            double rj = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+            double rk = sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
+            double hj, dhj, d2hj, hk, dhk, d2hk;
+            pair_vhat(pj, rj, &hj, &dhj, &d2hj);
+            pair_vhat(pk, rk, &hk, &dhk, &d2hk);
+            double aj = sqrt(pj->lambda3 * pj->eps);
+            double ak = sqrt(pk->lambda3 * pk->eps);
+            double pref = aj * ak;
+            double v3 = pref * hj * hk;
+            s->U3 += v3;
+            s->sU3 += pref * (fabs(hj * hk) + rj * fabs(dhj * hk) + rk * fabs(hj * dhk));
+            /* dU/drj = pref dhj hk ; dU/drk = pref hj dhk */
+            double dUj = pref * dhj * hk;
+            double dUk = pref * hj * dhk;
+            double gj = -dUj / rj; /* force on i from the (i,j) leg: gj * dj */
+            double gk = -dUk / rk;
+            if (force)
+                for (int c = 0; c < 3; c++) {
+                    force[3 * i + c] += gj * dj[c] + gk * dk[c];
+                    force[3 * j + c] -= gj * dj[c];
+                    force[3 * k + c] -= gk * dk[c];
+                }
+            s->W[0] += gj * dj[0] * dj[0] + gk * dk[0] * dk[0];
+            s->W[1] += gj * dj[1] * dj[1] + gk * dk[1] * dk[1];
+            s->W[2] += gj * dj[2] * dj[2] + gk * dk[2] * dk[2];
+            s->W[3] += gj * dj[0] * dj[1] + gk * dk[0] * dk[1];
+            s->W[4] += gj * dj[0] * dj[2] + gk * dk[0] * dk[2];
+            s->W[5] += gj * dj[1] * dj[2] + gk * dk[1] * dk[2];
+            double sj = pref * (fabs(dhj * hk) + rj * fabs(d2hj * hk) + rk * fabs(dhj * dhk));
+            double sk = pref * (fabs(hj * dhk) + rk * fabs(hj * d2hk) + rj * fabs(dhj * dhk));
+            s->sW += rj * sj + rk * sk;
+            if (fscale) {
+                fscale[i] += sj + sk;
+                fscale[j] += sj;
+                fscale[k] += sk;
+            }
+        }
+    }
+}
+
+#ifdef _OPENMP
+/* The pair terms (what = 0, count = pairs) or the centre terms (what = 1,
+ * count = n) on every thread, each over a contiguous range into its own sums
+ * and buffers, then added to s, force and fscale in thread order. */
+static int threaded_terms(int what, long count, const pairvec *pv, const long *rstart, const int *rpart, int n,
+                          const double *x, const int *type, int ntypes, const orc_pair *tab, const double *box,
+                          const decider *dc, int fp32, orc_sums *s, double *force, double *fscale)
+{
+    int nt = omp_get_max_threads();
+    orc_sums *ts = (orc_sums *)calloc((size_t)nt, sizeof(orc_sums));
+    double *fb = force ? (double *)calloc((size_t)nt * 3 * n, sizeof(double)) : NULL;
+    double *sb = fscale ? (double *)calloc((size_t)nt * n, sizeof(double)) : NULL;
+    if (!ts || (force && !fb) || (fscale && !sb)) {
+        free(ts);
+        free(fb);
+        free(sb);
+        return -1;
+    }
+#pragma omp parallel num_threads(nt)
+    {
+        int t = omp_get_thread_num();
+        double *ft = fb ? fb + (size_t)t * 3 * n : NULL;
+        double *st = sb ? sb + (size_t)t * n : NULL;
+#pragma omp for schedule(static)
+        for (long q = 0; q < count; q++) {
+            if (what == 0)
+                pair_terms(pv->a[q].i, pv->a[q].j, x, type, ntypes, tab, box, dc, fp32, &ts[t], ft, st);
+            else
+                centre_terms((int)q, rstart, rpart, x, type, ntypes, tab, box, &ts[t], ft, st);
+        }
+    }
+    for (int t = 0; t < nt; t++) {
+        s->U2 += ts[t].U2;
+        s->U3 += ts[t].U3;
+        for (int c = 0; c < 6; c++)
+            s->W[c] += ts[t].W[c];
+        s->sU2 += ts[t].sU2;
+        s->sU3 += ts[t].sU3;
+        s->sW += ts[t].sW;
+        s->nb += ts[t].nb;
+    }
+    if (force)
+        for (long k = 0; k < 3L * n; k++)
+            for (int t = 0; t < nt; t++)
+                force[k] += fb[(size_t)t * 3 * n + k];
+    if (fscale)
+        for (long k = 0; k < n; k++)
+            for (int t = 0; t < nt; t++)
+                fscale[k] += sb[(size_t)t * n + k];
+    free(ts);
+    free(fb);
+    free(sb);
+    return 0;
+}
+#endif
+
 int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
                const double *box, int fp32, double *force, double *out, double *scales,
                double *fscale)
@@ -423,9 +619,8 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
         decider_free(&dc);
         return -1;
     }
-    double U2 = 0, U3 = 0, W[6] = {0, 0, 0, 0, 0, 0};
-    double sU2 = 0, sU3 = 0, sW = 0;
-    long nb = 0;
+    orc_sums sm;
+    memset(&sm, 0, sizeof(sm));
     if (force)
         memset(force, 0, (size_t)n * 3 * sizeof(double));
     if (fscale)
@@ -439,41 +634,19 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
         return -1;
     }
 
+    /* Two-body terms, pair by pair. */
+    int err = 0;
+#ifdef _OPENMP
+    err = threaded_terms(0, pv.n, &pv, NULL, NULL, n, x, type, ntypes, tab, box, &dc, fp32, &sm, force, fscale);
+#else
+    for (long q = 0; q < pv.n; q++)
+        pair_terms(pv.a[q].i, pv.a[q].j, x, type, ntypes, tab, box, &dc, fp32, &sm, force, fscale);
+#endif
     for (long q = 0; q < pv.n; q++) {
         int i = pv.a[q].i, j = pv.a[q].j;
-        const orc_pair *p = &tab[type[i] * ntypes + type[j]];
-        double d[3];
-        for (int c = 0; c < 3; c++)
-            d[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]); /* r_ij = x_i - x_j */
-        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        double u, du, d2u;
-        pair_u2(p, r, &u, &du, &d2u);
-        U2 += u;
-        sU2 += fabs(u) + r * fabs(du);
-        /* F_i = -du/dr * d/r ; F_j = -F_i */
-        double g = -du / r;
-        if (force)
-            for (int c = 0; c < 3; c++) {
-                force[3 * i + c] += g * d[c];
-                force[3 * j + c] -= g * d[c];
-            }
-        W[0] += g * d[0] * d[0];
-        W[1] += g * d[1] * d[1];
-        W[2] += g * d[2] * d[2];
-        W[3] += g * d[0] * d[1];
-        W[4] += g * d[0] * d[2];
-        W[5] += g * d[1] * d[2];
-        sW += r * fabs(du) + r * r * fabs(d2u);
-        if (fscale) {
-            double s = fabs(du) + r * fabs(d2u);
-            fscale[i] += s;
-            fscale[j] += s;
-        }
-        if (p->kind == ORC_KIND_SWAP) {
+        if (tab[type[i] * ntypes + type[j]].kind == ORC_KIND_SWAP) {
             rcount[i]++;
             rcount[j]++;
-            if (decision_d2(&dc, i, j) < decision_cut2(p->rbond, fp32))
-                nb++;
         }
     }
 
@@ -483,7 +656,7 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
     for (int i = 0; i < n; i++)
         total += rcount[i];
     int *rpart = (int *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int));
-    if (!rstart || !rpart) {
+    if (err || !rstart || !rpart) {
         free(rstart);
         free(rpart);
         free(rcount);
@@ -505,73 +678,29 @@ int orc_forces(int n, const double *x, const int *type, int ntypes, const orc_pa
     }
 
     /* Eq. 3bp: explicit loop over every centre i and unordered {j,k}. */
-    for (int i = 0; i < n; i++) {
-        for (long qa = rstart[i]; qa < rstart[i + 1]; qa++) {
-            for (long qb = qa + 1; qb < rstart[i + 1]; qb++) {
-                int j = rpart[qa], k = rpart[qb];
-                const orc_pair *pj = &tab[type[i] * ntypes + type[j]];
-                const orc_pair *pk = &tab[type[i] * ntypes + type[k]];
-                double dj[3], dk[3];
-                for (int c = 0; c < 3; c++) {
-                    dj[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]);
-                    dk[c] = wrap_d(x[3 * i + c] - x[3 * k + c], box[c]);
-                }
-                double rj = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
-                double rk = sqrt(dk[0] * dk[0] + dk[1] * dk[1] + dk[2] * dk[2]);
-                double hj, dhj, d2hj, hk, dhk, d2hk;
-                pair_vhat(pj, rj, &hj, &dhj, &d2hj);
-                pair_vhat(pk, rk, &hk, &dhk, &d2hk);
-                double aj = sqrt(pj->lambda3 * pj->eps);
-                double ak = sqrt(pk->lambda3 * pk->eps);
-                double pref = aj * ak;
-                double v3 = pref * hj * hk;
-                U3 += v3;
-                sU3 += pref * (fabs(hj * hk) + rj * fabs(dhj * hk) + rk * fabs(hj * dhk));
-                /* dU/drj = pref dhj hk ; dU/drk = pref hj dhk */
-                double dUj = pref * dhj * hk;
-                double dUk = pref * hj * dhk;
-                double gj = -dUj / rj; /* force on i from the (i,j) leg: gj * dj */
-                double gk = -dUk / rk;
-                if (force)
-                    for (int c = 0; c < 3; c++) {
-                        force[3 * i + c] += gj * dj[c] + gk * dk[c];
-                        force[3 * j + c] -= gj * dj[c];
-                        force[3 * k + c] -= gk * dk[c];
-                    }
-                W[0] += gj * dj[0] * dj[0] + gk * dk[0] * dk[0];
-                W[1] += gj * dj[1] * dj[1] + gk * dk[1] * dk[1];
-                W[2] += gj * dj[2] * dj[2] + gk * dk[2] * dk[2];
-                W[3] += gj * dj[0] * dj[1] + gk * dk[0] * dk[1];
-                W[4] += gj * dj[0] * dj[2] + gk * dk[0] * dk[2];
-                W[5] += gj * dj[1] * dj[2] + gk * dk[1] * dk[2];
-                double sj = pref * (fabs(dhj * hk) + rj * fabs(d2hj * hk) + rk * fabs(dhj * dhk));
-                double sk = pref * (fabs(hj * dhk) + rk * fabs(hj * d2hk) + rj * fabs(dhj * dhk));
-                sW += rj * sj + rk * sk;
-                if (fscale) {
-                    fscale[i] += sj + sk;
-                    fscale[j] += sj;
-                    fscale[k] += sk;
-                }
-            }
-        }
-    }
+#ifdef _OPENMP
+    err = threaded_terms(1, n, NULL, rstart, rpart, n, x, type, ntypes, tab, box, &dc, fp32, &sm, force, fscale);
+#else
+    for (int i = 0; i < n; i++)
+        centre_terms(i, rstart, rpart, x, type, ntypes, tab, box, &sm, force, fscale);
+#endif
 
-    out[0] = U2;
-    out[1] = U3;
+    out[0] = sm.U2;
+    out[1] = sm.U3;
     for (int c = 0; c < 6; c++)
-        out[2 + c] = W[c];
-    out[8] = (double)nb;
+        out[2 + c] = sm.W[c];
+    out[8] = (double)sm.nb;
     if (scales) {
-        scales[0] = sU2;
-        scales[1] = sU3;
-        scales[2] = sW;
+        scales[0] = sm.sU2;
+        scales[1] = sm.sU3;
+        scales[2] = sm.sW;
     }
     free(rstart);
     free(rpart);
     free(rcount);
     free(pv.a);
     decider_free(&dc);
-    return 0;
+    return err ? -1 : 0;
 }
 
 /* Harmonic bonds of a fixed topology (the chains of the vitrimer network, a
@@ -668,6 +797,16 @@ int orc_nlist(int n, const double *x, const int *type, int ntypes, const orc_pai
     }
     free(pv.a);
     return mx;
+}
+
+/* Threads the force sums use (1 unless built with OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ---------------------------------------------------------------------- */

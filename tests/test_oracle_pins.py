@@ -479,6 +479,30 @@ def test_nvt_equipartition(orc):
     assert K == pytest.approx(1.5 * n * kT, rel=0.03)
 
 
+def test_threaded_oracle_matches_one_thread(orc):
+    """The OpenMP build (the all-cores CPU baseline) computes the same terms:
+    equal to the one-thread oracle up to the grouping of the additions."""
+    try:
+        orc.build(openmp=True)
+    except Exception as e:  # pragma: no cover - no OpenMP runtime here
+        pytest.skip(f"no OpenMP build: {e}")
+    wl = inputs.workload("mix2k", lambda3=5.0, n=3000, density=0.5, seed=5)
+    tab = orc.pair_table(2, wl["pairs"])
+    for fp32 in (False, True):
+        a = orc.forces(wl["x"], wl["types"], 2, tab, wl["box"], fp32=fp32)
+        b = orc.forces(wl["x"], wl["types"], 2, tab, wl["box"], fp32=fp32, threaded=True)
+        assert np.all(np.linalg.norm(a["F"] - b["F"], axis=1) <= 1e-13 * a["fscale"])
+        for q in ("U2", "U3"):
+            assert abs(a[q] - b[q]) <= 1e-13 * a["scale_" + q]
+        assert np.all(np.abs(a["W"] - b["W"]) <= 1e-13 * a["scale_W"])
+        assert a["n_bonds"] == b["n_bonds"]
+    xa, va, _, tha = orc.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], 2, tab, wl["box"], 0.001, 10,
+                             kT=0.1, gamma=1.0, seed=3)
+    xb, vb, _, thb = orc.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], 2, tab, wl["box"], 0.001, 10,
+                             kT=0.1, gamma=1.0, seed=3, threaded=True)
+    assert np.abs(xa - xb).max() <= 1e-11 and np.abs(va - vb).max() <= 1e-9
+
+
 @pytest.mark.parametrize("gamma", [1.0, 4.0])
 def test_langevin_friction_rate(orc, gamma):
     """The friction of the Langevin dynamics ("canonical Langevin", section
