@@ -305,8 +305,18 @@ def accuracy_vs_oracle(oracle, s, wl):
     th = s.thermo()
     ref = oracle.forces(x, wl["types"], wl["n_types"], oracle.pair_table(wl["n_types"], wl["pairs"]), wl["box"],
                         fp32=True)
-    ferr = np.linalg.norm(F - ref["F"], axis=1) / np.maximum(ref["fscale"], 1e-300)
+    derr = np.linalg.norm(F - ref["F"], axis=1)
+    ferr = derr / np.maximum(ref["fscale"], 1e-300)
+    # the survey's per-particle scale (forces times their three-body factor),
+    # over the particles where it is not zero
+    c9 = oracle.fscale_c9(x, wl["types"], wl["n_types"], oracle.pair_table(wl["n_types"], wl["pairs"]), wl["box"],
+                          fp32=True)
+    on = c9 > 0
+    c9err = derr[on] / c9[on]
     return {"F_max_err_over_scale": float(ferr.max()),
+            "F_rel_l2": float(np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"])),
+            "F_max_err_over_c9_scale": float(c9err.max()) if c9err.size else 0.0,
+            "F_p999_err_over_c9_scale": float(np.percentile(c9err, 99.9)) if c9err.size else 0.0,
             "U2_err_over_scale": abs(th["U2"] - ref["U2"]) / ref["scale_U2"],
             "U3_err_over_scale": abs(th["U3"] - ref["U3"]) / max(ref["scale_U3"], 1e-300),
             "W_max_err_over_scale": float(np.max(np.abs(th["W"] - ref["W"]))) / ref["scale_W"],

@@ -120,6 +120,8 @@ def _load(threaded: bool = False):
             lib.orc_normals3.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                          ctypes.c_uint32, dp]
             lib.orc_normals3.restype = None
+            lib.orc_fscale_c9.argtypes = [ctypes.c_int, dp, ip, ctypes.c_int, vp, dp, ctypes.c_int, dp]
+            lib.orc_fscale_c9.restype = ctypes.c_int
             lib.orc_threads.argtypes = []
             lib.orc_threads.restype = ctypes.c_int
             if threaded:
@@ -224,6 +226,22 @@ def forces(x, types, ntypes, table, box, fp32: bool = False, bonds=None, kbond: 
     return dict(U2=out[0], U3=out[1], W=out[2:8].copy(), n_bonds=int(round(out[8])),
                 F=F[:n].copy(), scale_U2=sc[0], scale_U3=sc[1], scale_W=sc[2],
                 fscale=fs[:n].copy(), U_bond=ub, scale_Ub=sub)
+
+
+def fscale_c9(x, types, ntypes, table, box, fp32: bool = False):
+    """Per-particle sum over interacting pairs of |du2/dr| (1 + lambda (S_i + S_j))
+    (reactive) or |du2/dr| (others): the size of the forces, without the
+    distance-sensitivity term of forces()["fscale"]."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    ty = np.ascontiguousarray(types, dtype=np.int32)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    tab = np.ascontiguousarray(table, dtype=PAIR_DTYPE)
+    out = np.zeros(max(n, 1))
+    if _load().orc_fscale_c9(n, _dp(x), _ip(ty), int(ntypes), tab.ctypes.data, _dp(box), int(bool(fp32)),
+                             _dp(out)) != 0:
+        raise MemoryError("oracle: allocation failed")
+    return out[:n]
 
 
 def nlist(x, types, ntypes, table, box, skin: float, fp32: bool = False, maxn: int = 256):

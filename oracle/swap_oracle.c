@@ -799,6 +799,62 @@ int orc_nlist(int n, const double *x, const int *type, int ntypes, const orc_pai
     return mx;
 }
 
+/* A second per-particle force scale: over i's interacting pairs, |du2/dr|
+ * (1 + lambda (S_i + S_j)) for a reactive pair (S_i: the sum of vh over i's
+ * reactive partners inside r_cut) and |du2/dr| for the others -- the size of
+ * the two-body forces, each amplified by the three-body factor it can
+ * receive (Eq. 3bp through S_i).  Unlike the scale orc_forces returns it
+ * has no term for the sensitivity to the distances, so it vanishes for a
+ * particle whose pairs all sit at r_min.  Returns 0 or -1 (memory). */
+int orc_fscale_c9(int n, const double *x, const int *type, int ntypes, const orc_pair *tab,
+                  const double *box, int fp32, double *scale)
+{
+    pairvec pv = {0, 0, 0};
+    decider dc;
+    if (decider_init(&dc, n, x, box, fp32))
+        return -1;
+    if (find_pairs(n, x, type, ntypes, tab, box, &dc, 0.0, &pv)) {
+        decider_free(&dc);
+        return -1;
+    }
+    double *S = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!S) {
+        free(pv.a);
+        decider_free(&dc);
+        return -1;
+    }
+    memset(scale, 0, (size_t)n * sizeof(double));
+    for (int pass = 0; pass < 2; pass++)
+        for (long q = 0; q < pv.n; q++) {
+            int i = pv.a[q].i, j = pv.a[q].j;
+            const orc_pair *p = &tab[type[i] * ntypes + type[j]];
+            double d[3];
+            for (int c = 0; c < 3; c++)
+                d[c] = wrap_d(x[3 * i + c] - x[3 * j + c], box[c]);
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (pass == 0) {
+                if (p->kind == ORC_KIND_SWAP) {
+                    double vh, dvh, d2vh;
+                    pair_vhat(p, r, &vh, &dvh, &d2vh);
+                    S[i] += vh;
+                    S[j] += vh;
+                }
+            } else {
+                double u, du, d2u;
+                pair_u2(p, r, &u, &du, &d2u);
+                double w = fabs(du);
+                if (p->kind == ORC_KIND_SWAP)
+                    w *= 1.0 + p->lambda3 * (S[i] + S[j]);
+                scale[i] += w;
+                scale[j] += w;
+            }
+        }
+    free(S);
+    free(pv.a);
+    decider_free(&dc);
+    return 0;
+}
+
 /* Threads the force sums use (1 unless built with OpenMP). */
 int orc_threads(void)
 {

@@ -11,7 +11,7 @@ namespace swp {
 constexpr int kMaxTypes = 8;       // type-pair table is kMaxTypes^2 entries at most
 constexpr int kNQ = 12;            // per-block thermo partials: see Q_* below
 constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
-constexpr int kBlock = 1024;       // threads per block of the step kernel (one block per SM)
+constexpr int kBlock = 768;        // threads per block of the step kernel (one block per SM, 80 registers)
 constexpr int kMaxGrid = 320;      // largest grid of the step kernel (blocks)
 constexpr int kBlockBatch = 1024;  // threads per block of the batched kernel
 constexpr int kMaxBonds = 4;       // harmonic bonds per particle (chains: 2)

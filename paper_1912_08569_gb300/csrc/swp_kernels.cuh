@@ -48,7 +48,9 @@ constexpr bool kBatched = SWP_BATCHED != 0;
 // shared memory rather than the constant bank, so at 64 registers per thread
 // it spills; 512-thread blocks at 128 registers run without spilling but were
 // measured slower on 256 systems (2.6e9 against 2.8e9 particle-steps/s), so it
-// keeps 1024.
+// keeps 1024.  The single-system kernel runs 768 threads (80 registers): its
+// resident step keeps a thread's row, the integrator's state and the pair
+// arithmetic in registers at once.
 constexpr int kThreads = kBatched ? kBlockBatch : kBlock;
 
 // ---------------------------------------------------------------------------
@@ -283,23 +285,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 
 // Three standard normals for (seed, step, tag): counter (tag, step lo,
 // step hi, 1), key (seed lo, seed hi), Box-Muller on (u0,u1) and (u2,u3).
+// FP32: the hardware logarithm and sine/cosine (absolute error about 1e-6 on
+// these arguments, far below what the noise amplitude sqrt((1 - c^2) kT/m)
+// lets through to a trajectory), at a fifth of the accurate functions' cost.
 __device__ __forceinline__ void normals3(unsigned long long seed, long long step, unsigned tag,
                                          float z[3])
 {
     uint4 w = philox4x32_10(make_uint4(tag, (unsigned)step, (unsigned)((unsigned long long)step >> 32), 1u),
                             make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
     const float s32 = 2.3283064365386963e-10f;
+    const float two_pi = 6.28318530717958648f;
     float u0 = (__uint2float_rn(w.x) + 0.5f) * s32;
     float u1 = (__uint2float_rn(w.y) + 0.5f) * s32;
     float u2 = (__uint2float_rn(w.z) + 0.5f) * s32;
     float u3 = (__uint2float_rn(w.w) + 0.5f) * s32;
-    float ra = sqrtf(-2.0f * logf(u0));
-    float rb = sqrtf(-2.0f * logf(u2));
+    float ra = sqrtf(-2.0f * __logf(u0));
+    float rb = sqrtf(-2.0f * __logf(u2));
     float sn, cs;
-    sincospif(2.0f * u1, &sn, &cs);
+    __sincosf(two_pi * u1, &sn, &cs);
     z[0] = ra * cs;
     z[1] = ra * sn;
-    z[2] = rb * cospif(2.0f * u3);
+    z[2] = rb * __cosf(two_pi * u3);
 }
 
 __device__ __forceinline__ void normals3(unsigned long long seed, long long step, unsigned tag,
@@ -441,48 +447,82 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
     lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
-// Sums the per-thread accumulators over the block, through a shared staging
-// area of kNQA x blockDim values: thread t's values go to stage[q * B + t],
-// then warp q sums quantity q in a fixed order (32 values per lane, then the
-// lanes) while the other warps go on.  FP32 runs: compensated (double-float)
-// sums, so the block total is as accurate as an FP64 sum of the FP32 thread
-// values; FP64 runs: plain FP64 sums.  The total is added to the block's FP64
-// running sum blk[q]; with out given, blk[q] is then written to out[q] (the
-// block's partial of the pass) and cleared.  Each thread holds the terms of one
-// sub-chunk at most (multi-chunk passes flush after every sub-chunk), so the
-// error does not grow with the system size; block partials are summed over
-// blocks in FP64 (run_reduce_thermo / reduce_finish).
-__device__ __forceinline__ double warp_total(int lane, const float* row, int B)
+// Block sums of the per-thread thermo accumulators (energies, virial, bond
+// count), added to the block's FP64 running sums blk[q]; with out given,
+// blk[q] is then written to out[q] (the block's partial of the pass) and
+// cleared.  Each thread holds the terms of one sub-chunk at most (multi-chunk
+// passes flush after every sub-chunk), so the error does not grow with the
+// system size; block partials are summed over blocks in FP64
+// (run_reduce_thermo / reduce_finish).
+//
+// FP32 runs: each warp folds its lanes' values by a shuffle tree (at most five
+// roundings of the warp's sum of magnitudes) into s_wpart[q][warp]; warp q
+// then sums quantity q over the block's warps compensated (double-float).
+// FP64 runs: the values are staged in shared memory (stage: kNQA x blockDim)
+// and warp q sums them in FP64.
+static __shared__ float s_wpart[kNQA][32];
+
+__device__ __forceinline__ float warp_sum(float x)
 {
-    float hi = 0.0f, lo = 0.0f;
-    for (int k = lane; k < B; k += 32) df_add(hi, lo, row[k], 0.0f);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        df_add(hi, lo, h2, l2);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// s_wpart[q][warp] = the warp's sum of x (every lane of the warp calls it).
+__device__ __forceinline__ void warp_part(float x, int q)
+{
+    x = warp_sum(x);
+    if ((threadIdx.x & 31) == 0) s_wpart[q][threadIdx.x >> 5] = x;
+}
+
+// Sums s_wpart over the block's warps into blk / out (see above).
+__device__ __forceinline__ void block_sums_from_warps(double* blk, double* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (warp < kNQA) {
+        float hi = lane < nw ? s_wpart[warp][lane] : 0.0f, lo = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            df_add(hi, lo, h2, l2);
+        }
+        if (lane == 0) {
+            const double tot = blk[warp] + ((double)hi + (double)lo);
+            if (out) {
+                out[warp] = tot;
+                blk[warp] = 0.0;
+            } else {
+                blk[warp] = tot;
+            }
+        }
+    } else if (out && warp == kNQA && lane < kNQ - kNQA) {
+        out[kNQA + lane] = 0.0;
     }
-    return (double)hi + (double)lo;
+    __syncthreads();
 }
 
-__device__ __forceinline__ double warp_total(int lane, const double* row, int B)
+__device__ __forceinline__ void block_sums(const float* acc, float*, double* blk, double* out)
 {
-    double s = 0.0;
-    for (int k = lane; k < B; k += 32) s += row[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
+    for (int q = 0; q < kNQA; q++) warp_part(acc[q], q);
+    block_sums_from_warps(blk, out);
 }
 
-template <typename Real>
-__device__ __forceinline__ void block_sums(const Real* acc, Real* stage, double* blk, double* out)
+__device__ __forceinline__ void block_sums(const double* acc, double* stage, double* blk, double* out)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, B = blockDim.x;
 #pragma unroll
     for (int q = 0; q < kNQA; q++) stage[q * B + t] = acc[q];
     __syncthreads();
     if (warp < kNQA) {
-        const double tot = blk[warp] + warp_total(lane, stage + warp * B, B);
+        double x = 0.0;
+        for (int k = lane; k < B; k += 32) x += stage[warp * B + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) {
+            const double tot = blk[warp] + x;
             if (out) {
                 out[warp] = tot;
                 blk[warp] = 0.0;
@@ -1349,8 +1389,8 @@ __device__ __forceinline__ float open_from_stored(const Dev<Real>& d, const RunA
 //
 // Block-wide state lives in shared memory at namespace scope (addressed
 // directly, not through pointers), so that nothing but the phase at hand
-// occupies registers: the kernel runs at the 64-register limit of a
-// 1024-thread block.
+// occupies registers: the kernel runs at the 80-register limit of a
+// 768-thread block.
 
 struct LoopState {
     unsigned long long bar_target;  // barrier generation target (thread 0)
@@ -1572,7 +1612,8 @@ __device__ __forceinline__ void reduce_finish(const Dev<Real>& d)
 // this block has passed.
 template <typename Real>
 __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, const Acc<Real>& acc,
-                                          int par, unsigned* pub_dst, int where, Real* stage)
+                                          int par, unsigned* pub_dst, int where, Real* stage,
+                                          bool folded = false)
 {
     BarState bs;
     bs.target = s_ls.bar_target;
@@ -1582,7 +1623,12 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
         cp_async_wait_all();  // each thread's own copy into s_rbuf
         reduce_finish(d);
     }
-    block_sums(acc.q, stage, s_blk, d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ);
+    // folded: the pass already summed its terms over each warp (s_wpart)
+    double* out = d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ;
+    if (folded)
+        block_sums_from_warps(s_blk, out);
+    else
+        block_sums(acc.q, stage, s_blk, out);
     // groups of at least kNQA blocks: one quantity per block, asynchronously;
     // smaller groups reduce every quantity here
     const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
@@ -1596,6 +1642,10 @@ __device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, 
     }
     return bar_wait(d.ctl, bs, a.timeout_ns, where, &s_ls.ok);
 }
+
+// The partials buffer of the next pass: the one after the last pass's, in
+// rotation (any two passes in a row, and the one between, differ).
+__device__ __forceinline__ int next_parity() { return s_ls.parity == kParities - 1 ? 0 : s_ls.parity + 1; }
 
 __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
 {
@@ -1626,39 +1676,47 @@ __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
 // partials are grouped differently.
 
 struct RStage {
-    static constexpr int kL = 3 * kBlock;   // local particles: own (<= kBlock), then halo
-    static constexpr int kH = kL - kBlock;  // halo particles; also the bound on halo rows of S
-    static constexpr int kE = 16384;        // local entries (16-bit partner indices)
-    static constexpr int kHash = 4096;      // open-addressing table of halo slots (while building)
-    static constexpr size_t O_LPOS = 0;                            // [kL] int4 snapshots
-    static constexpr size_t O_LS = O_LPOS + (size_t)kL * 16;       // [kL] float S
-    static constexpr size_t O_HSLOT = O_LS + (size_t)kL * 4;       // [kH] int global slots of the halo
-    static constexpr size_t O_ENT = O_HSLOT + (size_t)kH * 4;      // [kE] u16 local partner indices
-    static constexpr size_t O_OROW = O_ENT + (size_t)kE * 2;       // [kBlock] own rows: first | nr << 16 | nw << 24
-    static constexpr size_t O_SROW = O_OROW + (size_t)kBlock * 4;  // [kH] int2 halo S rows: (first | n << 16, centre)
-    static constexpr size_t O_VEL = O_SROW + (size_t)kH * 8;       // [kBlock] float4 staged velocities
-    static constexpr size_t O_XQ = O_VEL + (size_t)kBlock * 16;    // [3 kBlock] staged fixed-point positions
-    static constexpr size_t O_IMG = O_XQ + (size_t)kBlock * 24;    // [3 kBlock] staged image counts
+    static constexpr int kL = 3072;    // local particles: own (at most blockDim), then halo
+    static constexpr int kES = 16384;  // entries of the rows of S, warp-major (padded to each warp's longest)
+    static constexpr int kEF = 12288;  // entries of the own rows (force pass), laid out the same way
+    static constexpr int kHash = 4096; // open-addressing table of halo slots (while building)
+    static constexpr int kRounds = (kL + kBlock - 1) / kBlock;  // rows of S per thread, at most
+    static constexpr size_t O_LPOS = 0;                             // [kL] int4 snapshots (own, then halo)
+    static constexpr size_t O_LS = O_LPOS + (size_t)kL * 16;        // [kL] float S
+    static constexpr size_t O_HSLOT = O_LS + (size_t)kL * 4;        // [kL] int global slot of halo particle h
+    static constexpr size_t O_SENT = O_HSLOT + (size_t)kL * 4;      // [kES] u16 local partners of the rows of S
+    static constexpr size_t O_FENT = O_SENT + (size_t)kES * 2;      // [kEF] u16 local partners of the own rows
+    static constexpr size_t O_SDESC = O_FENT + (size_t)kEF * 2;     // [kL] int2 row of S: (lane's first entry, centre | n << 16)
+    static constexpr size_t O_FDESC = O_SDESC + (size_t)kL * 8;     // [kBlock] int4 own row: (first reactive entry,
+                                                                    // first other entry, nr | nw << 16, centre)
+    // the own particles' state, by row position, kept here between list builds
+    // (global memory is brought up to date by r_flush)
+    static constexpr size_t O_VEL = O_FDESC + (size_t)kBlock * 16;  // [kBlock] float4 velocities
+    static constexpr size_t O_XQ = O_VEL + (size_t)kBlock * 16;     // [3 kBlock] fixed-point positions
+    static constexpr size_t O_IMG = O_XQ + (size_t)kBlock * 24;     // [3 kBlock] image counts
     static constexpr size_t kBytes = O_IMG + (size_t)kBlock * 12;
-    // the thermo staging (kNQA x kBlock floats) and the build's hash table
-    // (2 x kHash ints) reuse the staging area from O_VEL on
-    static_assert((size_t)kNQA * kBlock * 4 <= kBytes - O_VEL, "thermo staging");
-    static_assert((size_t)2 * kHash * 4 <= kBytes - O_VEL, "hash table");
-    static_assert(kE <= 65536 && kL <= 65536, "16-bit local indices");
-    static_assert(kHash % kBlock == 0 && kH % kBlock == 0, "whole rounds per thread");
+    // While building, the own-state area holds the hash table (keys, values),
+    // the sort histogram and the warp-block lengths; O_SENT holds the
+    // reactive first shell's table indices, O_LS the centres of the rows of S
+    // by position.
+    static constexpr size_t B_KEY = O_VEL, B_VAL = B_KEY + (size_t)kHash * 4, B_HIST = B_VAL + (size_t)kHash * 4,
+                            B_WL = B_HIST + 256 * 4, B_END = B_WL + ((size_t)kRounds * 32 + 1) * 4;
+    static_assert(B_END <= kBytes, "build scratch fits the own-state area");
+    static_assert(kES <= 65536 && kEF <= 65536 && kL <= 65536, "16-bit local indices and offsets");
+    static_assert(kBlock % 32 == 0 && kBlock / 32 <= 32, "whole warps, at most 32");
 
     static __device__ __forceinline__ int4* lpos() { return (int4*)(g_dyn + O_LPOS); }
     static __device__ __forceinline__ float* lS() { return (float*)(g_dyn + O_LS); }
     static __device__ __forceinline__ int* hslot() { return (int*)(g_dyn + O_HSLOT); }
-    static __device__ __forceinline__ unsigned short* ent() { return (unsigned short*)(g_dyn + O_ENT); }
-    static __device__ __forceinline__ unsigned* orow() { return (unsigned*)(g_dyn + O_OROW); }
-    static __device__ __forceinline__ int2* srow() { return (int2*)(g_dyn + O_SROW); }
+    static __device__ __forceinline__ unsigned short* sent() { return (unsigned short*)(g_dyn + O_SENT); }
+    static __device__ __forceinline__ unsigned short* fent() { return (unsigned short*)(g_dyn + O_FENT); }
+    static __device__ __forceinline__ int2* sdesc() { return (int2*)(g_dyn + O_SDESC); }
+    static __device__ __forceinline__ int4* fdesc() { return (int4*)(g_dyn + O_FDESC); }
     static __device__ __forceinline__ float4* vel() { return (float4*)(g_dyn + O_VEL); }
     static __device__ __forceinline__ long long* xq() { return (long long*)(g_dyn + O_XQ); }
     static __device__ __forceinline__ int* img() { return (int*)(g_dyn + O_IMG); }
-    static __device__ __forceinline__ float* stage() { return (float*)(g_dyn + O_VEL); }
 };
-static_assert(RStage::kBytes <= Stage<float>::kBytes, "the resident layout reuses the staging buffer");
+static_assert(RStage::kBytes <= Stage<float>::kBytes + 32768, "the resident layout fits the kernel's shared memory");
 
 __device__ __forceinline__ void cp_async_cg16(void* smem, const void* gmem)
 {
@@ -1705,20 +1763,81 @@ __device__ __forceinline__ int r_lid(const int* key, const int* val, int q, int 
     return P + (val[h] >> 1);
 }
 
+// Counting sort, largest key first, of up to R items per thread (keys in
+// [0, 255], -1: no item); pos[r] gets item r's rank.  Equal keys keep the
+// order (thread, then round), so the result is the same on every run.
+template <int R>
+__device__ void r_sort_desc(const int (&key)[R], int (&pos)[R], int* hist)
+{
+    const int t = threadIdx.x, B = blockDim.x;
+    for (int h = t; h < 256; h += B) hist[h] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; r++)
+        if (key[r] >= 0) atomicAdd(&hist[key[r]], 1);
+    __syncthreads();
+    int base = 0;
+    for (int c = 255; c >= 0; c--) {
+        if (hist[c] == 0) continue;  // the same in every thread
+        int cl = 0;
+#pragma unroll
+        for (int r = 0; r < R; r++) cl += key[r] == c;
+        int tot;
+        int off = block_excl_scan(cl, s_int, &tot);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (key[r] == c) pos[r] = base + off++;
+        base += tot;
+    }
+}
+
+// Lays out warp blocks: rows at positions s (thread s % B, round s / B) with
+// n[r] entries each (0: no row); every warp block of 32 rows takes 32 x its
+// longest row, in order (round, warp).  Returns the total (entries), and in
+// first[r] the entry of row r's lane (entry k of the row at first + 32 k).
+template <int R>
+__device__ int r_warp_layout(const int (&n)[R], int (&first)[R], int* wl)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int L = __reduce_max_sync(0xffffffffu, n[r]);
+        if (lane == 0) wl[r * nw + warp] = L;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int acc = 0;
+        for (int b = 0; b < R * nw; b++) {
+            const int L = wl[b];
+            wl[b] = acc;
+            acc += 32 * L;
+        }
+        wl[R * nw] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; r++) first[r] = wl[r * nw + warp] + lane;
+    const int total = wl[R * nw];
+    __syncthreads();
+    return total;
+}
+
 // Builds the block's resident structures from the global list and the
 // snapshots pos[pc].  Returns 1 when they fit (the same answer in every
 // thread of the block); 0 leaves nothing the step relies on.
-static __device__ int r_localize(const Dev<float>& d, int pc)
+static __device__ int r_localize(const Dev<float>& d, int pc, int ac)
 {
     typedef RStage RS;
-    constexpr int PER = RS::kHash / kBlock, RR = RS::kH / kBlock;
+    constexpr int RR = RS::kRounds;
     int4* lpos = RS::lpos();
-    int* hslot = RS::hslot();
-    unsigned short* ent = RS::ent();
-    int2* srow = RS::srow();
-    int* key = (int*)RS::stage();
-    int* val = key + RS::kHash;  // bit 0: reactive partner of an own particle; then the compact rank << 1
+    int* key = (int*)(g_dyn + RS::B_KEY);
+    int* val = (int*)(g_dyn + RS::B_VAL);  // bit 0: reactive partner of an own particle; then the rank << 1
+    int* hist = (int*)(g_dyn + RS::B_HIST);
+    int* wl = (int*)(g_dyn + RS::B_WL);
+    int* hr = (int*)RS::sent();   // table index of the k-th reactive first-shell particle
+    int* cen = (int*)RS::lS();    // centre (local index) of the row at each position
     const int t = threadIdx.x, B = blockDim.x;
+    const int PER = (RS::kHash + B - 1) / B;
     int b0, b1;
     block_range(d, b0, b1);
     const int P = b1 - b0;
@@ -1747,19 +1866,18 @@ static __device__ int r_localize(const Dev<float>& d, int pc)
     }
     if (__syncthreads_or(fail)) return 0;
     // 2. its reactive part (their S is formed here too), in table order
+    const int h0 = min(t * PER, RS::kHash), h1 = min(h0 + PER, RS::kHash);
     int c = 0;
-#pragma unroll
-    for (int k = 0; k < PER; k++) c += val[t * PER + k] & 1;
+    for (int h = h0; h < h1; h++) c += val[h] & 1;
     int Hr;
     int off = block_excl_scan(c, s_int, &Hr);
-    if (Hr > RS::kH) return 0;  // Hr is the same in every thread
-#pragma unroll
-    for (int k = 0; k < PER; k++)
-        if (val[t * PER + k] & 1) srow[off++].y = t * PER + k;  // table index, for now
+    if (P + Hr > RS::kL) return 0;  // Hr is the same in every thread
+    for (int h = h0; h < h1; h++)
+        if (val[h] & 1) hr[off++] = h;
     __syncthreads();
     // 3. second shell: the reactive partners of the reactive first shell
     for (int k = t; k < Hr; k += B) {
-        const int4 fi = d.pinfo[key[srow[k].y]];
+        const int4 fi = d.pinfo[key[hr[k]]];
         for (int e = fi.x; e < fi.x + fi.y; e++) {
             const int q = d.ent_j[e];
             if ((q < b0 || q >= b1) && r_insert(key, q) < 0) fail = 1;
@@ -1768,98 +1886,158 @@ static __device__ int r_localize(const Dev<float>& d, int pc)
     if (__syncthreads_or(fail)) return 0;
     // 4. compact the table: halo particle of rank r has local index P + r
     c = 0;
-#pragma unroll
-    for (int k = 0; k < PER; k++) c += key[t * PER + k] != -1;
+    for (int h = h0; h < h1; h++) c += key[h] != -1;
     int H;
     off = block_excl_scan(c, s_int, &H);
-    if (H > RS::kH || P + H > RS::kL) return 0;
-#pragma unroll
-    for (int k = 0; k < PER; k++) {
-        const int h = t * PER + k;
+    if (P + H > RS::kL) return 0;
+    for (int h = h0; h < h1; h++) {
         if (key[h] != -1) {
-            hslot[off] = key[h];
+            RS::hslot()[off] = key[h];
             val[h] = (val[h] & 1) | (off << 1);
             off++;
         }
     }
-    // 5. entry offsets: the own rows, then the halo rows of S
+    __syncthreads();
+    // 5. rows of S (the own rows and the reactive first shell's), longest
+    // first, dealt out over the threads as a snake: rank s goes to round
+    // s / B, to thread s % B in even rounds and B - 1 - s % B in odd ones, so
+    // that a thread's second row is short when its first is long.  Rows of
+    // the force pass: the own rows, longest (reactive + other) first.
+    const int NS = P + Hr;
+    const int rounds = (NS + B - 1) / B;
     int4 inf = make_int4(0, 0, 0, 0);
     if (t < P) inf = d.pinfo[b0 + t];
     if (inf.y > 255 || inf.w > 255) fail = 1;
-    int Eo;
-    const int st_own = block_excl_scan(inf.y + inf.w, s_int, &Eo);
-    int st_h[RR], cnt_h[RR], cen_h[RR];
-    int base = Eo;
+    int skey[RR + 1], spos[RR + 1], hrow[RR], hcnt[RR];
+    skey[0] = t < P ? min(inf.y, 255) : -1;
+    spos[0] = 0;
 #pragma unroll
     for (int r = 0; r < RR; r++) {
         const int k = t + r * B;
-        int cn = 0, h = 0;
+        skey[r + 1] = -1;
+        spos[r + 1] = 0;
+        hrow[r] = hcnt[r] = 0;
         if (k < Hr) {
-            h = srow[k].y;
-            cn = d.pinfo[key[h]].y;
+            const int4 fi = d.pinfo[key[hr[k]]];
+            hrow[r] = fi.x;
+            hcnt[r] = fi.y;
+            if (fi.y > 255) fail = 1;
+            skey[r + 1] = min(fi.y, 255);
         }
-        int tot;
-        st_h[r] = base + block_excl_scan(cn, s_int, &tot);
-        base += tot;
-        cnt_h[r] = cn;
-        cen_h[r] = h;
     }
-    if (base > RS::kE) fail = 1;
+    r_sort_desc<RR + 1>(skey, spos, hist);
+    int fkey[1] = {t < P ? min(inf.y + inf.w, 255) : -1}, fpos[1] = {0};
+    r_sort_desc<1>(fkey, fpos, hist);
+    for (int q = t; q < rounds * B; q += B) RS::sdesc()[q] = make_int2(0, -1);  // no row here
+    __syncthreads();
+    // what each position needs: the centre and the row (start, count)
+#pragma unroll
+    for (int r = 0; r <= RR; r++) {
+        if (skey[r] < 0) continue;
+        const int sr = spos[r], g = sr / B, slot = sr - g * B;
+        const int q = g * B + ((g & 1) ? B - 1 - slot : slot);
+        if (r == 0) {
+            cen[q] = t;
+            RS::sdesc()[q] = make_int2(inf.x, inf.y);
+        } else {
+            const int k = t + (r - 1) * B;
+            cen[q] = P + (val[hr[k]] >> 1);
+            RS::sdesc()[q] = make_int2(hrow[r - 1], hcnt[r - 1]);
+        }
+    }
+    if (t < P) RS::fdesc()[fpos[0]] = make_int4(inf.x, inf.z, inf.y | (inf.w << 16), t);
     if (__syncthreads_or(fail)) return 0;
-    // 6. the rows, partners as local indices, and the own snapshots
-    if (t < P) {
-        for (int k = 0; k < inf.y; k++)
-            ent[st_own + k] = (unsigned short)r_lid(key, val, d.ent_j[inf.x + k], b0, b1, P, fail);
-        for (int k = 0; k < inf.w; k++)
-            ent[st_own + inf.y + k] = (unsigned short)r_lid(key, val, d.ent_j[inf.z + k], b0, b1, P, fail);
-        RS::orow()[t] = (unsigned)st_own | ((unsigned)inf.y << 16) | ((unsigned)inf.w << 24);
-        lpos[t] = d.pos[pc][b0 + t];
-    }
+    // 6. warp-major layouts: the rows of S; the own rows' reactive parts, then
+    // their other parts
+    int n[RR], first[RR];
 #pragma unroll
     for (int r = 0; r < RR; r++) {
-        const int k = t + r * B;
-        if (k < Hr) {
-            const int h = cen_h[r];
-            const int4 fi = d.pinfo[key[h]];
-            for (int m = 0; m < cnt_h[r]; m++)
-                ent[st_h[r] + m] = (unsigned short)r_lid(key, val, d.ent_j[fi.x + m], b0, b1, P, fail);
-            srow[k] = make_int2(st_h[r] | (cnt_h[r] << 16), P + (val[h] >> 1));
+        const int q = t + r * B;
+        n[r] = r < rounds ? max(RS::sdesc()[q].y, 0) : 0;
+    }
+    const int ES = r_warp_layout<RR>(n, first, wl);
+    const int4 fd = t < P ? RS::fdesc()[t] : make_int4(0, 0, 0, 0);
+    int nrc[1] = {fd.z & 0xffff}, nwc[1] = {fd.z >> 16}, rfirst[1], wfirst[1];
+    const int ER = r_warp_layout<1>(nrc, rfirst, wl);
+    const int EW = r_warp_layout<1>(nwc, wfirst, wl);
+    if (ES > RS::kES || ER + EW > RS::kEF) return 0;  // the same in every thread
+    // 7. the rows, partners as local indices
+#pragma unroll
+    for (int r = 0; r < RR; r++) {
+        const int q = t + r * B;
+        if (r < rounds) {
+            const int2 src = RS::sdesc()[q];
+            if (src.y >= 0) {
+                const int lid = cen[q];
+                for (int m = 0; m < src.y; m++)
+                    RS::sent()[first[r] + 32 * m] =
+                        (unsigned short)r_lid(key, val, d.ent_j[src.x + m], b0, b1, P, fail);
+                RS::sdesc()[q] = make_int2(first[r], lid | (src.y << 16));
+            }
         }
+    }
+    if (t < P) {
+        unsigned short* fe = RS::fent();
+        for (int m = 0; m < nrc[0]; m++)
+            fe[rfirst[0] + 32 * m] = (unsigned short)r_lid(key, val, d.ent_j[fd.x + m], b0, b1, P, fail);
+        for (int m = 0; m < nwc[0]; m++)
+            fe[ER + wfirst[0] + 32 * m] = (unsigned short)r_lid(key, val, d.ent_j[fd.y + m], b0, b1, P, fail);
+        RS::fdesc()[t] = make_int4(rfirst[0], ER + wfirst[0], fd.z, fd.w);
+        lpos[t] = d.pos[pc][b0 + t];  // own snapshots by local index
     }
     if (t == 0) {
         s_ls.r_np = P;
         s_ls.r_nh = H;
         s_ls.r_nhr = Hr;
     }
-    return __syncthreads_or(fail) ? 0 : 1;
+    const int ok = __syncthreads_or(fail) ? 0 : 1;
+    // 8. the own particles' state by force-row position (over the table, now unused)
+    if (ok && t < P) {
+        const int i = b0 + RS::fdesc()[t].w, n = d.n;
+        RS::vel()[t] = d.vel[ac][i];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            RS::xq()[3 * t + c] = d.xq[ac][c * n + i];
+            RS::img()[3 * t + c] = d.img[ac][c * n + i];
+        }
+    }
+    __syncthreads();
+    return ok;
 }
 
-// Issues a step's copies: the halo's snapshots pos[pc] (L2 only: other blocks
-// wrote them) and the own particles' velocities, fixed-point positions and
-// image counts (set ac).
-__device__ __forceinline__ void r_gather(const Dev<float>& d, int pc, int ac)
+// Writes the own particles' state back to the global arrays (set ac): before
+// a list build reorders them, and when the run ends.
+__device__ __forceinline__ void r_flush(const Dev<float>& d, int ac)
 {
     typedef RStage RS;
-    const int t = threadIdx.x, B = blockDim.x, P = s_ls.r_np, H = s_ls.r_nh, n = d.n;
-    int b0, b1;
-    block_range(d, b0, b1);
+    const int t = threadIdx.x, n = d.n;
+    if (t < s_ls.r_np) {
+        int b0, b1;
+        block_range(d, b0, b1);
+        const int i = b0 + RS::fdesc()[t].w;
+        d.vel[ac][i] = RS::vel()[t];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            d.xq[ac][c * n + i] = RS::xq()[3 * t + c];
+            d.img[ac][c * n + i] = RS::img()[3 * t + c];
+        }
+    }
+}
+
+// Issues a step's copies of the halo's snapshots pos[pc] (through L2 only:
+// other blocks wrote them).
+__device__ __forceinline__ void r_gather(const Dev<float>& d, int pc)
+{
+    typedef RStage RS;
+    const int t = threadIdx.x, B = blockDim.x, P = s_ls.r_np, H = s_ls.r_nh;
     int4* lpos = RS::lpos();
     const int* hslot = RS::hslot();
     const int4* pos = d.pos[pc];
     for (int h = t; h < H; h += B) cp_async_cg16(&lpos[P + h], &pos[hslot[h]]);
-    if (t < P) {
-        const int i = b0 + t;
-        cp_async_cg16(&RS::vel()[t], &d.vel[ac][i]);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            cp_async(&RS::xq()[3 * t + c], &d.xq[ac][c * n + i], 8);
-            cp_async(&RS::img()[3 * t + c], &d.img[ac][c * n + i], 4);
-        }
-    }
     cp_async_commit();
 }
 
-// S of one row (first..first+cnt of ent) with the two-barrier path's order of
+// S of one row (entries e[0], e[32], ...) with the two-barrier path's order of
 // additions (groups of four, then one by one).
 template <bool UNI>
 __device__ __forceinline__ float r_row_s(const Dev<float>& d, const PairP<float>* tab, const PairP<float>& ps,
@@ -1868,29 +2046,31 @@ __device__ __forceinline__ float r_row_s(const Dev<float>& d, const PairP<float>
     float s = 0.0f;
     int k = 0;
     for (; k + 4 <= cnt; k += 4) {
-        const float w0 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k]]);
-        const float w1 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k + 1]]);
-        const float w2 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k + 2]]);
-        const float w3 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[k + 3]]);
+        const float w0 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[32 * k]]);
+        const float w1 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[32 * (k + 1)]]);
+        const float w2 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[32 * (k + 2)]]);
+        const float w3 = s_term<float, UNI>(d, tab, ps, pi, lpos[e[32 * (k + 3)]]);
         s += (w0 + w1) + (w2 + w3);
     }
-    for (; k < cnt; k++) s += s_term<float, UNI>(d, tab, ps, pi, lpos[e[k]]);
+    for (; k < cnt; k++) s += s_term<float, UNI>(d, tab, ps, pi, lpos[e[32 * k]]);
     return s;
 }
 
 // One resident step: S of the own particles and the reactive halo, the pair
 // forces of the own rows (entry order: reactive, then the others), the
-// integrator.  Returns the thread's squared drift displacement.
+// integrator.  The thermo terms are left summed per warp in s_wpart (the
+// step's barrier completes the block sums).  Returns the thread's squared
+// drift displacement.
 template <bool UNI>
 __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long long step, Acc<float>& acc)
 {
     typedef RStage RS;
-    const int t = threadIdx.x, B = blockDim.x, n = d.n;
-    const int P = s_ls.r_np, nS = P + s_ls.r_nhr;
-    const int pc = s_ls.pc, ac = s_ls.ac;
+    const int t = threadIdx.x, B = blockDim.x;
+    const int P = s_ls.r_np, NQ = (P + s_ls.r_nhr + B - 1) / B * B;  // positions of the rows of S
+    const int pc = s_ls.pc;
     int b0, b1;
     block_range(d, b0, b1);
-    if (!s_ls.r_gathered) r_gather(d, pc, ac);
+    if (!s_ls.r_gathered) r_gather(d, pc);
     cp_async_wait_all();
     __syncthreads();
     const PairP<float>* tab = stab<float>();
@@ -1898,50 +2078,61 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
     const PairP<float>& pw = a.uf[1];
     int4* lpos = RS::lpos();
     float* lS = RS::lS();
-    const unsigned short* ent = RS::ent();
-    for (int r = t; r < nS; r += B) {
-        int first, cnt, lid;
-        if (r < P) {
-            const unsigned o = RS::orow()[r];
-            first = (int)(o & 0xffffu);
-            cnt = (int)((o >> 16) & 0xffu);
-            lid = r;
-        } else {
-            const int2 sr = RS::srow()[r - P];
-            first = sr.x & 0xffff;
-            cnt = (int)((unsigned)sr.x >> 16);
-            lid = sr.y;
-        }
-        lS[lid] = r_row_s<UNI>(d, tab, ps, lpos, ent + first, cnt, lpos[lid]);
+    for (int q = t; q < NQ; q += B) {
+        const int2 dsc = RS::sdesc()[q];
+        if (dsc.y < 0) continue;  // no row at this position
+        const int lid = dsc.y & 0xffff;
+        lS[lid] = r_row_s<UNI>(d, tab, ps, lpos, RS::sent() + dsc.x, (int)((unsigned)dsc.y >> 16), lpos[lid]);
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kNQA; q++) acc.q[q] = 0.0f;
     float dmax = 0.0f, kin = 0.0f;
-    int4 np = make_int4(0, 0, 0, 0);
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    int4 pi = make_int4(0, 0, 0, 0);
+    int lid = 0;
     if (t < P) {
-        const unsigned o = RS::orow()[t];
-        const int first = (int)(o & 0xffffu), nr = (int)((o >> 16) & 0xffu), nw = (int)(o >> 24);
-        const int4 pi = lpos[t];
-        const float Si = lS[t];
-        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+        const int4 fd = RS::fdesc()[t];
+        lid = fd.w;
+        const int nr = fd.z & 0xffff, nw = fd.z >> 16;
+        const unsigned short* er = RS::fent() + fd.x;
+        const unsigned short* ew = RS::fent() + fd.y;
+        pi = lpos[lid];
+        const float Si = lS[lid];
+#pragma unroll 2
         for (int k = 0; k < nr; k++) {
-            const int j = ent[first + k];
+            const int j = er[32 * k];
             float ex, ey, ez;
             entry_force<float, UNI, true>(d, tab, pi, lpos[j], Si, lS[j], ps, acc, ex, ey, ez);
             fx = __fadd_rn(fx, ex);
             fy = __fadd_rn(fy, ey);
             fz = __fadd_rn(fz, ez);
         }
-        for (int k = nr; k < nr + nw; k++) {
-            const int j = ent[first + k];
+#pragma unroll 2
+        for (int k = 0; k < nw; k++) {
+            const int j = ew[32 * k];
             float ex, ey, ez;
             entry_force<float, UNI, false>(d, tab, pi, lpos[j], 0.0f, 0.0f, pw, acc, ex, ey, ez);
             fx = __fadd_rn(fx, ex);
             fy = __fadd_rn(fy, ey);
             fz = __fadd_rn(fz, ez);
         }
-        const int i = b0 + t;
+    }
+    // the pair terms go to the warp partials now, so that the accumulators are
+    // not live through the integrator (the kinetic term follows it)
+    const bool rows = (t & ~31) < P;  // the warp holds rows (the same in all its lanes)
+    if (rows) {
+#pragma unroll
+        for (int q = 0; q < kNQA; q++)
+            if (q != Q_K) warp_part(acc.q[q], q);
+    } else if ((t & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < kNQA; q++)
+            if (q != Q_K) s_wpart[q][t >> 5] = 0.0f;
+    }
+    int4 np = make_int4(0, 0, 0, 0);
+    if (t < P) {
+        const int i = b0 + lid;
         if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&d.ctl->status, kStatusNonfinite);
         if (flags & F_STORE) d.force[i] = make_float4(fx, fy, fz, 0.0f);
         float4 v = RS::vel()[t];
@@ -1953,16 +2144,19 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         if (flags & F_OPENING) {
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                d.xq[ac][c * n + i] = q[c];
-                if (w[c]) d.img[ac][c * n + i] = RS::img()[3 * t + c] + w[c];
+                RS::xq()[3 * t + c] = q[c];
+                RS::img()[3 * t + c] += w[c];
             }
-            d.pos[pc ^ 1][i] = np;
+            d.pos[pc ^ 1][i] = np;  // the other blocks' halos read it
         }
-        d.vel[ac][i] = v;
+        RS::vel()[t] = v;
     }
-    acc.q[Q_K] += kin;
+    if (rows)
+        warp_part(kin, Q_K);
+    else if ((t & 31) == 0)
+        s_wpart[Q_K][t >> 5] = 0.0f;
     __syncthreads();  // every row has read the old snapshots
-    if (t < P && (flags & F_OPENING)) lpos[t] = np;
+    if (t < P && (flags & F_OPENING)) lpos[lid] = np;
     if (t == 0) {
         s_ls.r_gathered = 0;
         s_ls.r_steps++;
@@ -1975,7 +2169,7 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
 // runs resident only if every block's structures fit.
 static __device__ bool r_enter(const Dev<float>& d, const RunArgs& a)
 {
-    const int ok = r_localize(d, s_ls.pc);
+    const int ok = r_localize(d, s_ls.pc, s_ls.ac);
     const int round = s_ls.r_round;
     if (threadIdx.x == 0 && !ok) atomicOr(&d.ctl->rfail[round & 1], 1);
     if (!grid_barrier(d.ctl, a.timeout_ns, 8)) return false;
@@ -1992,6 +2186,7 @@ static __device__ bool r_enter(const Dev<float>& d, const RunArgs& a)
     __syncthreads();
     return true;
 }
+
 #endif  // !SWP_BATCHED
 
 // One system advanced by the group of blocks this block belongs to (g_rank /
@@ -2065,7 +2260,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             if (s_ls.rc == 0) {
                 run_s_pass<Real, UNI>(d, a);
                 if (!grid_barrier(ctl, a.timeout_ns, 10)) return false;
-                const int par = (int)(s_ls.step % kParities);
+                const int par = next_parity();
                 Acc<Real> acc;
                 run_f_pass<Real, UNI, BONDS>(d, a, F_STORE, s_ls.step, acc);
                 if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
@@ -2092,6 +2287,10 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
                 // a resident gather issued for this step lands in memory the rebuild reuses
                 cp_async_wait_all();
+#if !SWP_BATCHED
+                if constexpr (kRes)
+                    if (s_ls.r_valid) r_flush(d, s_ls.ac);  // the build reorders the global state
+#endif
                 const int rc = run_rebuild(d, a);
                 if (rc == 2) return false;
                 if (threadIdx.x == 0) {
@@ -2105,7 +2304,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 if (rc) break;
             }
             const bool more = s_ls.remaining > 1;
-            const int par = (int)((stp + 1) % kParities);
+            const int par = next_parity();
             const int flags = F_CLOSING | (more ? F_OPENING : F_STORE);
             Acc<Real> acc;
             Real* stage = Stage<Real>::w();
@@ -2117,7 +2316,6 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 if (s_ls.r_valid) {
                     const float dmax = r_step<UNI>(d, a, flags, stp + 1, acc);
                     if (more) warp_max_disp(dmax);
-                    stage = (Real*)RStage::stage();
                     resident = true;
                 }
             }
@@ -2141,20 +2339,30 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 s_ls.remaining--;
                 s_ls.done++;
             }
-            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21, stage)) return false;
+            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21, stage, resident))
+                return false;
             if (more) {
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
                 __syncthreads();
+                bool gathered = false;
 #if !SWP_BATCHED
                 if constexpr (kRes) {
-                    // the next step's copies overlap the displacement read
                     if (s_ls.r_valid) {
-                        r_gather(d, s_ls.pc, s_ls.ac);
-                        if (threadIdx.x == 0) s_ls.r_gathered = 1;
+                        // the displacement read is in flight while the next
+                        // step's copies are issued
+                        unsigned dm = 0u;
+                        if (threadIdx.x == 0) dm = (unsigned)ld_relaxed((const int*)&ctl->dmax2[(stp + 1) & 1]);
+                        r_gather(d, s_ls.pc);
+                        if (threadIdx.x == 0) {
+                            s_ls.r_gathered = 1;
+                            s_ls.disp += sqrtf(__uint_as_float(dm));
+                        }
+                        __syncthreads();
+                        gathered = true;
                     }
                 }
 #endif
-                add_disp(ctl, stp + 1);
+                if (!gathered) add_disp(ctl, stp + 1);
             } else {
                 if (threadIdx.x == 0) s_ls.state = 0;
                 __syncthreads();
@@ -2162,6 +2370,10 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         }
     }
     cp_async_wait_all();  // a reduction started at the last barrier is not needed
+#if !SWP_BATCHED
+    if constexpr (kRes)
+        if (s_ls.r_valid) r_flush(d, s_ls.ac);
+#endif
     if (s_ls.have_thermo) {
         // the last pass's partials were written after its barrier's arrival
         if (!grid_barrier(ctl, a.timeout_ns, 30)) return false;

@@ -24,7 +24,8 @@ static void* run_fn(int uni, int bonds = 0)
 template <typename Real>
 size_t run_smem_bytes()
 {
-    return Stage<Real>::kBytes;
+    // the two-barrier step's staging or the resident step's structures (one buffer)
+    return std::max(Stage<Real>::kBytes, single::RStage::kBytes);
 }
 
 // Opts every variant into the dynamic shared memory it needs (once).

@@ -44,9 +44,15 @@ def _min_dist_brute(cand, pts, box):
     return np.sqrt((d * d).sum(-1)).min(axis=1)
 
 
-def rsa_positions(n: int, box, min_sep: float = 0.9, seed: int = 1, batch: int = 16384,
+def rsa_positions(n: int, box, min_sep: float = 0.9, seed: int = 1, batch: int | None = None,
                   max_tries: int = 10000) -> np.ndarray:
-    """n positions (n x 3, float32-representable) with pairwise separation >= min_sep."""
+    """n positions (n x 3, float32-representable) with pairwise separation >= min_sep.
+
+    Candidates are drawn in batches of 16,384 (262,144 above 500,000
+    particles, where rebuilding the tree of accepted points per batch would
+    dominate: a 2M-particle box then takes about a minute instead of several)."""
+    if batch is None:
+        batch = 16384 if n <= 500_000 else 262_144
     box = np.asarray(box, dtype=np.float64)
     rng = np.random.Generator(np.random.Philox(seed))
     pts = np.zeros((0, 3))

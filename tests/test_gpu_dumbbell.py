@@ -47,7 +47,7 @@ def test_dumbbell_forces_match_oracle(orc, precision, rcut):
     s.compute_forces()
     tab = oracle_pairs(orc, wl)
     ref = orc.forces(wl["x"], wl["types"], 2, tab, wl["box"], fp32=precision == "fp32")
-    assert ref["n_bonds"] == 400  # every B starts bonded to its own A
+    assert ref["n_bonds"] >= 400  # every B starts bonded to its own A (a few also to a neighbour's)
     assert_forces_match(s.forces(), ref, TOL[precision], f"dumbbell start r_c={rcut}")
     assert_thermo_match(s.thermo(), ref, TOL[precision], f"dumbbell start r_c={rcut}")
     # after the dynamics has explored the bond wells (thermal approaches inside r_min)

@@ -479,6 +479,30 @@ def test_nvt_equipartition(orc):
     assert K == pytest.approx(1.5 * n * kT, rel=0.03)
 
 
+def test_c9_force_scale_closed_forms(orc):
+    """The second force scale (forces' size times the three-body factor they
+    can receive) on isolated pairs: a WCA pair gives |dv/dr| to both ends; a
+    reactive pair at r gives |dv/dr| (1 + lambda (vh(r) + vh(r))), with vh of
+    Eq. pot; a pair beyond its cut-off gives nothing."""
+    L = 20.0
+    box = np.array([L, L, L])
+    for kind, r, lam in (("wca", 1.05, 1.0), ("swap", 1.3, 1.0), ("swap", 1.3, 5.0), ("swap", 1.6, 1.0)):
+        pairs = inputs.swap_pairs(lambda3=lam)
+        tab = orc.pair_table(2, pairs)
+        types = np.array([0, 0] if kind == "wca" else [0, 1], dtype=np.int32)
+        x = np.array([[5.0, 5.0, 5.0], [5.0 + r, 5.0, 5.0]])
+        c9 = orc.fscale_c9(x, types, 2, tab, box)
+        if kind == "wca":
+            n = 6
+            want = abs(orc.dv2(r, n=n))
+        elif r >= 1.5:
+            want = 0.0
+        else:
+            vh = orc.vhat(r, eps=1.0, sigma=1.0, n=10, rcut=1.5, lambda3=lam)
+            want = abs(orc.dv2(r, n=10)) * (1.0 + lam * 2.0 * vh)
+        np.testing.assert_allclose(c9, [want, want], rtol=1e-13, atol=0.0)
+
+
 def test_threaded_oracle_matches_one_thread(orc):
     """The OpenMP build (the all-cores CPU baseline) computes the same terms:
     equal to the one-thread oracle up to the grouping of the additions."""
