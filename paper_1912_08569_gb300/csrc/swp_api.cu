@@ -197,7 +197,7 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     int* perm = (int*)take(sizeof(int) * n);
     int* bsum = (int*)take(sizeof(int) * c->max_blocks);
     // thermo partials of the step kernel; also the scratch of the parameter derivatives (4 * 512 + 4)
-    double* partials = (double*)take(sizeof(double) * std::max<size_t>((size_t)kParities * c->max_blocks * kNQ, 4 * 512 + 4));
+    double* partials = (double*)take(sizeof(double) * std::max<size_t>((size_t)c->max_blocks * kNQ, 4 * 512 + 4));
     double* io = (double*)take(sizeof(double) * 7 * n);
     int* io_int = (int*)take(sizeof(int) * 4 * n);
     int* bond_tag = (int*)take(sizeof(int) * kMaxBonds * n);

@@ -20,7 +20,6 @@ constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays c
 // Thermo quantities, in the order of the per-block partials.
 enum { Q_U2 = 0, Q_U3 = 1, Q_K = 2, Q_W0 = 3, Q_BONDS = 9, Q_SPARE0 = 10, Q_SPARE1 = 11 };
 constexpr int kNQA = 10;  // quantities accumulated per thread (Q_U2 .. Q_BONDS)
-constexpr int kParities = 3;  // thermo partial buffers in rotation (see f_barrier)
 
 // Fixed-point position unit: positions are int64 multiples of 2^-48 sigma.
 constexpr double kFix = 281474976710656.0;          // 2^48
@@ -145,7 +144,7 @@ struct Dev {
     int* cell_fill;    // [ncell]
     int* perm;         // [n] new slot -> old slot
     int* bsum;         // [max_blocks] per-block cell-count sums (scan)
-    double* partials;  // [kParities][max_blocks][kNQ]
+    double* partials;  // [max_blocks][kNQ]
     Ctl* ctl;
     double* io;        // host-exchange staging: [3n] x, [3n] v, [n] mass
     int* io_int;       // staging: [n] types, [3n] images

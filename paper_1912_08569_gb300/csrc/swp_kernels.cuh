@@ -1176,10 +1176,10 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
 }
 
 // One entry's pair force on its owner (returned as the components of
-// f (x_i - x_j)), with the entry's share of energies, virial and bond count.
-// REACT: a reactive pair (two-body plus the three-body factor); else a
-// purely two-body pair.
-template <typename Real, bool UNI, bool REACT>
+// f (x_i - x_j)), with the entry's share of energies, virial and bond count
+// when TH (the sampled step of a launch).  REACT: a reactive pair (two-body
+// plus the three-body factor); else a purely two-body pair.
+template <typename Real, bool UNI, bool REACT, bool TH>
 __device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real>* tab,
                                             const typename Dev<Real>::P4& pi,
                                             const typename Dev<Real>::P4& pj, Real Si, Real Sj,
@@ -1194,19 +1194,22 @@ __device__ __forceinline__ void entry_force(const Dev<Real>& d, const PairP<Real
     const bool in = r2 < p.rc2;
     Real v, ft;
     lj_eval(p, r2, v, ft);
-    acc.q[Q_U2] += in ? Real(0.5) * (v + p.ushift) : Real(0);
+    if (TH) acc.q[Q_U2] += in ? Real(0.5) * (v + p.ushift) : Real(0);
     if (REACT) {
         const bool beyond = r2 > p.rmin2;
         const Real vh = beyond ? (p.vshift - v) * p.inv_epshat : Real(1);
         const Real h = p.a * (Si + Sj - Real(2) * p.a * vh);
         ft = beyond ? ft * (Real(1) - h * p.inv_epshat) : ft;
-        acc.q[Q_U3] += in ? Real(0.5) * p.a * vh * (Si - p.a * vh) : Real(0);
-        acc.q[Q_BONDS] += (in && r2 < p.rbond2) ? Real(0.5) : Real(0);
+        if (TH) {
+            acc.q[Q_U3] += in ? Real(0.5) * p.a * vh * (Si - p.a * vh) : Real(0);
+            acc.q[Q_BONDS] += (in && r2 < p.rbond2) ? Real(0.5) : Real(0);
+        }
     }
     ft = in ? ft : Real(0);
     fx = -ft * dx;
     fy = -ft * dy;
     fz = -ft * dz;
+    if (!TH) return;
     const Real hf = Real(0.5) * ft;
     acc.q[Q_W0 + 0] += hf * dx * dx;
     acc.q[Q_W0 + 1] += hf * dy * dy;
@@ -1233,8 +1236,9 @@ __device__ __forceinline__ void sum_run(const R4* w, int wb, int k0, int k1, Rea
 
 // With one sub-chunk per block the S pass of the same step left the block's
 // positions, list ranges and S values in shared memory, and the integrator
-// keeps the shared positions current for the next S pass.
-template <typename Real, bool UNI, bool BONDS>
+// keeps the shared positions current for the next S pass.  TH: the sampled
+// step (thermo terms summed into the block's running sums blk).
+template <typename Real, bool UNI, bool BONDS, bool TH>
 __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const RunArgs& a, int pc,
                               int ac, int flags, long long step, Acc<Real>& acc,
                               const PairP<Real>& ps, const PairP<Real>& pw, double* blk)
@@ -1280,9 +1284,9 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
                 const Real sj = e < e_rend ? d.S[j_c] : Real(0);
                 Real ex, ey, ez;
                 if (e < e_rend)
-                    entry_force<Real, UNI, true>(d, tab, SM::pos()[o_c], pj, SM::S()[o_c], sj, ps, acc, ex, ey, ez);
+                    entry_force<Real, UNI, true, TH>(d, tab, SM::pos()[o_c], pj, SM::S()[o_c], sj, ps, acc, ex, ey, ez);
                 else
-                    entry_force<Real, UNI, false>(d, tab, SM::pos()[o_c], pj, Real(0), Real(0), pw, acc, ex, ey, ez);
+                    entry_force<Real, UNI, false, TH>(d, tab, SM::pos()[o_c], pj, Real(0), Real(0), pw, acc, ex, ey, ez);
                 R4 r;
                 r.x = ex;
                 r.y = ey;
@@ -1314,6 +1318,7 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
                 fx += g * dx;
                 fy += g * dy;
                 fz += g * dz;
+                if (!TH) continue;
                 acc.q[Q_U2] += Real(0.25) * d.bond_k * dr * dr;
                 const Real hf = Real(-0.5) * g;
                 acc.q[Q_W0 + 0] += hf * dx * dx;
@@ -1326,7 +1331,7 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         }
         // FP32: park the thermo accumulators in the (now free) wave buffer while
         // the integrator runs, so they do not hold registers at its peak
-        constexpr bool kPark = sizeof(Real) == 4;
+        constexpr bool kPark = TH && sizeof(Real) == 4;
         if (kPark)
 #pragma unroll
             for (int q = 0; q < kNQA; q++) SM::w()[q * blockDim.x + t] = acc.q[q];
@@ -1353,9 +1358,9 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         if (kPark)
 #pragma unroll
             for (int q = 0; q < kNQA; q++) acc.q[q] = SM::w()[q * blockDim.x + t];
-        acc.q[Q_K] += kin;
+        if (TH) acc.q[Q_K] += kin;
         __syncthreads();
-        if (!single) {
+        if (TH && !single) {
             // several sub-chunks: fold this one's terms into the block's FP64
             // running sums, so no thread accumulates more than one sub-chunk
             block_sums(acc.q, SM::w(), blk, (double*)nullptr);
@@ -1396,11 +1401,10 @@ struct LoopState {
     unsigned long long bar_target;  // barrier generation target (thread 0)
     long long step;
     long long rebuilds;
-    int state, pc, ac, need_rb, remaining, done, parity, have_thermo, rc, ok;
+    int state, pc, ac, need_rb, remaining, done, have_thermo, rc, ok;
     float disp;
     unsigned dmax_bits;  // the block's largest squared step displacement (float bits)
     int own_ok;          // shared positions and list ranges of the block's particles are current
-    int red_pending;     // a thermo reduction's copies are in flight into s_rbuf
     // resident mode (section below)
     int r_try;           // build the resident structures before the next step
     int r_valid;         // every block's resident structures are built and current
@@ -1413,7 +1417,6 @@ struct LoopState {
 
 static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
 static __shared__ double s_red[kNQ * 32];
-static __shared__ double s_rbuf[kMaxGrid];
 static __shared__ double s_blk[kNQ];  // the block's FP64 running thermo sums of the current pass
 static __shared__ int s_int[64];
 static __shared__ LoopState s_ls;
@@ -1504,13 +1507,13 @@ __device__ __forceinline__ void warp_max_disp(float v)
     if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(&s_ls.dmax_bits, __float_as_uint(v));
 }
 
-template <typename Real, bool UNI, bool BONDS>
+template <typename Real, bool UNI, bool BONDS, bool TH>
 __device__ __forceinline__ void run_f_pass(const Dev<Real>& d, const RunArgs& a, int flags, long long stp,
                                            Acc<Real>& acc)
 {
 #pragma unroll
     for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
-    const float dmax = f_pass_block<Real, UNI, BONDS>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
+    const float dmax = f_pass_block<Real, UNI, BONDS, TH>(d, stab<Real>(), a, s_ls.pc, s_ls.ac, flags, stp, acc,
                                                       uni_params(a, Real(0))[0], uni_params(a, Real(0))[1], s_blk);
     if (flags & F_OPENING) warp_max_disp(dmax);
 }
@@ -1525,18 +1528,17 @@ __device__ void run_open_pass(const Dev<Real>& d, const RunArgs& a, long long st
     warp_max_disp(dmax);
 }
 
-// Deterministic reduction of one force pass's block partials: block q sums
-// quantity q over all blocks in a fixed order.
+// Deterministic reduction of the block partials of the sampled step: block q
+// sums quantity q over all blocks in a fixed order.
 template <typename Real>
-__device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
+__device__ void run_reduce_thermo(const Dev<Real>& d)
 {
     const int G = g_size(), nwp = (G + 31) / 32;
     const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = g_rank(); q < kNQA; q += G) {  // block-uniform loop
         if (w < nwp) {
-            const double* src = d.partials + (size_t)par * a.max_blocks * kNQ + q;
             const int b = threadIdx.x;
-            double v = b < G ? src[(size_t)b * kNQ] : 0.0;
+            double v = b < G ? d.partials[(size_t)b * kNQ + q] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lw == 0) s_red[w] = v;
@@ -1554,98 +1556,35 @@ __device__ void run_reduce_thermo(const Dev<Real>& d, const RunArgs& a, int par)
 // The same reduction for a group of fewer than kNQA blocks (batched runs):
 // rank 0 alone, warp q summing quantity q over the group's blocks in order.
 template <typename Real>
-__device__ __forceinline__ void reduce_small(const Dev<Real>& d, const RunArgs& a, int par)
+__device__ __forceinline__ void reduce_small(const Dev<Real>& d)
 {
     if (g_rank() != 0) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (w < kNQA) {
-        double v = lane < g_size() ? d.partials[((size_t)par * a.max_blocks + lane) * kNQ + w] : 0.0;
+        double v = lane < g_size() ? d.partials[(size_t)lane * kNQ + w] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) d.ctl->thermo[w] = v;
     }
 }
 
-// The same reduction in two halves, kept off the blocks' critical path: at a
-// force-pass barrier block q (< kNQA) starts asynchronous copies of quantity
-// q of every block's partials of the previous pass into s_rbuf; the copies are
-// waited for before the block's next barrier arrival (so the buffer may be
-// written again from that barrier on: the partials rotate over kParities
-// buffers, and the buffer read here is written next two passes later), and the
-// sum is formed in a fixed order after that arrival.
+// Writes the block's partials of the sampled step's thermo terms (energies,
+// virial, bond count, kinetic energy) from the threads' accumulators (or, for
+// a resident step, from the per-warp sums s_wpart it left).  Every call is
+// followed by a grid barrier, so the partials are complete for the reduction
+// at the end of the launch.  Only the last step of a launch is sampled: its
+// values are the ones a launch reports, and the other steps skip the terms.
 template <typename Real>
-__device__ __forceinline__ void reduce_issue(const Dev<Real>& d, const RunArgs& a, int par)
+__device__ __forceinline__ void thermo_partials(const Dev<Real>& d, const Acc<Real>& acc, Real* stage,
+                                                bool folded)
 {
-    const int b = threadIdx.x;
-    if (b < g_size())
-        cp_async(&s_rbuf[b], d.partials + ((size_t)par * a.max_blocks + b) * kNQ + g_rank(), 8);
-    cp_async_commit();
-}
-
-template <typename Real>
-__device__ __forceinline__ void reduce_finish(const Dev<Real>& d)
-{
-    const int G = g_size(), nwp = (G + 31) / 32;
-    const int lw = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w < nwp) {
-        double v = threadIdx.x < (unsigned)G ? s_rbuf[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lw == 0) s_red[w] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < nwp; k++) t += s_red[k];
-        d.ctl->thermo[g_rank()] = t;
-        s_ls.red_pending = 0;
-    }
-}
-
-// The barrier that ends a force pass.  After arriving (and publishing the
-// block's displacement maximum when the pass drifted), while the other blocks
-// finish, the block completes a reduction still pending from the previous
-// barrier, sums its thermo accumulators of this pass into its partials (stage:
-// kNQA x blockDim values of free shared memory), and the blocks that own a
-// quantity start the reduction of the previous pass's partials: every block
-// wrote those before arriving at the barrier that followed that pass, which
-// this block has passed.
-template <typename Real>
-__device__ __forceinline__ bool f_barrier(const Dev<Real>& d, const RunArgs& a, const Acc<Real>& acc,
-                                          int par, unsigned* pub_dst, int where, Real* stage,
-                                          bool folded = false)
-{
-    BarState bs;
-    bs.target = s_ls.bar_target;
-    bar_arrive(d.ctl, bs, pub_dst, &s_ls.dmax_bits);
-    const int had = s_ls.have_thermo, prev = s_ls.parity;
-    if (s_ls.red_pending) {
-        cp_async_wait_all();  // each thread's own copy into s_rbuf
-        reduce_finish(d);
-    }
-    // folded: the pass already summed its terms over each warp (s_wpart)
-    double* out = d.partials + ((size_t)par * a.max_blocks + g_rank()) * kNQ;
+    double* out = d.partials + (size_t)g_rank() * kNQ;
     if (folded)
         block_sums_from_warps(s_blk, out);
     else
         block_sums(acc.q, stage, s_blk, out);
-    // groups of at least kNQA blocks: one quantity per block, asynchronously;
-    // smaller groups reduce every quantity here
-    const bool red = had && (!kBatched || g_size() >= kNQA) && g_rank() < kNQA;
-    if (red) reduce_issue(d, a, prev);
-    if (kBatched && had && g_size() < kNQA) reduce_small(d, a, prev);
-    if (threadIdx.x == 0) {  // every thread read the old values before block_sums' barriers
-        s_ls.bar_target = bs.target;
-        s_ls.parity = par;
-        s_ls.have_thermo = 1;
-        if (red) s_ls.red_pending = 1;
-    }
-    return bar_wait(d.ctl, bs, a.timeout_ns, where, &s_ls.ok);
+    if (threadIdx.x == 0) s_ls.have_thermo = 1;
 }
-
-// The partials buffer of the next pass: the one after the last pass's, in
-// rotation (any two passes in a row, and the one between, differ).
-__device__ __forceinline__ int next_parity() { return s_ls.parity == kParities - 1 ? 0 : s_ls.parity + 1; }
 
 __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
 {
@@ -2058,10 +1997,10 @@ __device__ __forceinline__ float r_row_s(const Dev<float>& d, const PairP<float>
 
 // One resident step: S of the own particles and the reactive halo, the pair
 // forces of the own rows (entry order: reactive, then the others), the
-// integrator.  The thermo terms are left summed per warp in s_wpart (the
-// step's barrier completes the block sums).  Returns the thread's squared
-// drift displacement.
-template <bool UNI>
+// integrator.  TH (the sampled step): the thermo terms are left summed per
+// warp in s_wpart (thermo_partials completes the block sums).  Returns the
+// thread's squared drift displacement.
+template <bool UNI, bool TH>
 __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long long step, Acc<float>& acc)
 {
     typedef RStage RS;
@@ -2085,8 +2024,9 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         lS[lid] = r_row_s<UNI>(d, tab, ps, lpos, RS::sent() + dsc.x, (int)((unsigned)dsc.y >> 16), lpos[lid]);
     }
     __syncthreads();
+    if (TH)
 #pragma unroll
-    for (int q = 0; q < kNQA; q++) acc.q[q] = 0.0f;
+        for (int q = 0; q < kNQA; q++) acc.q[q] = 0.0f;
     float dmax = 0.0f, kin = 0.0f;
     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
     int4 pi = make_int4(0, 0, 0, 0);
@@ -2103,7 +2043,7 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         for (int k = 0; k < nr; k++) {
             const int j = er[32 * k];
             float ex, ey, ez;
-            entry_force<float, UNI, true>(d, tab, pi, lpos[j], Si, lS[j], ps, acc, ex, ey, ez);
+            entry_force<float, UNI, true, TH>(d, tab, pi, lpos[j], Si, lS[j], ps, acc, ex, ey, ez);
             fx = __fadd_rn(fx, ex);
             fy = __fadd_rn(fy, ey);
             fz = __fadd_rn(fz, ez);
@@ -2112,7 +2052,7 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         for (int k = 0; k < nw; k++) {
             const int j = ew[32 * k];
             float ex, ey, ez;
-            entry_force<float, UNI, false>(d, tab, pi, lpos[j], 0.0f, 0.0f, pw, acc, ex, ey, ez);
+            entry_force<float, UNI, false, TH>(d, tab, pi, lpos[j], 0.0f, 0.0f, pw, acc, ex, ey, ez);
             fx = __fadd_rn(fx, ex);
             fy = __fadd_rn(fy, ey);
             fz = __fadd_rn(fz, ez);
@@ -2121,14 +2061,16 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
     // the pair terms go to the warp partials now, so that the accumulators are
     // not live through the integrator (the kinetic term follows it)
     const bool rows = (t & ~31) < P;  // the warp holds rows (the same in all its lanes)
-    if (rows) {
+    if (TH) {
+        if (rows) {
 #pragma unroll
-        for (int q = 0; q < kNQA; q++)
-            if (q != Q_K) warp_part(acc.q[q], q);
-    } else if ((t & 31) == 0) {
+            for (int q = 0; q < kNQA; q++)
+                if (q != Q_K) warp_part(acc.q[q], q);
+        } else if ((t & 31) == 0) {
 #pragma unroll
-        for (int q = 0; q < kNQA; q++)
-            if (q != Q_K) s_wpart[q][t >> 5] = 0.0f;
+            for (int q = 0; q < kNQA; q++)
+                if (q != Q_K) s_wpart[q][t >> 5] = 0.0f;
+        }
     }
     int4 np = make_int4(0, 0, 0, 0);
     if (t < P) {
@@ -2151,10 +2093,12 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         }
         RS::vel()[t] = v;
     }
-    if (rows)
-        warp_part(kin, Q_K);
-    else if ((t & 31) == 0)
-        s_wpart[Q_K][t >> 5] = 0.0f;
+    if (TH) {
+        if (rows)
+            warp_part(kin, Q_K);
+        else if ((t & 31) == 0)
+            s_wpart[Q_K][t >> 5] = 0.0f;
+    }
     __syncthreads();  // every row has read the old snapshots
     if (t < P && (flags & F_OPENING)) lpos[lid] = np;
     if (t == 0) {
@@ -2215,13 +2159,11 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                        (ctl->list_chunk != (int)blockDim.x);
         s_ls.remaining = a.nsteps;
         s_ls.done = 0;
-        s_ls.parity = 0;
         s_ls.have_thermo = 0;
         s_ls.rc = 0;
         s_ls.disp = (float)ctl->disp;
         s_ls.dmax_bits = 0u;
         s_ls.own_ok = 0;
-        s_ls.red_pending = 0;
         s_ls.r_try = (kRes && a.resident && single_chunk(d)) ? 1 : 0;
         s_ls.r_valid = 0;
         s_ls.r_gathered = 0;
@@ -2260,11 +2202,11 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             if (s_ls.rc == 0) {
                 run_s_pass<Real, UNI>(d, a);
                 if (!grid_barrier(ctl, a.timeout_ns, 10)) return false;
-                const int par = next_parity();
                 Acc<Real> acc;
-                run_f_pass<Real, UNI, BONDS>(d, a, F_STORE, s_ls.step, acc);
+                run_f_pass<Real, UNI, BONDS, true>(d, a, F_STORE, s_ls.step, acc);
                 if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
-                if (!f_barrier(d, a, acc, par, nullptr, 11, Stage<Real>::w())) return false;
+                thermo_partials(d, acc, Stage<Real>::w(), false);
+                if (!grid_barrier(ctl, a.timeout_ns, 11)) return false;
             }
         }
         if (s_ls.rc == 0 && s_ls.remaining > 0 && s_ls.state == 0) {
@@ -2281,9 +2223,21 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             if (!grid_barrier(ctl, a.timeout_ns, 13, &ctl->dmax2[stp & 1])) return false;
             add_disp(ctl, stp);
         }
+        [[maybe_unused]] unsigned dm_pending = 0u;  // thread 0: the displacement maximum read after a resident barrier
         while (s_ls.rc == 0 && s_ls.state == 2) {
             const long long stp = s_ls.step;
             if (threadIdx.x == 0 && g_rank() == 0) ctl->dmax2[(stp + 1) & 1] = 0u;
+#if !SWP_BATCHED
+            if constexpr (kRes) {
+                if (s_ls.r_gathered) {
+                    // the halo copies and the displacement read issued after the
+                    // last barrier were in flight together until here
+                    cp_async_wait_all();
+                    if (threadIdx.x == 0) s_ls.disp += sqrtf(__uint_as_float(dm_pending));
+                    __syncthreads();
+                }
+            }
+#endif
             if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
                 // a resident gather issued for this step lands in memory the rebuild reuses
                 cp_async_wait_all();
@@ -2304,17 +2258,19 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 if (rc) break;
             }
             const bool more = s_ls.remaining > 1;
-            const int par = next_parity();
+            // the thermo terms are summed on the launch's last step only: it is
+            // the step a launch reports them for
+            const bool th = !more;
             const int flags = F_CLOSING | (more ? F_OPENING : F_STORE);
             Acc<Real> acc;
-            Real* stage = Stage<Real>::w();
             bool resident = false;
 #if !SWP_BATCHED
             if constexpr (kRes) {
                 if (s_ls.r_try)
                     if (!r_enter(d, a)) return false;
                 if (s_ls.r_valid) {
-                    const float dmax = r_step<UNI>(d, a, flags, stp + 1, acc);
+                    const float dmax = th ? r_step<UNI, true>(d, a, flags, stp + 1, acc)
+                                          : r_step<UNI, false>(d, a, flags, stp + 1, acc);
                     if (more) warp_max_disp(dmax);
                     resident = true;
                 }
@@ -2322,25 +2278,20 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 #endif
             if (!resident) {
                 run_s_pass<Real, UNI>(d, a);
-                const bool fin = s_ls.red_pending;
-                if (fin) cp_async_wait_all();
-                {
-                    BarState bs;
-                    bs.target = s_ls.bar_target;
-                    bar_arrive(ctl, bs);
-                    if (fin) reduce_finish(d);
-                    if (threadIdx.x == 0) s_ls.bar_target = bs.target;
-                    if (!bar_wait(ctl, bs, a.timeout_ns, 20, &s_ls.ok)) return false;
-                }
-                run_f_pass<Real, UNI, BONDS>(d, a, flags, stp + 1, acc);
+                if (!grid_barrier(ctl, a.timeout_ns, 20)) return false;
+                if (th)
+                    run_f_pass<Real, UNI, BONDS, true>(d, a, flags, stp + 1, acc);
+                else
+                    run_f_pass<Real, UNI, BONDS, false>(d, a, flags, stp + 1, acc);
             }
             if (threadIdx.x == 0) {  // every thread read `remaining` before the pass's barriers
                 s_ls.step = stp + 1;
                 s_ls.remaining--;
                 s_ls.done++;
             }
-            if (!f_barrier(d, a, acc, par, more ? &ctl->dmax2[(stp + 1) & 1] : nullptr, 21, stage, resident))
-                return false;
+            if (th) thermo_partials(d, acc, Stage<Real>::w(), resident);
+            unsigned* pub = more ? &ctl->dmax2[(stp + 1) & 1] : nullptr;
+            if (!grid_barrier(ctl, a.timeout_ns, 21, pub)) return false;
             if (more) {
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
                 __syncthreads();
@@ -2348,15 +2299,12 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 #if !SWP_BATCHED
                 if constexpr (kRes) {
                     if (s_ls.r_valid) {
-                        // the displacement read is in flight while the next
-                        // step's copies are issued
-                        unsigned dm = 0u;
-                        if (threadIdx.x == 0) dm = (unsigned)ld_relaxed((const int*)&ctl->dmax2[(stp + 1) & 1]);
+                        // the displacement read and the next step's copies
+                        // overlap; the read is used after the copies land (top
+                        // of the loop)
+                        if (threadIdx.x == 0) dm_pending = (unsigned)ld_relaxed((const int*)pub);
                         r_gather(d, s_ls.pc);
-                        if (threadIdx.x == 0) {
-                            s_ls.r_gathered = 1;
-                            s_ls.disp += sqrtf(__uint_as_float(dm));
-                        }
+                        if (threadIdx.x == 0) s_ls.r_gathered = 1;
                         __syncthreads();
                         gathered = true;
                     }
@@ -2369,18 +2317,18 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             }
         }
     }
-    cp_async_wait_all();  // a reduction started at the last barrier is not needed
+    cp_async_wait_all();  // copies issued for a step that did not come
 #if !SWP_BATCHED
     if constexpr (kRes)
         if (s_ls.r_valid) r_flush(d, s_ls.ac);
 #endif
     if (s_ls.have_thermo) {
-        // the last pass's partials were written after its barrier's arrival
-        if (!grid_barrier(ctl, a.timeout_ns, 30)) return false;
+        // the partials were written before the arrival at the barrier that
+        // followed their pass, which every block has passed
         if (kBatched && g_size() < kNQA)
-            reduce_small(d, a, s_ls.parity);
+            reduce_small(d);
         else
-            run_reduce_thermo(d, a, s_ls.parity);
+            run_reduce_thermo(d);
     }
     if (g_rank() == 0 && threadIdx.x == 0) {
         ctl->state = s_ls.state;
