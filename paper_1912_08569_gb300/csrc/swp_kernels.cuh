@@ -1275,7 +1275,7 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         const int e_beg = SM::info()[0].x;
         const int e_rend = SM::info()[P - 1].x + SM::info()[P - 1].y;
         const int e_end = SM::info()[P - 1].z + SM::info()[P - 1].w;
-        Real fx = 0, fy = 0, fz = 0;
+        Real fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;  // reactive and other entries' sums
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
             for (int e = wb + t; e < we; e += blockDim.x) {
@@ -1298,10 +1298,15 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
             if (t < P) {
                 const int4 inf = SM::info()[t];
                 sum_run(SM::w4(), wb, max(inf.x, wb), min(inf.x + inf.y, we), fx, fy, fz);
-                sum_run(SM::w4(), wb, max(inf.z, wb), min(inf.z + inf.w, we), fx, fy, fz);
+                sum_run(SM::w4(), wb, max(inf.z, wb), min(inf.z + inf.w, we), gx, gy, gz);
             }
             __syncthreads();
         }
+        // the force: the reactive entries' sum plus the others' (the order of
+        // the resident step, so both paths give the same bits)
+        fx = add_rn(fx, gx);
+        fy = add_rn(fy, gy);
+        fz = add_rn(fz, gz);
         // harmonic bonds (vitrimer chains): F_i = k (r - r0) (x_j - x_i) / r, half
         // of the energy and virial to each end (added to the two-body terms)
         if (BONDS && d.has_bonds && t < P) {  // BONDS: some system of the launch has bonds
@@ -1416,7 +1421,7 @@ struct LoopState {
 };
 
 static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
-static __shared__ double s_red[kNQ * 32];
+static __shared__ double s_red[32];
 static __shared__ double s_blk[kNQ];  // the block's FP64 running thermo sums of the current pass
 static __shared__ int s_int[64];
 static __shared__ LoopState s_ls;
@@ -1604,8 +1609,8 @@ __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
 // reactive partner of those that are reactive partners of an own particle --
 // the own rows, and the reactive rows of that first halo shell (each the
 // owner's row, in the owner's order), all with partners as 16-bit local
-// indices.  A step then copies the halo's new snapshots in once (one bulk
-// asynchronous copy), forms S for the own particles and for the reactive halo
+// indices.  A step then copies the halo's new snapshots in once (one
+// asynchronous 16-byte copy each), forms S for the own particles and for the reactive halo
 // from shared memory (a halo row is its owner's row, evaluated in the same
 // order with the same operations, so both blocks hold bit-identical S), and
 // the pair forces and the integrator with no further global gather: one grid
@@ -1626,11 +1631,13 @@ struct RStage {
     static constexpr size_t O_SENT = O_HSLOT + (size_t)kL * 4;      // [kES] u16 local partners of the rows of S
     static constexpr size_t O_FENT = O_SENT + (size_t)kES * 2;      // [kEF] u16 local partners of the own rows
     static constexpr size_t O_SDESC = O_FENT + (size_t)kEF * 2;     // [kL] int2 row of S: (lane's first entry, centre | n << 16)
-    static constexpr size_t O_FDESC = O_SDESC + (size_t)kL * 8;     // [kBlock] int4 own row: (first reactive entry,
-                                                                    // first other entry, nr | nw << 16, centre)
+    static constexpr size_t O_FDESC = O_SDESC + (size_t)kL * 8;     // [kBlock] int4 by thread: (first entry of its
+                                                                    // reactive row, of its other row, nr | nw << 16,
+                                                                    // centre of each (16 bits each, 0xffff: none))
+    static constexpr size_t O_FW = O_FDESC + (size_t)kBlock * 16;   // [3][kBlock] float other-row forces by centre
     // the own particles' state, by row position, kept here between list builds
     // (global memory is brought up to date by r_flush)
-    static constexpr size_t O_VEL = O_FDESC + (size_t)kBlock * 16;  // [kBlock] float4 velocities
+    static constexpr size_t O_VEL = O_FW + (size_t)kBlock * 12;     // [kBlock] float4 velocities
     static constexpr size_t O_XQ = O_VEL + (size_t)kBlock * 16;     // [3 kBlock] fixed-point positions
     static constexpr size_t O_IMG = O_XQ + (size_t)kBlock * 24;     // [3 kBlock] image counts
     static constexpr size_t kBytes = O_IMG + (size_t)kBlock * 12;
@@ -1643,6 +1650,7 @@ struct RStage {
     static_assert(B_END <= kBytes, "build scratch fits the own-state area");
     static_assert(kES <= 65536 && kEF <= 65536 && kL <= 65536, "16-bit local indices and offsets");
     static_assert(kBlock % 32 == 0 && kBlock / 32 <= 32, "whole warps, at most 32");
+    static_assert(kBlock >= 256 && kEF >= kBlock / 32 * 256, "force-row sort scratch (r_rank1_desc) in O_FENT");
 
     static __device__ __forceinline__ int4* lpos() { return (int4*)(g_dyn + O_LPOS); }
     static __device__ __forceinline__ float* lS() { return (float*)(g_dyn + O_LS); }
@@ -1651,6 +1659,7 @@ struct RStage {
     static __device__ __forceinline__ unsigned short* fent() { return (unsigned short*)(g_dyn + O_FENT); }
     static __device__ __forceinline__ int2* sdesc() { return (int2*)(g_dyn + O_SDESC); }
     static __device__ __forceinline__ int4* fdesc() { return (int4*)(g_dyn + O_FDESC); }
+    static __device__ __forceinline__ float* fw() { return (float*)(g_dyn + O_FW); }
     static __device__ __forceinline__ float4* vel() { return (float4*)(g_dyn + O_VEL); }
     static __device__ __forceinline__ long long* xq() { return (long long*)(g_dyn + O_XQ); }
     static __device__ __forceinline__ int* img() { return (int*)(g_dyn + O_IMG); }
@@ -1728,6 +1737,41 @@ __device__ void r_sort_desc(const int (&key)[R], int (&pos)[R], int* hist)
             if (key[r] == c) pos[r] = base + off++;
         base += tot;
     }
+}
+
+// Stable counting sort, largest key first, of one item per thread (key in
+// [0, 255], -1: no item): returns the item's rank.  Equal keys keep the thread
+// order.  wh: scratch of blockDim / 32 x 256 u16 counts; hist: 256 ints;
+// blockDim >= 256.
+static __device__ int r_rank1_desc(int key, unsigned short* wh, int* hist)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, NW = blockDim.x >> 5;
+    __syncthreads();  // a previous call's readers are done with wh and hist
+    for (int k = t; k < NW * 256; k += blockDim.x) wh[k] = 0;
+    __syncthreads();
+    // the warp's lanes with this key, and how many come before this lane
+    const unsigned m = __match_any_sync(0xffffffffu, key);
+    const int before = __popc(m & ((1u << lane) - 1u));
+    if (key >= 0 && before == 0) wh[warp * 256 + key] = (unsigned short)__popc(m);
+    __syncthreads();
+    // per key: the counts of the warps before each warp, and the key's total
+    if (t < 256) {
+        int run = 0;
+        for (int w = 0; w < NW; w++) {
+            const int c = wh[w * 256 + t];
+            wh[w * 256 + t] = (unsigned short)run;
+            run += c;
+        }
+        hist[t] = run;
+    }
+    __syncthreads();
+    // keys in descending order: the first rank of key b is the count above it
+    const int b = 255 - t;
+    int tot;
+    const int ex = block_excl_scan(t < 256 ? hist[b] : 0, s_int, &tot);
+    if (t < 256) hist[b] = ex;  // every thread read hist before the scan's barriers
+    __syncthreads();
+    return key >= 0 ? hist[key] + wh[warp * 256 + key] + before : 0;
 }
 
 // Lays out warp blocks: rows at positions s (thread s % B, round s / B) with
@@ -1840,8 +1884,11 @@ static __device__ int r_localize(const Dev<float>& d, int pc, int ac)
     // 5. rows of S (the own rows and the reactive first shell's), longest
     // first, dealt out over the threads as a snake: rank s goes to round
     // s / B, to thread s % B in even rounds and B - 1 - s % B in odd ones, so
-    // that a thread's second row is short when its first is long.  Rows of
-    // the force pass: the own rows, longest (reactive + other) first.
+    // that a thread's second row is short when its first is long.  The force
+    // pass runs two loops per thread, over a reactive row and over another
+    // particle's other (purely two-body) row: reactive rows longest first
+    // from warp 0, other rows longest first from the last warp, so that the
+    // rows of a warp are alike in each loop and the warps' totals even out.
     const int NS = P + Hr;
     const int rounds = (NS + B - 1) / B;
     int4 inf = make_int4(0, 0, 0, 0);
@@ -1865,9 +1912,12 @@ static __device__ int r_localize(const Dev<float>& d, int pc, int ac)
         }
     }
     r_sort_desc<RR + 1>(skey, spos, hist);
-    int fkey[1] = {t < P ? min(inf.y + inf.w, 255) : -1}, fpos[1] = {0};
-    r_sort_desc<1>(fkey, fpos, hist);
+    const int W32 = (P + 31) & ~31;
+    const int rpos = r_rank1_desc(t < P ? inf.y : -1, RS::fent(), hist);
+    const int wrank = r_rank1_desc(t < P ? inf.w : -1, RS::fent(), hist);
+    const int wpos = W32 - 32 - (wrank & ~31) + (wrank & 31);  // rank chunk c -> warp W32/32 - 1 - c
     for (int q = t; q < rounds * B; q += B) RS::sdesc()[q] = make_int2(0, -1);  // no row here
+    if (t < W32) RS::fdesc()[t] = make_int4(0, 0, 0, -1);  // no rows; centres 0xffff
     __syncthreads();
     // what each position needs: the centre and the row (start, count)
 #pragma unroll
@@ -1884,7 +1934,17 @@ static __device__ int r_localize(const Dev<float>& d, int pc, int ac)
             RS::sdesc()[q] = make_int2(hrow[r - 1], hcnt[r - 1]);
         }
     }
-    if (t < P) RS::fdesc()[fpos[0]] = make_int4(inf.x, inf.z, inf.y | (inf.w << 16), t);
+    if (t < P) {
+        // 16-bit fields: (z, w) = (nr, nw, reactive centre, other centre)
+        int4* fr = &RS::fdesc()[rpos];
+        int4* fo = &RS::fdesc()[wpos];
+        fr->x = inf.x;
+        fo->y = inf.z;
+        ((unsigned short*)&fr->z)[0] = (unsigned short)inf.y;
+        ((unsigned short*)&fo->z)[1] = (unsigned short)inf.w;
+        ((unsigned short*)&fr->w)[0] = (unsigned short)t;
+        ((unsigned short*)&fo->w)[1] = (unsigned short)t;
+    }
     if (__syncthreads_or(fail)) return 0;
     // 6. warp-major layouts: the rows of S; the own rows' reactive parts, then
     // their other parts
@@ -1895,8 +1955,8 @@ static __device__ int r_localize(const Dev<float>& d, int pc, int ac)
         n[r] = r < rounds ? max(RS::sdesc()[q].y, 0) : 0;
     }
     const int ES = r_warp_layout<RR>(n, first, wl);
-    const int4 fd = t < P ? RS::fdesc()[t] : make_int4(0, 0, 0, 0);
-    int nrc[1] = {fd.z & 0xffff}, nwc[1] = {fd.z >> 16}, rfirst[1], wfirst[1];
+    const int4 fd = t < W32 ? RS::fdesc()[t] : make_int4(0, 0, 0, -1);
+    int nrc[1] = {fd.z & 0xffff}, nwc[1] = {(int)((unsigned)fd.z >> 16)}, rfirst[1], wfirst[1];
     const int ER = r_warp_layout<1>(nrc, rfirst, wl);
     const int EW = r_warp_layout<1>(nwc, wfirst, wl);
     if (ES > RS::kES || ER + EW > RS::kEF) return 0;  // the same in every thread
@@ -1915,24 +1975,24 @@ static __device__ int r_localize(const Dev<float>& d, int pc, int ac)
             }
         }
     }
-    if (t < P) {
+    if (t < W32) {
         unsigned short* fe = RS::fent();
         for (int m = 0; m < nrc[0]; m++)
             fe[rfirst[0] + 32 * m] = (unsigned short)r_lid(key, val, d.ent_j[fd.x + m], b0, b1, P, fail);
         for (int m = 0; m < nwc[0]; m++)
             fe[ER + wfirst[0] + 32 * m] = (unsigned short)r_lid(key, val, d.ent_j[fd.y + m], b0, b1, P, fail);
         RS::fdesc()[t] = make_int4(rfirst[0], ER + wfirst[0], fd.z, fd.w);
-        lpos[t] = d.pos[pc][b0 + t];  // own snapshots by local index
     }
+    if (t < P) lpos[t] = d.pos[pc][b0 + t];  // own snapshots by local index
     if (t == 0) {
         s_ls.r_np = P;
         s_ls.r_nh = H;
         s_ls.r_nhr = Hr;
     }
     const int ok = __syncthreads_or(fail) ? 0 : 1;
-    // 8. the own particles' state by force-row position (over the table, now unused)
+    // 8. the own particles' state by reactive-row position (over the table, now unused)
     if (ok && t < P) {
-        const int i = b0 + RS::fdesc()[t].w, n = d.n;
+        const int i = b0 + (RS::fdesc()[t].w & 0xffff), n = d.n;
         RS::vel()[t] = d.vel[ac][i];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -1953,7 +2013,7 @@ __device__ __forceinline__ void r_flush(const Dev<float>& d, int ac)
     if (t < s_ls.r_np) {
         int b0, b1;
         block_range(d, b0, b1);
-        const int i = b0 + RS::fdesc()[t].w;
+        const int i = b0 + (RS::fdesc()[t].w & 0xffff);
         d.vel[ac][i] = RS::vel()[t];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -2031,31 +2091,45 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
     float fx = 0.0f, fy = 0.0f, fz = 0.0f;
     int4 pi = make_int4(0, 0, 0, 0);
     int lid = 0;
-    if (t < P) {
+    float* fw = RS::fw();
+    if (t < ((P + 31) & ~31)) {
         const int4 fd = RS::fdesc()[t];
-        lid = fd.w;
-        const int nr = fd.z & 0xffff, nw = fd.z >> 16;
-        const unsigned short* er = RS::fent() + fd.x;
-        const unsigned short* ew = RS::fent() + fd.y;
-        pi = lpos[lid];
-        const float Si = lS[lid];
+        const int nr = fd.z & 0xffff, nw = (int)((unsigned)fd.z >> 16);
+        const int cw = (int)((unsigned)fd.w >> 16);
+        lid = fd.w & 0xffff;
+        if (cw != 0xffff) {
+            // the other (purely two-body) row of particle cw: its sum goes to
+            // fw, for the thread that integrates cw
+            const unsigned short* ew = RS::fent() + fd.y;
+            const int4 pc_ = lpos[cw];
+            float gx = 0.0f, gy = 0.0f, gz = 0.0f;
 #pragma unroll 2
-        for (int k = 0; k < nr; k++) {
-            const int j = er[32 * k];
-            float ex, ey, ez;
-            entry_force<float, UNI, true, TH>(d, tab, pi, lpos[j], Si, lS[j], ps, acc, ex, ey, ez);
-            fx = __fadd_rn(fx, ex);
-            fy = __fadd_rn(fy, ey);
-            fz = __fadd_rn(fz, ez);
+            for (int k = 0; k < nw; k++) {
+                const int j = ew[32 * k];
+                float ex, ey, ez;
+                entry_force<float, UNI, false, TH>(d, tab, pc_, lpos[j], 0.0f, 0.0f, pw, acc, ex, ey, ez);
+                gx = __fadd_rn(gx, ex);
+                gy = __fadd_rn(gy, ey);
+                gz = __fadd_rn(gz, ez);
+            }
+            fw[cw] = gx;
+            fw[kBlock + cw] = gy;
+            fw[2 * kBlock + cw] = gz;
         }
+        if (t < P) {
+            // the reactive row of particle lid
+            const unsigned short* er = RS::fent() + fd.x;
+            pi = lpos[lid];
+            const float Si = lS[lid];
 #pragma unroll 2
-        for (int k = 0; k < nw; k++) {
-            const int j = ew[32 * k];
-            float ex, ey, ez;
-            entry_force<float, UNI, false, TH>(d, tab, pi, lpos[j], 0.0f, 0.0f, pw, acc, ex, ey, ez);
-            fx = __fadd_rn(fx, ex);
-            fy = __fadd_rn(fy, ey);
-            fz = __fadd_rn(fz, ez);
+            for (int k = 0; k < nr; k++) {
+                const int j = er[32 * k];
+                float ex, ey, ez;
+                entry_force<float, UNI, true, TH>(d, tab, pi, lpos[j], Si, lS[j], ps, acc, ex, ey, ez);
+                fx = __fadd_rn(fx, ex);
+                fy = __fadd_rn(fy, ey);
+                fz = __fadd_rn(fz, ez);
+            }
         }
     }
     // the pair terms go to the warp partials now, so that the accumulators are
@@ -2072,9 +2146,13 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
                 if (q != Q_K) s_wpart[q][t >> 5] = 0.0f;
         }
     }
-    int4 np = make_int4(0, 0, 0, 0);
+    __syncthreads();  // every row has read the old snapshots, and fw is complete
     if (t < P) {
         const int i = b0 + lid;
+        // the force: the reactive row's sum plus the other row's
+        fx = __fadd_rn(fx, fw[lid]);
+        fy = __fadd_rn(fy, fw[kBlock + lid]);
+        fz = __fadd_rn(fz, fw[2 * kBlock + lid]);
         if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) atomicOr(&d.ctl->status, kStatusNonfinite);
         if (flags & F_STORE) d.force[i] = make_float4(fx, fy, fz, 0.0f);
         float4 v = RS::vel()[t];
@@ -2082,6 +2160,7 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         int w[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) q[c] = RS::xq()[3 * t + c];
+        int4 np = make_int4(0, 0, 0, 0);
         dmax = advance_particle(d, a, fx, fy, fz, flags, step, pi.w, v, q, w, kin, np);
         if (flags & F_OPENING) {
 #pragma unroll
@@ -2090,6 +2169,7 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
                 RS::img()[3 * t + c] += w[c];
             }
             d.pos[pc ^ 1][i] = np;  // the other blocks' halos read it
+            lpos[lid] = np;
         }
         RS::vel()[t] = v;
     }
@@ -2099,8 +2179,6 @@ __device__ float r_step(const Dev<float>& d, const RunArgs& a, int flags, long l
         else if ((t & 31) == 0)
             s_wpart[Q_K][t >> 5] = 0.0f;
     }
-    __syncthreads();  // every row has read the old snapshots
-    if (t < P && (flags & F_OPENING)) lpos[lid] = np;
     if (t == 0) {
         s_ls.r_gathered = 0;
         s_ls.r_steps++;
