@@ -7,9 +7,11 @@ separation 0.9, A-B swap pair (eps = sigma = 1, n = 10, r_cut = 1.5, lambda 1
 by default), A-A and B-B WCA (sigma = 1), BAOAB Langevin at kT = 0.05,
 gamma = 1, dt = 0.001, skin 0.3, list rebuilt on the device on displacement.
 One benchmark step = one launch of the persistent step kernel advancing
-``--md-steps`` (default 1,000) time steps with energy and virial every step;
-the inputs stay resident in HBM, and L2 is flushed (a 512 MB write) between
-timed launches.
+``--md-steps`` (default 1,000) time steps, with the energies, virial, kinetic
+energy and bond count of every ``--thermo-every`` th step (default: every
+step) written to the device thermo log and reduced into per-step records
+after the launch; the inputs stay resident in HBM, and L2 is flushed (a
+512 MB write) between timed launches.
 
 Other workloads (``--workload``): batch256 (256 independent systems in one
 launch), diff20k (force-matching gradient), vitrimer2m (2M-bead bonded
@@ -59,6 +61,8 @@ def _args():
     ap.add_argument("--bps", type=int, default=0)
     ap.add_argument("--no-resident", action="store_true",
                     help="forbid the resident mode (one barrier per step): the two-barrier step")
+    ap.add_argument("--thermo-every", type=int, default=1,
+                    help="thermo-log interval of the mix100k workload in steps (0: only each launch's last step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -119,6 +123,9 @@ def _config(a, n, world):
                         f"lambda={a.lam:g}, BAOAB kT=0.05 gamma=1 dt=0.001, skin 0.3",
             "n_particles": n, "md_steps_per_step": a.md_steps, "lambda": a.lam,
             "replicas": world, "l2": "flushed (512 MB write) between timed launches",
+            "thermo": (f"energies, virial, kinetic energy and bond count of every {a.thermo_every} step(s), "
+                       "logged on the device and reduced per step after each launch (in the timed region)"
+                       if a.thermo_every > 0 else "energies and virial of each launch's last step only"),
             "parallelism": f"replicas x{world}"}
 
 
@@ -403,6 +410,12 @@ def run_ours(a):
     stream = s.stream
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     dt, kT, gamma = wl["dt"], wl["kT"], wl["gamma"]
+    # the thermo log: one record per thermo_every steps of a launch
+    log_cap = a.md_steps // a.thermo_every if a.thermo_every > 0 else 0
+    if log_cap > 0:
+        s.set_thermo_log(a.thermo_every, log_cap)
+        log_rec = torch.empty((log_cap, 10), dtype=torch.float64, device=dev)
+        log_stp = torch.empty(log_cap, dtype=torch.int64, device=dev)
 
     # warm-up (grows the list if a rebuild overflows)
     for _ in range(a.warmup):
@@ -423,10 +436,15 @@ def run_ours(a):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             s.run(a.md_steps, dt, kT, gamma, sync=False)
             e1.record(stream)
-            evs.append((e0, e1))
+            if log_cap > 0:  # the launch's per-step records (waits for the launch, then one reduction kernel)
+                got = A.swp_thermo_log(s.ctx, log_rec, log_stp, log_cap)
+                assert got == log_cap, (got, log_cap)
+            e2.record(stream)
+            evs.append((e0, e1, e2))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     s.sync()  # raises if the device reported an error during the timed launches
@@ -434,8 +452,8 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    launch_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_ms = float(np.sum(launch_ms))
+    launch_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]  # the step kernel alone (roofline)
+    total_ms = float(np.sum([e0.elapsed_time(e2) for e0, _, e2 in evs]))  # with the log's reduction
     assert th1["step"] - th0["step"] == a.steps * a.md_steps, "timed launches did not complete"
     rebuilds = (th1["n_rebuilds"] - th0["n_rebuilds"]) / a.steps
     total_ms = max_over_ranks(total_ms, dev)
@@ -446,6 +464,10 @@ def run_ours(a):
     peak, peak_kind = _peaks()
     b_alg = algorithmic_bytes(n, a.md_steps, nn, nn_r, rebuilds)
     achieved = b_alg / (float(np.mean(launch_ms)) / 1e3) / 1e9
+    if log_cap > 0:  # the last launch's records: its steps, finite energies
+        steps_logged = log_stp.cpu().numpy()
+        assert np.array_equal(steps_logged, th1["step"] - a.md_steps + a.thermo_every * np.arange(1, log_cap + 1))
+        assert np.all(np.isfinite(log_rec.cpu().numpy()))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": _profile_traffic(n, a.md_steps),
             "peak_kind": peak_kind, "alg_bytes_per_launch": b_alg,
@@ -467,18 +489,25 @@ def run_ours(a):
         h2d = xh.numel() * 8 + vh.numel() * 8 + th_.numel() * 4 + mh.numel() * 8 + ih.numel() * 4
         ctx = s.ctx
         times = []
+        d2h = CTL_BYTES
+        if log_cap > 0:
+            log_host = torch.empty((log_cap, 10), dtype=torch.float64).pin_memory()
+            d2h += log_host.numel() * 8
         for k in range(a.warmup + a.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             A.swp_set_state(ctx, xh, vh, th_, mh, ih, A.SWP_HOST)
             A.swp_step_nvt(ctx, dt, kT, gamma, a.md_steps)
+            if log_cap > 0:  # every logged step's record to the host
+                A.swp_thermo_log(ctx, log_rec, log_stp, log_cap)
+                log_host.copy_(log_rec)
             rec = A.swp_read_thermo(ctx)
             el = time.perf_counter() - t0
             if k >= a.warmup:
                 times.append(el)
         e2e_ms = 1e3 * max_over_ranks(float(np.sum(times)), dev)
         e2e = {"value": job_throughput(world, n, a.md_steps, a.steps, e2e_ms), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": CTL_BYTES,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "last_U": float(rec.U2 + rec.U3)}
 
     cpu = None
@@ -494,7 +523,7 @@ def run_ours(a):
                "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": _config(a, n, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": a.steps, "clocks": clk, "wall_s_timed": t_wall,
+               "gpu_launches": a.steps * (2 if log_cap > 0 else 1), "clocks": clk, "wall_s_timed": t_wall,
                "kernel_digest": _kernel_digest(),
                "resident_steps_last_launch": th1["resident_steps"],
                "thermo_last": {"U2": th1["U2"], "U3": th1["U3"], "K": th1["K"],

@@ -51,7 +51,7 @@ extern "C" {
 #define SWP_API
 #endif
 
-#define SWP_ABI_VERSION 2
+#define SWP_ABI_VERSION 3
 
 /* Status codes. */
 #define SWP_OK 0
@@ -240,6 +240,33 @@ SWP_API int swp_param_grad(swp_ctx* ctx, int ti, int tj, double dU[3], double* d
  * f [n][3].  swp_read_state: x [n][3] wrapped into [0, L), v [n][3], img
  * [n][3]; any of them may be NULL.  Pointers of kind `where`. */
 SWP_API int swp_read_thermo(swp_ctx* ctx, swp_thermo* out);
+
+/* Thermo log: a record of the energies, virial, kinetic energy and bond count
+ * (the quantities of swp_read_thermo) of every step whose number is a
+ * multiple of `every`, written by the step kernel into a ring of `capacity`
+ * records that the caller provides.  A step kernel sums these terms only on
+ * the steps it logs and on the last step of each launch (the one
+ * swp_read_thermo reports); every = 0 (the default) turns the log off.
+ *
+ * swp_thermo_log_bytes: bytes of the ring for `capacity` records (0 if the
+ * capacity is not in [1, 2^31 - 1]).  swp_set_thermo_log: every >= 0; with
+ * every > 0, ring is a device buffer of this context's device, 256-byte
+ * aligned, of at least swp_thermo_log_bytes(ctx, capacity) bytes, which the
+ * library uses (does not own) until the log is set again or the context is
+ * destroyed.  It restarts the count of records, and so does swp_set_state.
+ * Errors: SWP_ERR_INVALID.
+ *
+ * swp_thermo_log: the newest min(written, capacity, max_records) records,
+ * oldest first, into rec_dev [max_records][10] doubles (U2, U3, K, W[6],
+ * n_bonds, each summed over the blocks as in swp_read_thermo) and step_dev
+ * [max_records] (the step numbers), both device pointers; *n_records (host)
+ * gets the count.  Synchronises the stream to read the count; the sums are
+ * formed by a kernel enqueued on it.  Errors: SWP_ERR_INVALID (no log set,
+ * null pointers), the latched errors of swp_sync. */
+SWP_API size_t swp_thermo_log_bytes(const swp_ctx* ctx, int64_t capacity);
+SWP_API int swp_set_thermo_log(swp_ctx* ctx, int every, int64_t capacity, void* ring, size_t ring_bytes);
+SWP_API int swp_thermo_log(swp_ctx* ctx, double* rec_dev, int64_t* step_dev, int64_t max_records,
+                           int64_t* n_records);
 SWP_API int swp_read_forces(swp_ctx* ctx, double* f, int where);
 SWP_API int swp_read_state(swp_ctx* ctx, double* x, double* v, int32_t* img, int where);
 
@@ -250,7 +277,7 @@ SWP_API int swp_read_state(swp_ctx* ctx, double* x, double* v, int32_t* img, int
 SWP_API int swp_read_nlist(swp_ctx* ctx, int32_t* rows_dev, int32_t* counts_dev, int width);
 
 /* Launch shape of the step kernel: resident blocks per SM (0: as many as
- * fit; the kernel uses 1024-thread blocks and most of an SM's shared memory,
+ * fit; the kernel uses 768-thread blocks and most of an SM's shared memory,
  * so one fits).  Changing it marks the list stale (its block partition
  * follows the grid). */
 SWP_API int swp_set_launch(swp_ctx* ctx, int blocks_per_sm);
@@ -270,7 +297,7 @@ SWP_API int swp_set_timeout(swp_ctx* ctx, int64_t ns);
 
 /* Resident mode of the FP32 step (enable: 1, the default; 0: off).  When a
  * run has one system in FP32 without bonds and every block of the step kernel
- * owns at most one sub-chunk of particles (n up to blockDim x grid, 155,648
+ * owns at most one sub-chunk of particles (n up to blockDim x grid, 116,736
  * on a 152-SM part), each block keeps in shared memory, between list builds,
  * its own rows and the reactive rows of its halo (the partners of its particles
  * that other blocks own) with partners as local indices; a step then copies

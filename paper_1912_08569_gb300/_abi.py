@@ -49,7 +49,7 @@ EXPORTS = (
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch", "swp_set_grid",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
     "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds", "swp_set_resident",
-    "swp_set_withhold_arrival",
+    "swp_set_withhold_arrival", "swp_thermo_log_bytes", "swp_set_thermo_log", "swp_thermo_log",
 )
 
 
@@ -116,6 +116,9 @@ def load_library(path: str = LIB_PATH):
         "swp_set_timeout": ([c_void_p, ctypes.c_int64], c_int),
         "swp_set_resident": ([c_void_p, c_int], c_int),
         "swp_set_withhold_arrival": ([c_void_p, c_int], c_int),
+        "swp_thermo_log_bytes": ([c_void_p, ctypes.c_int64], c_size_t),
+        "swp_set_thermo_log": ([c_void_p, c_int, ctypes.c_int64, c_void_p, c_size_t], c_int),
+        "swp_thermo_log": ([c_void_p, c_void_p, c_void_p, ctypes.c_int64, P(ctypes.c_int64)], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
         "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
@@ -268,6 +271,24 @@ def swp_set_resident(ctx, enable: int):
 
 def swp_set_withhold_arrival(ctx, on: int):
     return _check(ctx, load_library().swp_set_withhold_arrival(ctx, int(on)), "swp_set_withhold_arrival")
+
+
+def swp_thermo_log_bytes(ctx, capacity: int) -> int:
+    return int(load_library().swp_thermo_log_bytes(ctx, int(capacity)))
+
+
+def swp_set_thermo_log(ctx, every: int, capacity: int = 0, ring=None, ring_bytes: int = 0):
+    ptr = ring.data_ptr() if hasattr(ring, "data_ptr") else ring
+    return _check(ctx, load_library().swp_set_thermo_log(ctx, int(every), int(capacity), ptr, int(ring_bytes)),
+                  "swp_set_thermo_log")
+
+
+def swp_thermo_log(ctx, rec, steps, max_records: int) -> int:
+    """rec: device float64 [max_records][10]; steps: device int64 [max_records]."""
+    n = ctypes.c_int64(0)
+    _check(ctx, load_library().swp_thermo_log(ctx, rec.data_ptr(), steps.data_ptr(), int(max_records),
+                                             ctypes.byref(n)), "swp_thermo_log")
+    return int(n.value)
 
 
 def swp_last_error(ctx) -> str:

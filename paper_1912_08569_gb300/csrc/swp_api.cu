@@ -25,6 +25,31 @@ struct PairHost {
     double eps = 1.0, sigma = 1.0, lambda3 = 0.0, rcut = 0.0, rbond = 0.0;
 };
 
+// Thermo-log record first + blockIdx.x (in ring slot (first + r) % cap): warp
+// q sums quantity q of the block partials of the grid that wrote the record,
+// in the order of the step kernel's end-of-launch reduction (32 blocks per
+// shuffle tree, the trees' sums in block order), so a logged last step reads
+// the same as the launch's thermo record.
+__global__ void k_tlog_reduce(const double* ring, const long long* steps, int cap, int max_blocks,
+                              long long first, double* out, long long* out_step)
+{
+    const long long r = blockIdx.x;
+    const int slot = (int)((first + r) % cap);
+    const int G = (int)steps[2 * slot + 1];
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* src = ring + (size_t)slot * max_blocks * kNQ + q;
+    double t = 0.0;
+    for (int w = 0; w < (G + 31) / 32; w++) {
+        const int b = 32 * w + lane;
+        double v = b < G ? src[(size_t)b * kNQ] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        t += v;
+    }
+    if (lane == 0) out[r * kNQA + q] = t;
+    if (threadIdx.x == 0) out_step[r] = steps[2 * slot];
+}
+
 __global__ void k_mark_stale(Ctl* ctl)
 {
     if (ctl->state == 0) ctl->state = 1;
@@ -49,6 +74,7 @@ struct swp_ctx {
     long long timeout_ns = 2000000000LL;
     int resident = 1;  // the FP32 step may keep each block's neighbourhood in shared memory
     int withhold = 0;  // test hook: the next launch withholds one barrier arrival
+    int tlog_every = 0;  // thermo log: every how many steps a record is written (0: off)
     void* ws = nullptr;
     size_t ws_bytes = 0;
     void* nl = nullptr;
@@ -476,6 +502,7 @@ int run(swp_ctx* c, RunArgs a)
     if (rc) return rc;
     a.resident = c->resident;
     a.withhold = c->withhold;
+    a.tlog_every = d.tlog ? c->tlog_every : 0;
     c->withhold = 0;  // one launch consumes the request
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
     SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
@@ -1177,6 +1204,59 @@ int swp_set_resident(swp_ctx* c, int enable)
     if (!c) return SWP_ERR_INVALID;
     if (enable != 0 && enable != 1) return fail(c, SWP_ERR_INVALID, "enable must be 0 or 1");
     c->resident = enable;
+    return SWP_OK;
+}
+
+size_t swp_thermo_log_bytes(const swp_ctx* c, int64_t capacity)
+{
+    if (!c || capacity < 1 || capacity > INT32_MAX || c->max_blocks < 1) return 0;
+    return ((sizeof(double) * (size_t)capacity * c->max_blocks * kNQ + 255) & ~(size_t)255) +
+           sizeof(long long) * 2 * (size_t)capacity;
+}
+
+int swp_set_thermo_log(swp_ctx* c, int every, int64_t capacity, void* ring, size_t ring_bytes)
+{
+    if (!c) return SWP_ERR_INVALID;
+    if (every < 0) return fail(c, SWP_ERR_INVALID, "every must be >= 0");
+    if (every > 0) {
+        const size_t need = swp_thermo_log_bytes(c, capacity);
+        if (need == 0) return fail(c, SWP_ERR_INVALID, "capacity must be in [1, 2^31 - 1]");
+        if (!ring || ((uintptr_t)ring & 255)) return fail(c, SWP_ERR_INVALID, "ring must be a 256-byte aligned device buffer");
+        if (ring_bytes < need) return fail(c, SWP_ERR_INVALID, "ring smaller than swp_thermo_log_bytes");
+    }
+    double* rec = every > 0 ? (double*)ring : nullptr;
+    long long* stp = every > 0 ? (long long*)((char*)ring + ((sizeof(double) * (size_t)capacity * c->max_blocks * kNQ + 255) &
+                                                            ~(size_t)255))
+                               : nullptr;
+    const int cap = every > 0 ? (int)capacity : 0;
+    c->df.tlog = c->dd.tlog = rec;
+    c->df.tlog_step = c->dd.tlog_step = stp;
+    c->df.tlog_cap = c->dd.tlog_cap = cap;
+    c->tlog_every = every;
+    if (c->ws_bound) {
+        SWP_CUDA(c, cudaMemsetAsync(&dev_ctl(c)->tlog_n, 0, sizeof(long long), c->stream));
+    }
+    return SWP_OK;
+}
+
+int swp_thermo_log(swp_ctx* c, double* rec_dev, int64_t* step_dev, int64_t max_records, int64_t* n_records)
+{
+    int rc = ready(c, true);
+    if (rc) return rc;
+    if (!n_records || max_records < 0) return fail(c, SWP_ERR_INVALID, "need n_records and max_records >= 0");
+    *n_records = 0;
+    if (!c->df.tlog) return fail(c, SWP_ERR_INVALID, "no thermo log set (swp_set_thermo_log)");
+    if (max_records > 0 && (!rec_dev || !step_dev)) return fail(c, SWP_ERR_INVALID, "null output buffer");
+    rc = sync_ctl(c);
+    if (rc) return rc;
+    const long long written = c->hctl.tlog_n;
+    const long long n = std::min<long long>(std::min<long long>(written, c->df.tlog_cap), max_records);
+    if (n <= 0) return SWP_OK;
+    k_tlog_reduce<<<(unsigned)n, 32 * kNQA, 0, c->stream>>>(c->df.tlog, c->df.tlog_step, c->df.tlog_cap,
+                                                             c->max_blocks, written - n, rec_dev,
+                                                             (long long*)step_dev);
+    SWP_CUDA(c, cudaGetLastError());
+    *n_records = n;
     return SWP_OK;
 }
 

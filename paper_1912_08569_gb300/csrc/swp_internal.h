@@ -71,6 +71,7 @@ struct Ctl {
                                  // fit sets its round's word (rounds alternate; cleared on device)
     int resident_steps;          // steps of the last run call taken in the resident mode
     int pad_;
+    long long tlog_n;            // thermo-log records written since the log was set
 };
 
 // Status bits latched on the device.
@@ -153,6 +154,11 @@ struct Dev {
     int* slot_of_tag;  // [n] slot of every tag (written at each rebuild when has_bonds)
     int has_bonds;     // harmonic bonds k/2 (r - r0)^2 act (the vitrimer network's chains)
     Real bond_k, bond_r0;
+    // thermo log (null: none): a ring of tlog_cap records, each the block partials
+    // [max_blocks][kNQ] of one logged step, with (step, grid size) in tlog_step[2 r]
+    double* tlog = nullptr;
+    long long* tlog_step = nullptr;
+    int tlog_cap = 0;
 };
 
 // What one launch of the step kernel does.
@@ -173,6 +179,7 @@ struct RunArgs {
     int max_blocks;     // partials stride
     int resident;       // 1: an FP32 single-system run may keep each block's neighbourhood in shared memory
     int withhold;       // test hook: block 0 withholds its arrival at the launch's first grid barrier
+    int tlog_every;     // > 0: the steps whose number is a multiple of it write a thermo-log record
     int uni;            // 1: uniform coefficients (see uni_swap / uni_other)
     int uni_swap;       // table index of the reactive pair coefficients (UNI)
     int uni_other;      // table index of the other pairs' coefficients (UNI)

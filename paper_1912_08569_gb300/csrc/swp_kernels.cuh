@@ -476,8 +476,9 @@ __device__ __forceinline__ void warp_part(float x, int q)
     if ((threadIdx.x & 31) == 0) s_wpart[q][threadIdx.x >> 5] = x;
 }
 
-// Sums s_wpart over the block's warps into blk / out (see above).
-__device__ __forceinline__ void block_sums_from_warps(double* blk, double* out)
+// Sums s_wpart over the block's warps into blk / out (see above); out2, when
+// given with out, gets the same values.
+__device__ __forceinline__ void block_sums_from_warps(double* blk, double* out, double* out2 = nullptr)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     __syncthreads();
@@ -492,6 +493,7 @@ __device__ __forceinline__ void block_sums_from_warps(double* blk, double* out)
             const double tot = blk[warp] + ((double)hi + (double)lo);
             if (out) {
                 out[warp] = tot;
+                if (out2) out2[warp] = tot;
                 blk[warp] = 0.0;
             } else {
                 blk[warp] = tot;
@@ -499,18 +501,21 @@ __device__ __forceinline__ void block_sums_from_warps(double* blk, double* out)
         }
     } else if (out && warp == kNQA && lane < kNQ - kNQA) {
         out[kNQA + lane] = 0.0;
+        if (out2) out2[kNQA + lane] = 0.0;
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ void block_sums(const float* acc, float*, double* blk, double* out)
+__device__ __forceinline__ void block_sums(const float* acc, float*, double* blk, double* out,
+                                           double* out2 = nullptr)
 {
 #pragma unroll
     for (int q = 0; q < kNQA; q++) warp_part(acc[q], q);
-    block_sums_from_warps(blk, out);
+    block_sums_from_warps(blk, out, out2);
 }
 
-__device__ __forceinline__ void block_sums(const double* acc, double* stage, double* blk, double* out)
+__device__ __forceinline__ void block_sums(const double* acc, double* stage, double* blk, double* out,
+                                           double* out2 = nullptr)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, B = blockDim.x;
 #pragma unroll
@@ -525,6 +530,7 @@ __device__ __forceinline__ void block_sums(const double* acc, double* stage, dou
             const double tot = blk[warp] + x;
             if (out) {
                 out[warp] = tot;
+                if (out2) out2[warp] = tot;
                 blk[warp] = 0.0;
             } else {
                 blk[warp] = tot;
@@ -532,6 +538,7 @@ __device__ __forceinline__ void block_sums(const double* acc, double* stage, dou
         }
     } else if (out && warp == kNQA && lane < kNQ - kNQA) {
         out[kNQA + lane] = 0.0;
+        if (out2) out2[kNQA + lane] = 0.0;
     }
     __syncthreads();
 }
@@ -1418,6 +1425,9 @@ struct LoopState {
     int r_fail;          // this block's structures do not fit
     int r_np, r_nh, r_nhr;  // own particles, halo particles, halo rows of S
     int r_steps;         // steps this launch took in the resident mode
+    int tlog_left;       // steps up to and including the next logged one (0: no log)
+    int tlog_slot;       // ring slot of the next thermo-log record
+    int tlog_k;          // records this launch wrote
 };
 
 static __shared__ __align__(16) unsigned char s_tab_raw[kMaxTypes * kMaxTypes * sizeof(PairP<double>)];
@@ -1573,22 +1583,24 @@ __device__ __forceinline__ void reduce_small(const Dev<Real>& d)
     }
 }
 
-// Writes the block's partials of the sampled step's thermo terms (energies,
+// Writes the block's partials of a sampled step's thermo terms (energies,
 // virial, bond count, kinetic energy) from the threads' accumulators (or, for
-// a resident step, from the per-warp sums s_wpart it left).  Every call is
-// followed by a grid barrier, so the partials are complete for the reduction
-// at the end of the launch.  Only the last step of a launch is sampled: its
-// values are the ones a launch reports, and the other steps skip the terms.
+// a resident step, from the per-warp sums s_wpart it left) to the launch's
+// partials (last: the last step of the launch, whose values the launch
+// reports; reduced after the loop) and/or to a thermo-log record (log).
+// Every call is followed by a grid barrier.  Steps that are neither the
+// launch's last nor logged skip the thermo terms altogether.
 template <typename Real>
 __device__ __forceinline__ void thermo_partials(const Dev<Real>& d, const Acc<Real>& acc, Real* stage,
-                                                bool folded)
+                                                bool folded, bool last, double* log)
 {
-    double* out = d.partials + (size_t)g_rank() * kNQ;
+    double* out = last ? d.partials + (size_t)g_rank() * kNQ : log;
+    double* out2 = last ? log : nullptr;
     if (folded)
-        block_sums_from_warps(s_blk, out);
+        block_sums_from_warps(s_blk, out, out2);
     else
-        block_sums(acc.q, stage, s_blk, out);
-    if (threadIdx.x == 0) s_ls.have_thermo = 1;
+        block_sums(acc.q, stage, s_blk, out, out2);
+    if (last && threadIdx.x == 0) s_ls.have_thermo = 1;
 }
 
 __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
@@ -2249,6 +2261,13 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         s_ls.r_fail = 0;
         s_ls.r_np = s_ls.r_nh = s_ls.r_nhr = 0;
         s_ls.r_steps = 0;
+        s_ls.tlog_left = 0;
+        s_ls.tlog_slot = 0;
+        s_ls.tlog_k = 0;
+        if (a.tlog_every > 0 && d.tlog) {
+            s_ls.tlog_left = a.tlog_every - (int)(s_ls.step % a.tlog_every);
+            s_ls.tlog_slot = (int)(ctl->tlog_n % d.tlog_cap);
+        }
         // both agreement words start clear: every round comes after a barrier
         if (kRes && g_rank() == 0) {
             ctl->rfail[0] = 0;
@@ -2283,7 +2302,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 Acc<Real> acc;
                 run_f_pass<Real, UNI, BONDS, true>(d, a, F_STORE, s_ls.step, acc);
                 if (threadIdx.x == 0) s_ls.state = 0;  // read again only after the barrier
-                thermo_partials(d, acc, Stage<Real>::w(), false);
+                thermo_partials(d, acc, Stage<Real>::w(), false, true, (double*)nullptr);
                 if (!grid_barrier(ctl, a.timeout_ns, 11)) return false;
             }
         }
@@ -2336,9 +2355,10 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 if (rc) break;
             }
             const bool more = s_ls.remaining > 1;
-            // the thermo terms are summed on the launch's last step only: it is
-            // the step a launch reports them for
-            const bool th = !more;
+            // the thermo terms are summed on the launch's last step (the one a
+            // launch reports) and on the logged steps only
+            const bool logged = s_ls.tlog_left == 1;
+            const bool th = !more || logged;
             const int flags = F_CLOSING | (more ? F_OPENING : F_STORE);
             Acc<Real> acc;
             bool resident = false;
@@ -2366,10 +2386,22 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 s_ls.step = stp + 1;
                 s_ls.remaining--;
                 s_ls.done++;
+                if (s_ls.tlog_left > 0) s_ls.tlog_left = logged ? a.tlog_every : s_ls.tlog_left - 1;
             }
-            if (th) thermo_partials(d, acc, Stage<Real>::w(), resident);
+            if (th) {
+                double* lg = logged ? d.tlog + ((size_t)s_ls.tlog_slot * a.max_blocks + g_rank()) * kNQ : nullptr;
+                thermo_partials(d, acc, Stage<Real>::w(), resident, !more, lg);
+                if (logged && threadIdx.x == 0 && g_rank() == 0) {
+                    d.tlog_step[2 * s_ls.tlog_slot] = stp + 1;
+                    d.tlog_step[2 * s_ls.tlog_slot + 1] = g_size();
+                }
+            }
             unsigned* pub = more ? &ctl->dmax2[(stp + 1) & 1] : nullptr;
             if (!grid_barrier(ctl, a.timeout_ns, 21, pub)) return false;
+            if (logged && threadIdx.x == 0) {  // every thread used the slot before the barrier
+                s_ls.tlog_k++;
+                s_ls.tlog_slot = s_ls.tlog_slot + 1 == d.tlog_cap ? 0 : s_ls.tlog_slot + 1;
+            }
             if (more) {
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
                 __syncthreads();
@@ -2418,6 +2450,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         ctl->steps_done = s_ls.done;
         ctl->need_rebuild = s_ls.need_rb;
         ctl->resident_steps = s_ls.r_steps;
+        ctl->tlog_n += s_ls.tlog_k;
         if (s_ls.rebuilds > 0) {
             ctl->list_grid = s_ls.rc == 0 ? g_size() : -1;
             ctl->list_chunk = blockDim.x;

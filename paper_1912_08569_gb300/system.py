@@ -87,6 +87,34 @@ class SwapSystem:
         """Allow (default) or forbid the resident mode of the FP32 step."""
         A.swp_set_resident(self.ctx, 1 if enable else 0)
 
+    def set_thermo_log(self, every: int, capacity: int = 1024):
+        """Log the thermo record of every step whose number is a multiple of
+        ``every`` into a device ring of ``capacity`` records (every=0: off)."""
+        import torch
+
+        if every <= 0:
+            A.swp_set_thermo_log(self.ctx, 0)
+            self._tlog = None
+            return
+        nb = A.swp_thermo_log_bytes(self.ctx, capacity)
+        ring = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        A.swp_set_thermo_log(self.ctx, every, capacity, ring, nb)
+        self._tlog = (ring, int(capacity))
+
+    def thermo_log(self) -> dict:
+        """The logged records, oldest first: step, U2, U3, K, W [m][6], n_bonds."""
+        import torch
+
+        if getattr(self, "_tlog", None) is None:
+            raise RuntimeError("no thermo log: call set_thermo_log first")
+        cap = self._tlog[1]
+        rec = torch.empty((cap, 10), dtype=torch.float64, device=self.device)
+        stp = torch.empty(cap, dtype=torch.int64, device=self.device)
+        m = A.swp_thermo_log(self.ctx, rec, stp, cap)
+        r = rec[:m].cpu().numpy()
+        return dict(step=stp[:m].cpu().numpy(), U2=r[:, 0], U3=r[:, 1], K=r[:, 2], W=r[:, 3:9],
+                    n_bonds=np.rint(r[:, 9]).astype(np.int64))
+
     # -- state --------------------------------------------------------------
     def set_state(self, x, v=None, types=None, mass=None, img=None):
         """Host arrays (numpy) or device tensors (torch, cuda) in user order."""

@@ -7,7 +7,9 @@ at dt = 0.001 from Maxwell velocities at kT = 0.1.
 
 The GPU's FP64 path is held to the oracle at 1e-12 of the error scales for the
 evaluation, and step by step along the trajectory: the total energy
-U2 + U3 + K of every step against the oracle's record of the same step.  In the
+U2 + U3 + K of every step against the oracle's record of the same step (read
+after each of 1,000 one-step launches, and from the step kernel's thermo log
+of one 1,000-step launch).  In the
 unshifted form the energy jumps (v(1.5) = -0.068 for n = 10) whenever a pair
 crosses the cut-off, on both sides at the same step; the two trajectories stay
 within a few 1e-14 of each other over the 1,000 steps (fixed-point against
@@ -51,6 +53,16 @@ def test_config1_fp64_evaluation_and_nve_record(orc):
         th = s.thermo()
         rec[k] = th["U2"], th["U3"], th["K"], th["n_bonds"]
     assert s.thermo()["step"] == nsteps
+    # the same record from the step kernel's thermo log, in one 1,000-step launch
+    s2 = make_gpu(wl, "fp64")
+    s2.set_thermo_log(1, nsteps)
+    s2.run(nsteps, dt)
+    log = s2.thermo_log()
+    s2.close()
+    np.testing.assert_array_equal(log["step"], np.arange(1, nsteps + 1))
+    np.testing.assert_array_equal(log["n_bonds"], rec[:, 3])
+    np.testing.assert_allclose(np.column_stack([log["U2"], log["U3"], log["K"]]), rec[:, :3], rtol=0,
+                               atol=1e-13 * (ref["scale_U2"] + ref["scale_U3"]))
     xo, vo, imo, tho = orc.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], 2, tab, wl["box"], dt,
                                nsteps)
     E_gpu = rec[:, 0] + rec[:, 1] + rec[:, 2]
