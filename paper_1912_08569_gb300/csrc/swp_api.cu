@@ -1341,7 +1341,7 @@ int static_forces(swp_ctx* c, const double* x, const int32_t* type, double* f, d
                       ws + nl, kStaticScratchBytes);
         return fail(c, SWP_ERR_INVALID, buf);
     }
-    Dev<Real> d;
+    Dev<Real> d{};
     layout<Real>(c, base, &d);
     set_list(c, base + ws, &d);
 

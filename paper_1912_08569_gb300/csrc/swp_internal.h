@@ -156,9 +156,9 @@ struct Dev {
     Real bond_k, bond_r0;
     // thermo log (null: none): a ring of tlog_cap records, each the block partials
     // [max_blocks][kNQ] of one logged step, with (step, grid size) in tlog_step[2 r]
-    double* tlog = nullptr;
-    long long* tlog_step = nullptr;
-    int tlog_cap = 0;
+    double* tlog;
+    long long* tlog_step;
+    int tlog_cap;
 };
 
 // What one launch of the step kernel does.

@@ -477,11 +477,11 @@ __device__ __forceinline__ void warp_part(float x, int q)
 }
 
 // Sums s_wpart over the block's warps into blk / out (see above); out2, when
-// given with out, gets the same values.
-__device__ __forceinline__ void block_sums_from_warps(double* blk, double* out, double* out2 = nullptr)
+// given with out, gets the same values.  The caller orders the s_wpart writes
+// before and the next ones after (block_sums_from_warps: two __syncthreads).
+__device__ __forceinline__ void warp_sums_to(double* blk, double* out, double* out2)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
     if (warp < kNQA) {
         float hi = lane < nw ? s_wpart[warp][lane] : 0.0f, lo = 0.0f;
 #pragma unroll
@@ -503,6 +503,12 @@ __device__ __forceinline__ void block_sums_from_warps(double* blk, double* out, 
         out[kNQA + lane] = 0.0;
         if (out2) out2[kNQA + lane] = 0.0;
     }
+}
+
+__device__ __forceinline__ void block_sums_from_warps(double* blk, double* out, double* out2 = nullptr)
+{
+    __syncthreads();
+    warp_sums_to(blk, out, out2);
     __syncthreads();
 }
 
@@ -2388,16 +2394,26 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 s_ls.done++;
                 if (s_ls.tlog_left > 0) s_ls.tlog_left = logged ? a.tlog_every : s_ls.tlog_left - 1;
             }
-            if (th) {
-                double* lg = logged ? d.tlog + ((size_t)s_ls.tlog_slot * a.max_blocks + g_rank()) * kNQ : nullptr;
-                thermo_partials(d, acc, Stage<Real>::w(), resident, !more, lg);
-                if (logged && threadIdx.x == 0 && g_rank() == 0) {
-                    d.tlog_step[2 * s_ls.tlog_slot] = stp + 1;
-                    d.tlog_step[2 * s_ls.tlog_slot + 1] = g_size();
-                }
+            double* lg = logged ? d.tlog + ((size_t)s_ls.tlog_slot * a.max_blocks + g_rank()) * kNQ : nullptr;
+            if (logged && threadIdx.x == 0 && g_rank() == 0) {
+                d.tlog_step[2 * s_ls.tlog_slot] = stp + 1;
+                d.tlog_step[2 * s_ls.tlog_slot + 1] = g_size();
             }
+            // a logged resident step that is not the launch's last sums its
+            // warps' thermo terms while it waits at the barrier (the record is
+            // read after the launch); the launch's last step writes the
+            // partials the launch reduces, before its arrival
+            const bool late = resident && more;
+            if (th && !late) thermo_partials(d, acc, Stage<Real>::w(), resident, !more, lg);
             unsigned* pub = more ? &ctl->dmax2[(stp + 1) & 1] : nullptr;
-            if (!grid_barrier(ctl, a.timeout_ns, 21, pub)) return false;
+            {
+                BarState bs;
+                bs.target = s_ls.bar_target;
+                bar_arrive(ctl, bs, pub, &s_ls.dmax_bits);
+                if (th && late) warp_sums_to(s_blk, lg, nullptr);  // bar_arrive ordered the s_wpart writes
+                if (threadIdx.x == 0) s_ls.bar_target = bs.target;
+                if (!bar_wait(ctl, bs, a.timeout_ns, 21, &s_ls.ok)) return false;
+            }
             if (logged && threadIdx.x == 0) {  // every thread used the slot before the barrier
                 s_ls.tlog_k++;
                 s_ls.tlog_slot = s_ls.tlog_slot + 1 == d.tlog_cap ? 0 : s_ls.tlog_slot + 1;
