@@ -51,7 +51,7 @@ extern "C" {
 #define SWP_API
 #endif
 
-#define SWP_ABI_VERSION 3
+#define SWP_ABI_VERSION 4
 
 /* Status codes. */
 #define SWP_OK 0
@@ -234,6 +234,27 @@ SWP_API int swp_set_bonds(swp_ctx* ctx, int n_bonds, const int32_t* bonds, doubl
  * SWP_ERR_INVALID (bad types, not a swap pair, shifted form, more than one
  * reactive type pair), SWP_ERR_STATE (forces not current). */
 SWP_API int swp_param_grad(swp_ctx* ctx, int ti, int tj, double dU[3], double* dF_dev);
+
+/* One evaluation of the differentiable energy, enqueued on the context's
+ * stream with no host synchronisation (for a fit that evaluates many
+ * snapshots in a row).  Inputs in device memory: theta_dev = (lambda, eps,
+ * sigma) of the reactive pair (ti, tj) (3 doubles; the unshifted form, one
+ * reactive type pair, as for swp_param_grad), x_dev [n][3] positions in user
+ * order, type_dev [n] types (NULL: all 0).  It replaces the state (as
+ * swp_set_state with zero velocities, unit masses and no images), writes
+ * theta's coefficients into the device copy of the pair table (the host
+ * coefficients of swp_set_pair stay as they were and serve the next other
+ * run), rebuilds the list and evaluates: U_dev [1] = U2 + U3 (Eq. pot);
+ * F_dev [n][3] the forces (NULL: not read); dU_dev [3] = dU/d(lambda, eps,
+ * sigma) and dF_dev [3][n][3] as for swp_param_grad (NULL: not formed).
+ * Nothing is read back: errors the device latches (a list row longer than
+ * max_nn, a non-finite force, e.g. from theta out of range) are reported by
+ * the next swp_sync, and the outputs of that evaluation are then invalid; size
+ * max_nn for the densest snapshot.  Errors returned at once: SWP_ERR_INVALID
+ * (null theta/x/U, bad types, not a single unshifted swap pair),
+ * SWP_ERR_STATE (no workspace or list buffer bound). */
+SWP_API int swp_eval_grad(swp_ctx* ctx, int ti, int tj, const double* theta_dev, const double* x_dev,
+                          const int32_t* type_dev, double* U_dev, double* F_dev, double* dU_dev, double* dF_dev);
 
 /* Synchronising reads.  swp_read_thermo fills *out with the record of the
  * last force evaluation.  swp_read_forces needs current forces (state 0):

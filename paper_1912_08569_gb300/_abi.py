@@ -49,7 +49,7 @@ EXPORTS = (
     "swp_read_thermo", "swp_read_forces", "swp_read_state", "swp_read_nlist", "swp_set_launch", "swp_set_grid",
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
     "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds", "swp_set_resident",
-    "swp_set_withhold_arrival", "swp_thermo_log_bytes", "swp_set_thermo_log", "swp_thermo_log",
+    "swp_set_withhold_arrival", "swp_thermo_log_bytes", "swp_set_thermo_log", "swp_thermo_log", "swp_eval_grad",
 )
 
 
@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH):
         "swp_thermo_log_bytes": ([c_void_p, ctypes.c_int64], c_size_t),
         "swp_set_thermo_log": ([c_void_p, c_int, ctypes.c_int64, c_void_p, c_size_t], c_int),
         "swp_thermo_log": ([c_void_p, c_void_p, c_void_p, ctypes.c_int64, P(ctypes.c_int64)], c_int),
+        "swp_eval_grad": ([c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                           c_void_p], c_int),
         "swp_last_error": ([c_void_p], ctypes.c_char_p),
         "swp_destroy": ([c_void_p], c_int),
         "swp_compute_forces_static": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int),
@@ -289,6 +291,13 @@ def swp_thermo_log(ctx, rec, steps, max_records: int) -> int:
     _check(ctx, load_library().swp_thermo_log(ctx, rec.data_ptr(), steps.data_ptr(), int(max_records),
                                              ctypes.byref(n)), "swp_thermo_log")
     return int(n.value)
+
+
+def swp_eval_grad(ctx, ti: int, tj: int, theta, x, types, U, F=None, dU=None, dF=None):
+    """All arguments device tensors (float64; types int32), outputs written in place, no sync."""
+    ptr = lambda t: None if t is None else t.data_ptr()
+    return _check(ctx, load_library().swp_eval_grad(ctx, int(ti), int(tj), ptr(theta), ptr(x), ptr(types), ptr(U),
+                                                    ptr(F), ptr(dU), ptr(dF)), "swp_eval_grad")
 
 
 def swp_last_error(ctx) -> str:

@@ -3,7 +3,12 @@
 ``energy(model, x, theta)`` returns U(x; theta) for positions x [n, 3]
 (float64, CUDA, user order) and theta = (lambda, eps, sigma) of the reactive
 type pair.  Its backward gives dU/dx = -F and dU/dtheta from the library's
-kernels (swp_compute_forces, swp_param_grad).  The force returned by that
+kernels, which one call (swp_eval_grad) enqueues together with the energy:
+theta, x and every result stay in device memory and nothing waits for the
+device, so a fit over many snapshots runs at the pace of its kernels.  Errors
+the device latches (a list row longer than the list buffer allows, a
+non-finite force) surface at the next ``SwapModel.check()`` or any other
+synchronising call of the system.  The force returned by that
 backward is itself differentiable with respect to theta (through dF/dtheta
 from swp_param_grad), so a loss built from forces obtained by
 ``torch.autograd.grad(U, x, create_graph=True)`` -- a force-matching fit --
@@ -26,7 +31,8 @@ from . import _abi as A
 
 class SwapModel:
     """A SwapSystem whose reactive pair (ti, tj) takes (lambda, eps, sigma)
-    from a tensor at every evaluation; the other coefficients stay as given."""
+    from a tensor at every evaluation; the other coefficients stay as given.
+    Evaluations replace the system's state (zero velocities, unit masses)."""
 
     def __init__(self, system, pairs, types, react=(0, 1), mass=None):
         import torch
@@ -41,30 +47,42 @@ class SwapModel:
         self.types = torch.as_tensor(np.asarray(types, dtype=np.int32), device=dev)
         self.mass = None if mass is None else torch.as_tensor(np.asarray(mass, dtype=np.float64), device=dev)
 
-    def _set_theta(self, theta):
-        lam, eps, sig = [float(v) for v in theta.detach().cpu().tolist()]
-        p = self.pairs[self.react]
-        ti, tj = self.react
-        A.swp_set_pair(self.s.ctx, ti, tj, 2, eps, sig, p.get("n", 6), p.get("rcut", 0.0), lam, 0,
-                       p.get("rbond", 0.0) or 0.0)
-
     def evaluate(self, x, theta, want_grad=True):
-        """(U, F [n, 3], dU/dtheta [3], dF/dtheta [3, n, 3]) at x, theta (float64, device)."""
+        """(U [], F [n, 3], dU/dtheta [3], dF/dtheta [3, n, 3]) at x, theta as
+        float64 device tensors, enqueued on the system's stream (no sync)."""
         t = self.torch
-        self._set_theta(theta)
-        xd = x.detach().to(dtype=t.float64).contiguous()
-        self.s.set_state(xd, None, self.types, self.mass)
-        self.s.compute_forces()
-        th = A.swp_read_thermo(self.s.ctx)
-        U = th.U2 + th.U3
+        dev = self.s.device
         n = self.s.n
-        F = t.empty((n, 3), dtype=t.float64, device=x.device)
-        A.swp_read_forces(self.s.ctx, F, A.SWP_DEVICE)
-        if not want_grad:
-            return U, F, None, None
-        dF = t.empty((3, n, 3), dtype=t.float64, device=x.device)
-        dU = A.swp_param_grad(self.s.ctx, self.react[0], self.react[1], dF)
-        return U, F, t.as_tensor(dU, dtype=t.float64, device=x.device), dF
+        th = theta.detach().to(device=dev, dtype=t.float64).contiguous()
+        xd = x.detach().to(device=dev, dtype=t.float64).contiguous()
+        U = t.empty((), dtype=t.float64, device=dev)
+        F = t.empty((n, 3), dtype=t.float64, device=dev)
+        dU = t.empty(3, dtype=t.float64, device=dev) if want_grad else None
+        dF = t.empty((3, n, 3), dtype=t.float64, device=dev) if want_grad else None
+        A.swp_eval_grad(self.s.ctx, self.react[0], self.react[1], th, xd, self.types, U, F, dU, dF)
+        return U, F, dU, dF
+
+    def evaluate_batch(self, X, theta):
+        """The same for snapshots X [S, n, 3] (one list of types): U [S],
+        F [S, n, 3], dU/dtheta [S, 3], dF/dtheta [S, 3, n, 3], one evaluation
+        per snapshot enqueued into the slices of the outputs (no sync)."""
+        t = self.torch
+        dev = self.s.device
+        S, n = X.shape[0], self.s.n
+        th = theta.detach().to(device=dev, dtype=t.float64).contiguous()
+        Xd = X.detach().to(device=dev, dtype=t.float64).contiguous()
+        U = t.empty(S, dtype=t.float64, device=dev)
+        F = t.empty((S, n, 3), dtype=t.float64, device=dev)
+        dU = t.empty((S, 3), dtype=t.float64, device=dev)
+        dF = t.empty((S, 3, n, 3), dtype=t.float64, device=dev)
+        ctx, ti, tj, ty = self.s.ctx, self.react[0], self.react[1], self.types
+        for k in range(S):
+            A.swp_eval_grad(ctx, ti, tj, th, Xd[k], ty, U[k], F[k], dU[k], dF[k])
+        return U, F, dU, dF
+
+    def check(self):
+        """Waits for the evaluations so far and raises if the device latched an error."""
+        A.swp_sync(self.s.ctx)
 
 
 def _functions():
@@ -87,15 +105,41 @@ def _functions():
         def forward(ctx, x, theta, model):
             U, F, dU, dF = model.evaluate(x, theta)
             ctx.save_for_backward(x, theta, F, dU, dF)
-            return torch.tensor(U, dtype=torch.float64, device=x.device)
+            return U
 
         @staticmethod
         def backward(ctx, gU):
             x, theta, F, dU, dF = ctx.saved_tensors
-            gx = -gU * _Forces.apply(x, theta, F, dF)
+            gx = _Forces.apply(x, theta, F, dF) * (-gU)
             return gx, gU * dU, None
 
-    return _Energy, _Forces
+    # snapshots in one Function: X [S, n, 3], U [S], dF [S, 3, n, 3]
+    class _ForcesBatch(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, theta, F, dF):
+            ctx.save_for_backward(dF)
+            return F.clone()
+
+        @staticmethod
+        def backward(ctx, gF):
+            (dF,) = ctx.saved_tensors
+            gtheta = torch.einsum("sknc,snc->k", dF, gF)
+            return None, gtheta, None, None
+
+    class _EnergyBatch(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, theta, model):
+            U, F, dU, dF = model.evaluate_batch(X, theta)
+            ctx.save_for_backward(X, theta, F, dU, dF)
+            return U
+
+        @staticmethod
+        def backward(ctx, gU):
+            X, theta, F, dU, dF = ctx.saved_tensors
+            gX = _ForcesBatch.apply(X, theta, F, dF) * (-gU)[:, None, None]
+            return gX, (gU[:, None] * dU).sum(0), None
+
+    return _Energy, _Forces, _EnergyBatch, _ForcesBatch
 
 
 _FN = None
@@ -117,3 +161,11 @@ def forces(model: SwapModel, x, theta):
     """F(x; theta) [n, 3] float64, differentiable with respect to theta."""
     U, F, dU, dF = model.evaluate(x, theta)
     return _fn()[1].apply(x, theta, F, dF)
+
+
+def energy_batch(model: SwapModel, X, theta):
+    """U(X_s; theta) for snapshots X [S, n, 3] (the model's types) as a float64
+    tensor [S], differentiable in X and theta like ``energy``: one autograd
+    node for the whole batch, so a fit over many snapshots pays the Python
+    cost of autograd once, not per snapshot."""
+    return _fn()[2].apply(X, theta, model)

@@ -50,6 +50,10 @@ __global__ void k_tlog_reduce(const double* ring, const long long* steps, int ca
     if (threadIdx.x == 0) out_step[r] = steps[2 * slot];
 }
 
+// End of the force part of a device-driven evaluation: U = U2 + U3 of the
+// thermo record.
+__global__ void k_eval_energy(const Ctl* ctl, double* U) { U[0] = ctl->thermo[Q_U2] + ctl->thermo[Q_U3]; }
+
 __global__ void k_mark_stale(Ctl* ctl)
 {
     if (ctl->state == 0) ctl->state = 1;
@@ -75,6 +79,8 @@ struct swp_ctx {
     int resident = 1;  // the FP32 step may keep each block's neighbourhood in shared memory
     int withhold = 0;  // test hook: the next launch withholds one barrier arrival
     int tlog_every = 0;  // thermo log: every how many steps a record is written (0: off)
+    int table_only = 0;      // the next launch reads pair coefficients from the device table (not the uniform copy)
+    bool table_theta = false;  // swp_eval_grad wrote theta's coefficients into the device table
     void* ws = nullptr;
     size_t ws_bytes = 0;
     void* nl = nullptr;
@@ -222,8 +228,8 @@ size_t layout(swp_ctx* c, char* base, Dev<Real>* d)
     int* cell_fill = (int*)take(sizeof(int) * (c->ncell + n));
     int* perm = (int*)take(sizeof(int) * n);
     int* bsum = (int*)take(sizeof(int) * c->max_blocks);
-    // thermo partials of the step kernel; also the scratch of the parameter derivatives (4 * 512 + 4)
-    double* partials = (double*)take(sizeof(double) * std::max<size_t>((size_t)c->max_blocks * kNQ, 4 * 512 + 4));
+    // thermo partials of the step kernel; also the scratch of the parameter derivatives (4 * 512 + 16)
+    double* partials = (double*)take(sizeof(double) * std::max<size_t>((size_t)c->max_blocks * kNQ, 4 * 512 + 16));
     double* io = (double*)take(sizeof(double) * 7 * n);
     int* io_int = (int*)take(sizeof(int) * 4 * n);
     int* bond_tag = (int*)take(sizeof(int) * kMaxBonds * n);
@@ -386,6 +392,7 @@ int map_status(swp_ctx* c)
                       c->hctl.timeout_at);
         return fail(c, SWP_ERR_TIMEOUT, buf);
     }
+    if (s & kStatusBadType) return fail(c, SWP_ERR_INVALID, "a particle type is out of range; set the state again");
     if (s & kStatusNonfinite) return fail(c, SWP_ERR_NONFINITE, "non-finite force; set the state again");
     if (s & kStatusOverflow) {
         cudaError_t e = cudaSuccess;
@@ -498,11 +505,16 @@ int run(swp_ctx* c, RunArgs a)
     if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
     bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
     c->grid = step_grid(c, bps);
+    if (!c->table_only && c->table_theta) {  // an ordinary run takes the host coefficients again
+        c->table_dirty = true;
+        c->table_theta = false;
+    }
     int rc = prepare_args<Real>(c, a);
     if (rc) return rc;
     a.resident = c->resident;
     a.withhold = c->withhold;
     a.tlog_every = d.tlog ? c->tlog_every : 0;
+    if (c->table_only) a.uni = 0;  // the device table holds coefficients the host copy does not
     c->withhold = 0;  // one launch consumes the request
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
     SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
@@ -1111,24 +1123,83 @@ int swp_param_grad(swp_ctx* c, int ti, int tj, double dU[3], double* dF_dev)
     rc = sync_ctl(c);
     if (rc) return rc;
     if (c->hctl.state != 0) return fail(c, SWP_ERR_STATE, "forces are not current: call swp_compute_forces");
-    const double lam = p.lambda3, eps = p.eps, sig = p.sigma;
-    double* part;
-    if (c->precision == SWP_FP64) {
-        part = c->dd.partials;
-        SWP_CUDA(c, launch_param_grad<double>(c->dd, c->hctl.pos_cur, c->dd.io, part, lam, eps, sig, dF_dev,
-                                               part + 2048, c->stream));
-    } else {
-        part = c->df.partials;
-        SWP_CUDA(c, launch_param_grad<float>(c->df, c->hctl.pos_cur, c->df.io, part, lam, eps, sig, dF_dev,
-                                              part + 2048, c->stream));
-    }
-    double t[4];
-    SWP_CUDA(c, cudaMemcpyAsync(t, part + 2048, sizeof t, cudaMemcpyDeviceToHost, c->stream));
+    // theta and dU/dtheta pass through the scratch after the four sums
+    double th[3] = {p.lambda3, p.eps, p.sigma}, out[3];
+    double* part = c->precision == SWP_FP64 ? c->dd.partials : c->df.partials;
+    double* dth = part + 2048 + 4;
+    double* ddu = dth + 3;
+    SWP_CUDA(c, cudaMemcpyAsync(dth, th, sizeof th, cudaMemcpyHostToDevice, c->stream));
+    if (c->precision == SWP_FP64)
+        SWP_CUDA(c, launch_param_grad<double>(c->dd, c->hctl.pos_cur, c->dd.io, part, dth, dF_dev, part + 2048,
+                                               ddu, c->stream));
+    else
+        SWP_CUDA(c, launch_param_grad<float>(c->df, c->hctl.pos_cur, c->df.io, part, dth, dF_dev, part + 2048,
+                                              ddu, c->stream));
+    SWP_CUDA(c, cudaMemcpyAsync(out, ddu, sizeof out, cudaMemcpyDeviceToHost, c->stream));
     SWP_CUDA(c, cudaStreamSynchronize(c->stream));
-    // t = (T, sum_i (sum_j vh q - S D), sum_pairs v/eps, sum_pairs Q)
-    dU[0] = eps * t[0];
-    dU[1] = t[2] + lam * t[0];
-    dU[2] = (eps * t[3] + lam * eps * t[1]) / sig;
+    dU[0] = out[0];
+    dU[1] = out[1];
+    dU[2] = out[2];
+    return SWP_OK;
+}
+
+int swp_eval_grad(swp_ctx* c, int ti, int tj, const double* theta_dev, const double* x_dev, const int32_t* type_dev,
+                  double* U_dev, double* F_dev, double* dU_dev, double* dF_dev)
+{
+    int rc = ready(c, false);
+    if (rc) return rc;
+    if (!theta_dev || !U_dev || (c->n > 0 && !x_dev)) return fail(c, SWP_ERR_INVALID, "null theta, x or U");
+    if (ti < 0 || tj < 0 || ti >= c->ntypes || tj >= c->ntypes) return fail(c, SWP_ERR_INVALID, "type out of range");
+    const PairHost& p = c->pairs[ti * c->ntypes + tj];
+    if (p.kind != KIND_SWAP) return fail(c, SWP_ERR_INVALID, "(ti, tj) is not a swap pair");
+    if (p.shift) return fail(c, SWP_ERR_INVALID, "parameter derivatives need the unshifted form");
+    for (int a = 0; a < c->ntypes; a++)
+        for (int b = a; b < c->ntypes; b++)
+            if (c->pairs[a * c->ntypes + b].kind == KIND_SWAP && !((a == ti && b == tj) || (a == tj && b == ti)))
+                return fail(c, SWP_ERR_INVALID, "parameter derivatives need a single reactive type pair");
+    rc = upload_table(c);
+    if (rc) return rc;
+    const size_t n = (size_t)c->n;
+    const double c_rmin = std::pow(2.0, 1.0 / p.n), c_rb = std::pow((1.0 - std::sqrt(0.5)) / 2.0, -1.0 / p.n);
+    const bool f64 = c->precision == SWP_FP64;
+    double* io = f64 ? c->dd.io : c->df.io;
+    SWP_CUDA(c, cudaMemsetAsync(f64 ? (void*)c->dd.cell_cnt : (void*)c->df.cell_cnt, 0, sizeof(int) * c->ncell,
+                                c->stream));
+    if (n > 0) SWP_CUDA(c, cudaMemcpyAsync(io, x_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, c->stream));
+    if (f64) SWP_CUDA(c, launch_eval_prep<double>(c->dd, ti, tj, theta_dev, c_rmin, c_rb, p.rbond, type_dev, c->stream));
+    else SWP_CUDA(c, launch_eval_prep<float>(c->df, ti, tj, theta_dev, c_rmin, c_rb, p.rbond, type_dev, c->stream));
+    c->state_set = true;
+    c->table_theta = true;
+    if (n == 0) {
+        SWP_CUDA(c, cudaMemsetAsync(U_dev, 0, sizeof(double), c->stream));
+        if (dU_dev) SWP_CUDA(c, cudaMemsetAsync(dU_dev, 0, 3 * sizeof(double), c->stream));
+        return SWP_OK;
+    }
+    if (f64) SWP_CUDA(c, launch_set_state<double>(c->dd, c->stream));
+    else SWP_CUDA(c, launch_set_state<float>(c->df, c->stream));
+    // forces at the new positions: rebuild and evaluate, coefficients from the device table
+    RunArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nsteps = 0;
+    a.force_rebuild = 1;
+    c->table_only = 1;
+    rc = run_any(c, a);
+    c->table_only = 0;
+    if (rc) return rc;
+    k_eval_energy<<<1, 1, 0, c->stream>>>(dev_ctl(c), U_dev);
+    SWP_CUDA(c, cudaGetLastError());
+    if (F_dev) {
+        if (f64) SWP_CUDA(c, launch_get_forces<double>(c->dd, -1, c->stream));
+        else SWP_CUDA(c, launch_get_forces<float>(c->df, -1, c->stream));
+        SWP_CUDA(c, cudaMemcpyAsync(F_dev, io, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (dU_dev || dF_dev) {
+        double* part = f64 ? c->dd.partials : c->df.partials;
+        if (f64)
+            SWP_CUDA(c, launch_param_grad<double>(c->dd, -1, io, part, theta_dev, dF_dev, part + 2048, dU_dev, c->stream));
+        else
+            SWP_CUDA(c, launch_param_grad<float>(c->df, -1, io, part, theta_dev, dF_dev, part + 2048, dU_dev, c->stream));
+    }
     return SWP_OK;
 }
 

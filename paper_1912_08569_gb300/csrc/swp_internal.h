@@ -79,6 +79,7 @@ constexpr int kStatusOverflow = 1;
 constexpr int kStatusTimeout = 2;
 constexpr int kStatusNonfinite = 4;
 constexpr int kStatusBadCell = 8;
+constexpr int kStatusBadType = 16;  // a state's type (device input) out of range
 
 template <typename Real>
 struct Vec4;
@@ -203,9 +204,14 @@ cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* 
 template <typename Real>
 cudaError_t batch_occupancy(int* blocks_per_sm);
 // Derivatives with respect to one reactive type pair's (lambda, eps, sigma).
+// theta: (lambda, eps, sigma) in device memory; pc < 0: the control block's
+// current snapshot set; dU (device, may be null): dU/dtheta from the sums.
 template <typename Real>
-cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* part, double lam, double eps,
-                              double sig, double* out, double* total, cudaStream_t s);
+cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* part, const double* theta,
+                              double* out, double* total, double* dU, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_eval_prep(const Dev<Real>& d, int ti, int tj, const double* theta, double c_rmin, double c_rb,
+                             double rbond, const int* type, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_set_state(const Dev<Real>& d, cudaStream_t s);
 template <typename Real>

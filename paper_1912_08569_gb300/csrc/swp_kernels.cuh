@@ -2548,6 +2548,10 @@ __global__ void k_set_state(Dev<Real> d)
             qs[c] = q;
         }
         int ty = d.io_int[i];
+        if ((unsigned)ty >= (unsigned)d.ntypes) {  // (device input is not checked on the host)
+            atomicOr(&d.ctl->status, kStatusBadType);
+            ty = 0;
+        }
         P4 p;
         p.x = snap_coord(qs[0], 0, d);
         p.y = snap_coord(qs[1], 1, d);
@@ -2583,11 +2587,13 @@ __global__ void k_get_state(Dev<Real> d, int pc, int ac)
     }
 }
 
+// pc < 0: the current snapshot set as the control block records it.
 template <typename Real>
 __global__ void k_get_forces(Dev<Real> d, int pc)
 {
     typedef typename Dev<Real>::R4 R4;
     const int n = d.n;
+    if (pc < 0) pc = d.ctl->pos_cur;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         int tag = pos_bits(d.pos[pc][q]) >> kTypeBits;
         R4 f = d.force[q];
@@ -2642,6 +2648,20 @@ __device__ __forceinline__ Real pair_x(const PairP<Real>& p, Real r2)
     return x;
 }
 
+// The two passes give each particle kPgLanes consecutive lanes of a warp:
+// lane l of the group takes the particle's reactive entries l, l + kPgLanes,
+// ..., and the group's partial sums meet in a fixed shuffle tree, so the
+// gathers of a particle's partners run in parallel (and the grid fills the
+// device at a few 10^4 particles).
+constexpr int kPgLanes = 4;
+
+__device__ __forceinline__ double pg_group_sum(double v)
+{
+#pragma unroll
+    for (int o = kPgLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, kPgLanes);
+    return v;
+}
+
 // Pass 1: S_i and D_i per slot into sd[2i], sd[2i+1]; per-block sums of
 // (T, sum_i (sum_j vh q - S D), sum_pairs v/eps, sum_pairs Q) into part[4b..].
 template <typename Real>
@@ -2649,35 +2669,51 @@ __global__ void k_pgrad_sums(Dev<Real> d, int pc, double* sd, double* part)
 {
     __shared__ double red[4][32];
     const int n = d.n;
+    if (pc < 0) pc = d.ctl->pos_cur;
+    const int g = threadIdx.x % kPgLanes;
+    const int gpb = blockDim.x / kPgLanes;  // particles per block and round
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const typename Dev<Real>::P4 pi = d.pos[pc][i];
-        const int4 inf = d.pinfo[i];
+    // every lane of a warp runs the same number of rounds (the shuffles need them all)
+    const int rounds = (n + gpb * gridDim.x - 1) / (gpb * gridDim.x);
+    for (int r = 0; r < rounds; r++) {
+        const int i = (r * gridDim.x + blockIdx.x) * gpb + (int)threadIdx.x / kPgLanes;
         double S = 0.0, D = 0.0, v2 = 0.0, vq = 0.0, ve = 0.0, qq = 0.0;
-        for (int e = inf.x; e < inf.x + inf.y; e++) {
-            const typename Dev<Real>::P4 pj = d.pos[pc][d.ent_j[e]];
-            const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
-            Real dx, dy, dz;
-            const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
-            if (!(r2 < p.rc2)) continue;
-            const double x = (double)pair_x(p, r2), nn = (double)p.n_real;
-            const bool beyond = r2 > p.rmin2;
-            const double vh = beyond ? 4.0 * (x - x * x) : 1.0;
-            const double Q = 4.0 * nn * (2.0 * x * x - x);
-            const double q = beyond ? Q : 0.0;
-            S += vh;
-            D += q;
-            v2 += vh * vh;
-            vq += vh * q;
-            ve += 0.5 * 4.0 * (x * x - x);  // each pair is listed from both ends
-            qq += 0.5 * Q;
+        if (i < n) {
+            const typename Dev<Real>::P4 pi = d.pos[pc][i];
+            const int4 inf = d.pinfo[i];
+            for (int e = inf.x + g; e < inf.x + inf.y; e += kPgLanes) {
+                const typename Dev<Real>::P4 pj = d.pos[pc][d.ent_j[e]];
+                const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
+                Real dx, dy, dz;
+                const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+                if (!(r2 < p.rc2)) continue;
+                const double x = (double)pair_x(p, r2), nn = (double)p.n_real;
+                const bool beyond = r2 > p.rmin2;
+                const double vh = beyond ? 4.0 * (x - x * x) : 1.0;
+                const double Q = 4.0 * nn * (2.0 * x * x - x);
+                const double q = beyond ? Q : 0.0;
+                S += vh;
+                D += q;
+                v2 += vh * vh;
+                vq += vh * q;
+                ve += 0.5 * 4.0 * (x * x - x);  // each pair is listed from both ends
+                qq += 0.5 * Q;
+            }
         }
-        sd[2 * i] = S;
-        sd[2 * i + 1] = D;
-        acc[0] += 0.5 * (S * S - v2);
-        acc[1] += vq - S * D;
-        acc[2] += ve;
-        acc[3] += qq;
+        S = pg_group_sum(S);
+        D = pg_group_sum(D);
+        v2 = pg_group_sum(v2);
+        vq = pg_group_sum(vq);
+        ve = pg_group_sum(ve);
+        qq = pg_group_sum(qq);
+        if (i < n && g == 0) {
+            sd[2 * i] = S;
+            sd[2 * i + 1] = D;
+            acc[0] += 0.5 * (S * S - v2);
+            acc[1] += vq - S * D;
+            acc[2] += ve;
+            acc[3] += qq;
+        }
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -2695,56 +2731,127 @@ __global__ void k_pgrad_sums(Dev<Real> d, int pc, double* sd, double* part)
     }
 }
 
-// Pass 2: dF/dtheta per particle, in user order: out[(k n + tag) 3 + c].
+// Pass 2: dF/dtheta per particle, in user order: out[(k n + tag) 3 + c];
+// theta = (lambda, eps, sigma) in device memory.
 template <typename Real>
-__global__ void k_pgrad_forces(Dev<Real> d, int pc, const double* sd, double lam, double eps, double sig,
-                               double* out)
+__global__ void k_pgrad_forces(Dev<Real> d, int pc, const double* sd, const double* theta, double* out)
 {
     const int n = d.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const typename Dev<Real>::P4 pi = d.pos[pc][i];
-        const int4 inf = d.pinfo[i];
-        const double Si = sd[2 * i], Di = sd[2 * i + 1];
+    if (pc < 0) pc = d.ctl->pos_cur;
+    const double lam = theta[0], eps = theta[1], sig = theta[2];
+    const int g = threadIdx.x % kPgLanes;
+    const int gpb = blockDim.x / kPgLanes;
+    const int rounds = (n + gpb * gridDim.x - 1) / (gpb * gridDim.x);
+    for (int r = 0; r < rounds; r++) {
+        const int i = (r * gridDim.x + blockIdx.x) * gpb + (int)threadIdx.x / kPgLanes;
         double g3[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
-        for (int e = inf.x; e < inf.x + inf.y; e++) {
-            const int j = d.ent_j[e];
-            const typename Dev<Real>::P4 pj = d.pos[pc][j];
-            const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
-            Real dx, dy, dz;
-            const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
-            if (!(r2 < p.rc2)) continue;
-            const double x = (double)pair_x(p, r2), nn = (double)p.n_real, rr = (double)r2;
-            const bool beyond = r2 > p.rmin2;
-            const double vh = beyond ? 4.0 * (x - x * x) : 1.0;
-            const double Q = 4.0 * nn * (2.0 * x * x - x);
-            const double q = beyond ? Q : 0.0;
-            const double Qs = 4.0 * nn * nn * x * (4.0 * x - 1.0);
-            const double qs = beyond ? Qs : 0.0;
-            const double g = Si + sd[2 * j] - 2.0 * vh;
-            const double Dsum = Di + sd[2 * j + 1];
-            const double dft[3] = {-eps * g * q / rr, (Q - lam * g * q) / rr,
-                                   (eps * Qs - lam * eps * ((2.0 * q - Dsum) * q + g * qs)) / (sig * rr)};
-            const double dv[3] = {(double)dx, (double)dy, (double)dz};
+        int tag = 0;
+        if (i < n) {
+            const typename Dev<Real>::P4 pi = d.pos[pc][i];
+            const int4 inf = d.pinfo[i];
+            const double Si = sd[2 * i], Di = sd[2 * i + 1];
+            tag = pos_bits(pi) >> kTypeBits;
+            for (int e = inf.x + g; e < inf.x + inf.y; e += kPgLanes) {
+                const int j = d.ent_j[e];
+                const typename Dev<Real>::P4 pj = d.pos[pc][j];
+                const PairP<Real>& p = d.table[type_of(pi) * d.ntypes + type_of(pj)];
+                Real dx, dy, dz;
+                const Real r2 = dist2_listed(pi, pj, d, dx, dy, dz);
+                if (!(r2 < p.rc2)) continue;
+                const double x = (double)pair_x(p, r2), nn = (double)p.n_real, rr = (double)r2;
+                const bool beyond = r2 > p.rmin2;
+                const double vh = beyond ? 4.0 * (x - x * x) : 1.0;
+                const double Q = 4.0 * nn * (2.0 * x * x - x);
+                const double q = beyond ? Q : 0.0;
+                const double Qs = 4.0 * nn * nn * x * (4.0 * x - 1.0);
+                const double qs = beyond ? Qs : 0.0;
+                const double gg = Si + sd[2 * j] - 2.0 * vh;
+                const double Dsum = Di + sd[2 * j + 1];
+                const double dft[3] = {-eps * gg * q / rr, (Q - lam * gg * q) / rr,
+                                       (eps * Qs - lam * eps * ((2.0 * q - Dsum) * q + gg * qs)) / (sig * rr)};
+                const double dv[3] = {(double)dx, (double)dy, (double)dz};
 #pragma unroll
-            for (int k = 0; k < 3; k++)
+                for (int k = 0; k < 3; k++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) g3[k][c] -= dft[k] * dv[c];
+                    for (int c = 0; c < 3; c++) g3[k][c] -= dft[k] * dv[c];
+            }
         }
-        const int tag = pos_bits(pi) >> kTypeBits;
 #pragma unroll
         for (int k = 0; k < 3; k++)
 #pragma unroll
-            for (int c = 0; c < 3; c++) out[((size_t)k * n + tag) * 3 + c] = g3[k][c];
+            for (int c = 0; c < 3; c++) g3[k][c] = pg_group_sum(g3[k][c]);
+        if (i < n && g < 3) {  // lanes 0..2 of the group write parameter k = g
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if (k == g)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) out[((size_t)k * n + tag) * 3 + c] = g3[k][c];
+        }
     }
 }
 
-// Pass 3: one block adds the per-block sums in block order.
-static __global__ void k_pgrad_total(const double* part, int nblocks, double* total)
+// Pass 3: one block adds the per-block sums in block order into total[4],
+// and forms dU/dtheta from them into dU[3] (when given).
+static __global__ void k_pgrad_total(const double* part, int nblocks, double* total, const double* theta,
+                                     double* dU)
 {
+    __shared__ double t[4];
     if (threadIdx.x < 4) {
-        double t = 0.0;
-        for (int b = 0; b < nblocks; b++) t += part[4 * b + threadIdx.x];
-        total[threadIdx.x] = t;
+        double v = 0.0;
+        for (int b = 0; b < nblocks; b++) v += part[4 * b + threadIdx.x];
+        total[threadIdx.x] = v;
+        t[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && dU) {
+        // t = (T, sum_i (sum_j vh q - S D), sum_pairs v/eps, sum_pairs Q)
+        const double lam = theta[0], eps = theta[1], sig = theta[2];
+        dU[0] = eps * t[0];
+        dU[1] = t[2] + lam * t[0];
+        dU[2] = (eps * t[3] + lam * eps * t[1]) / sig;
+    }
+}
+
+// Start of one device-driven evaluation (swp_eval_grad): resets the control
+// block as a new state does (forces stale, list to be rebuilt), writes the
+// reactive pair's coefficients from theta = (lambda, eps, sigma) in device
+// memory into both (ti, tj) entries of the device pair table (the
+// theta-dependent ones; the same arithmetic as the host table), and fills
+// the state staging: velocities 0, masses 1, images 0, types from type.
+// c_rmin = 2^(1/n), c_rb = ((1 - sqrt(1/2)) / 2)^(-1/n) (host constants),
+// rbond > 0: the bond radius as given.
+template <typename Real>
+__global__ void k_eval_prep(Dev<Real> d, int ti, int tj, const double* theta, double c_rmin, double c_rb,
+                            double rbond, const int* type)
+{
+    const int n = d.n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctl* ctl = d.ctl;
+        int* w = (int*)ctl;
+        for (int k = 0; k < (int)(sizeof(Ctl) / sizeof(int)); k++) w[k] = 0;
+        ctl->state = 1;
+        ctl->need_rebuild = 1;
+        const double lam = theta[0], eps = theta[1], sig = theta[2];
+        PairP<Real>* tab = (PairP<Real>*)d.table;
+        PairP<Real> e = tab[ti * d.ntypes + tj];
+        e.four_eps = (Real)(4.0 * eps);
+        e.sig2 = (Real)(sig * sig);
+        const double rmin = sig * c_rmin;
+        e.rmin2 = (Real)(rmin * rmin);
+        e.a = (Real)sqrt(lam * eps);
+        e.inv_epshat = (Real)(1.0 / eps);
+        const double rb = rbond > 0.0 ? rbond : sig * c_rb;
+        e.rbond2 = (Real)(rb * rb);
+        tab[ti * d.ntypes + tj] = e;
+        tab[tj * d.ntypes + ti] = e;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int c = 0; c < 3; c++) {
+            d.io[3 * n + 3 * i + c] = 0.0;
+            d.io_int[n + 3 * i + c] = 0;
+        }
+        d.io[6 * n + i] = 1.0;
+        d.io_int[i] = type ? type[i] : 0;
     }
 }
 

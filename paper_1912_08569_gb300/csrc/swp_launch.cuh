@@ -144,19 +144,28 @@ cudaError_t launch_get_nlist(const Dev<Real>& d, int pc, int* rows, int* counts,
 // into out [3][n][3] (user order) when out is not null, the four sums into
 // total [4]; part: scratch of 4 * 512 doubles.
 template <typename Real>
-cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* part, double lam, double eps,
-                              double sig, double* out, double* total, cudaStream_t s)
+cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* part, const double* theta,
+                              double* out, double* total, double* dU, cudaStream_t s)
 {
-    const int blocks = std::max(1, std::min(512, (d.n + 255) / 256));
+    // kPgLanes threads per particle; at most 512 blocks (the partials scratch)
+    const int blocks = std::max(1, std::min(512, (d.n * single::kPgLanes + 255) / 256));
     single::k_pgrad_sums<Real><<<blocks, 256, 0, s>>>(d, pc, sd, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (out) {
-        single::k_pgrad_forces<Real><<<blocks, 256, 0, s>>>(d, pc, sd, lam, eps, sig, out);
+        single::k_pgrad_forces<Real><<<blocks, 256, 0, s>>>(d, pc, sd, theta, out);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    single::k_pgrad_total<<<1, 32, 0, s>>>(part, blocks, total);
+    single::k_pgrad_total<<<1, 32, 0, s>>>(part, blocks, total, theta, dU);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_eval_prep(const Dev<Real>& d, int ti, int tj, const double* theta, double c_rmin, double c_rb,
+                             double rbond, const int* type, cudaStream_t s)
+{
+    single::k_eval_prep<Real><<<io_grid(d.n), 256, 0, s>>>(d, ti, tj, theta, c_rmin, c_rb, rbond, type);
     return cudaGetLastError();
 }
 
@@ -170,8 +179,10 @@ cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* pa
     template cudaError_t launch_batch<R>(const Dev<R>*, const RunArgs*, const int*, const int4*, int, int, int, \
                                          cudaStream_t);                                                   \
     template cudaError_t batch_occupancy<R>(int*);                                               \
-    template cudaError_t launch_param_grad<R>(const Dev<R>&, int, double*, double*, double, double, double, \
+    template cudaError_t launch_param_grad<R>(const Dev<R>&, int, double*, double*, const double*, double*, \
                                               double*, double*, cudaStream_t);                            \
+    template cudaError_t launch_eval_prep<R>(const Dev<R>&, int, int, const double*, double, double, double, \
+                                             const int*, cudaStream_t);                                  \
     template size_t run_smem_bytes<R>();
 
 }  // namespace swp

@@ -22,11 +22,15 @@ class ToyModel:
     def evaluate(self, x, theta, want_grad=True):
         x = x.detach().to(torch.float64)
         th = theta.detach().to(torch.float64)
-        U = float(_toy_u(x, th))
+        U = _toy_u(x, th)  # a 0-dim tensor, like the real model's device scalar
         F = -(th[0] * x + th[1] + th[2] * x ** 3)
         dU = torch.stack([(x * x).sum() / 2, x.sum(), (x ** 4).sum() / 4])
         dF = torch.stack([-x, -torch.ones_like(x), -(x ** 3)])
         return U, F, dU, dF
+
+    def evaluate_batch(self, X, theta):
+        out = [self.evaluate(x, theta) for x in X]
+        return tuple(torch.stack([o[k] for o in out]) for k in range(4))
 
 
 def test_energy_backward_gives_minus_forces_and_dU_dtheta():
@@ -73,3 +77,29 @@ def test_force_matching_double_backward_matches_autograd():
     loss3 = sum(((autodiff.forces(model, x, t3) - Fr) ** 2).mean() for x, Fr in zip(snaps, ref))
     loss3.backward()
     torch.testing.assert_close(t3.grad, tr.grad, rtol=1e-12, atol=1e-14)
+
+
+def test_energy_batch_matches_per_snapshot_functions():
+    """energy_batch (one autograd node for all snapshots) gives the loss and the
+    gradient of the per-snapshot form."""
+    g = torch.Generator().manual_seed(3)
+    X0 = torch.randn(4, 30, 3, generator=g, dtype=torch.float64)
+    th0 = torch.tensor([0.9, 0.2, 0.5], dtype=torch.float64)
+    R = torch.stack([-(1.0 * x + 0.1 + 0.3 * x ** 3) for x in X0])
+    model = ToyModel()
+    th = th0.clone().requires_grad_(True)
+    X = X0.clone().requires_grad_(True)
+    U = autodiff.energy_batch(model, X, th)
+    (gX,) = torch.autograd.grad(U.sum(), X, create_graph=True)
+    loss = ((gX + R) ** 2).mean()
+    loss.backward()
+    tr = th0.clone().requires_grad_(True)
+    loss2 = 0.0
+    for x, r in zip(X0, R):
+        xr = x.clone().requires_grad_(True)
+        (gx,) = torch.autograd.grad(_toy_u(xr, tr), xr, create_graph=True)
+        loss2 = loss2 + ((gx + r) ** 2).mean()
+    (loss2 / len(X0)).backward()
+    assert loss.item() == pytest.approx(loss2.item() / len(X0), rel=1e-13)
+    torch.testing.assert_close(th.grad, tr.grad, rtol=1e-12, atol=1e-14)
+    torch.testing.assert_close(U, torch.stack([_toy_u(x, th0) for x in X0]), rtol=1e-13, atol=1e-13)

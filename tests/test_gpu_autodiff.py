@@ -225,3 +225,147 @@ def test_force_matching_double_backward(orc, precision):
         loss2 = loss2 + ((F - torch.as_tensor(Fr, device=m.s.device)) ** 2).mean()
     (loss2 / len(snaps)).backward()
     np.testing.assert_allclose(theta2.grad.cpu().numpy(), g, rtol=1e-12, atol=0)
+
+
+def _oracle_threaded_forces(orc, w, theta, fp32):
+    pairs = _with_theta(w["pairs"], theta)
+    try:
+        return orc.forces(w["x"], w["types"], 2, orc.pair_table(2, pairs), w["box"], fp32=fp32, threaded=True)["F"]
+    except Exception:  # no OpenMP build on this host: the serial oracle (same arithmetic)
+        return orc.forces(w["x"], w["types"], 2, orc.pair_table(2, pairs), w["box"], fp32=fp32)["F"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_force_matching_double_backward_64_snapshots_of_20k(orc, precision):
+    """The differentiable case as stated: 64 seeded snapshots of 20,000
+    particles (A:B 1:1, density 0.4), loss = mean over snapshots of the mean
+    squared force error against oracle forces at theta_ref = (1, 1, 1),
+    gradient at theta0 through autodiff.energy and a double backward, every
+    evaluation enqueued without host synchronisation.  Against central
+    differences of the oracle's loss with h = 1e-5: at this size some reactive
+    pairs always lie within h of r_min, where dF/dsigma jumps, but over 1.3 M
+    particles their share is small -- the difference quotients at h = 1e-4,
+    1e-5 and 1e-6 agree to 8e-6 (sigma) and 1e-8 (lambda, eps) relative."""
+    import torch
+    from paper_1912_08569_gb300 import autodiff
+
+    h, fp32 = 1e-5, precision == "fp32"
+    theta_ref, theta0 = (1.0, 1.0, 1.0), [1.3, 0.9, 1.02]
+    snaps = [inputs.workload("mix100k", n=20000, density=0.4, seed=100 + k, shift=0) for k in range(64)]
+    refs = [_oracle_threaded_forces(orc, w, theta_ref, fp32) for w in snaps]
+    m = _model(snaps[0], precision)
+    dev = m.s.device
+    theta = torch.tensor(theta0, dtype=torch.float64, device=dev, requires_grad=True)
+    loss = 0.0
+    for w, Fr in zip(snaps, refs):
+        m.types = torch.as_tensor(w["types"], device=dev)
+        x = torch.tensor(w["x"], dtype=torch.float64, device=dev, requires_grad=True)
+        (gx,) = torch.autograd.grad(autodiff.energy(m, x, theta), x, create_graph=True)
+        loss = loss + ((-gx - torch.as_tensor(Fr, device=dev)) ** 2).mean()
+    loss = loss / len(snaps)
+    loss.backward()
+    m.check()  # nothing latched on the device (list rows, non-finite forces)
+    g = theta.grad.cpu().numpy()
+
+    def oracle_loss(th):
+        return np.mean([np.mean((_oracle_threaded_forces(orc, w, th, fp32) - Fr) ** 2)
+                        for w, Fr in zip(snaps, refs)])
+
+    L0 = oracle_loss(theta0)
+    assert abs(loss.item() - L0) <= (1e-10 if precision == "fp64" else 1e-4) * L0
+    tol = {"fp64": 1e-5, "fp32": 1e-3}[precision]
+    for k in range(3):
+        tp, tm = list(theta0), list(theta0)
+        tp[k] += h
+        tm[k] -= h
+        fd = (oracle_loss(tp) - oracle_loss(tm)) / (2 * h)
+        assert abs(g[k] - fd) <= tol * (abs(fd) + 1e-3 * L0), (k, g[k], fd)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_eval_grad_equals_host_driven_path(precision):
+    """swp_eval_grad (theta and positions from device memory, nothing read
+    back) against swp_set_pair + swp_set_state + swp_compute_forces +
+    swp_param_grad on the same inputs: the same coefficients reach the same
+    kernels, so energy, forces and derivatives agree bit for bit; several
+    thetas in a row on one context, then an ordinary run that must take the
+    host coefficients again."""
+    import torch
+    from paper_1912_08569_gb300 import _abi as A
+
+    wl = _wl(n=3000, seed=8)
+    m = _model(wl, precision)
+    dev = m.s.device
+    x = torch.tensor(wl["x"], dtype=torch.float64, device=dev)
+    for theta in [(1.0, 1.0, 1.0), (2.0, 0.8, 1.05), (0.5, 1.2, 0.95)]:
+        U, F, dU, dF = m.evaluate(x, torch.tensor(theta, dtype=torch.float64, device=dev))
+        h = make_gpu(dict(wl, pairs=_with_theta(wl["pairs"], theta)), precision)
+        h.compute_forces()
+        th = h.thermo()
+        dF_h = torch.empty((3, wl["n"], 3), dtype=torch.float64, device=dev)
+        dU_h = A.swp_param_grad(h.ctx, 0, 1, dF_h)
+        assert U.item() == th["U2"] + th["U3"], (theta, U.item(), th["U2"] + th["U3"])
+        np.testing.assert_array_equal(F.cpu().numpy(), h.forces())
+        np.testing.assert_array_equal(dU.cpu().numpy(), np.asarray(dU_h))
+        np.testing.assert_array_equal(dF.cpu().numpy(), dF_h.cpu().numpy())
+        h.close()
+    m.check()
+    # an ordinary evaluation afterwards uses the coefficients of swp_set_pair (theta = 1, 1, 1)
+    m.s.set_state(wl["x"], None, wl["types"])
+    m.s.compute_forces()
+    U1, _, _, _ = m.evaluate(x, torch.tensor((1.0, 1.0, 1.0), dtype=torch.float64, device=dev), want_grad=False)
+    th = m.s.thermo()
+    assert th["U2"] + th["U3"] == U1.item()
+
+
+def test_eval_grad_latches_out_of_range_types():
+    import torch
+    from paper_1912_08569_gb300 import _abi as A
+
+    wl = _wl(n=800, seed=9)
+    m = _model(wl, "fp32")
+    dev = m.s.device
+    bad = torch.as_tensor(wl["types"], device=dev).clone()
+    bad[5] = 7
+    m.types = bad
+    m.evaluate(torch.tensor(wl["x"], dtype=torch.float64, device=dev),
+               torch.tensor((1.0, 1.0, 1.0), dtype=torch.float64, device=dev))
+    with pytest.raises(A.SwpError) as e:
+        m.check()
+    assert e.value.code == A.SWP_ERR_INVALID and "type" in str(e.value)
+    # the context recovers with a valid state
+    m.types = torch.as_tensor(wl["types"], device=dev)
+    m.evaluate(torch.tensor(wl["x"], dtype=torch.float64, device=dev),
+               torch.tensor((1.0, 1.0, 1.0), dtype=torch.float64, device=dev))
+    m.check()
+
+
+def test_energy_batch_matches_per_snapshot_energy():
+    """The batched Function (one autograd node for S snapshots) gives the
+    per-snapshot Function's energies bit for bit and its force-matching
+    gradient to rounding."""
+    import torch
+    from paper_1912_08569_gb300 import autodiff
+
+    snaps = [_wl(n=1500, seed=60 + k) for k in range(5)]
+    m = _model(snaps[0], "fp32")
+    dev = m.s.device
+    R = torch.stack([torch.as_tensor(w["x"] * 0.0 + 0.1, device=dev) for w in snaps])
+    theta0 = (1.3, 0.9, 1.02)
+    X = torch.stack([torch.tensor(w["x"], dtype=torch.float64, device=dev) for w in snaps]).requires_grad_(True)
+    th = torch.tensor(theta0, dtype=torch.float64, device=dev, requires_grad=True)
+    U = autodiff.energy_batch(m, X, th)
+    (gX,) = torch.autograd.grad(U.sum(), X, create_graph=True)
+    ((gX + R) ** 2).mean().backward()
+    t2 = torch.tensor(theta0, dtype=torch.float64, device=dev, requires_grad=True)
+    loss2, U2 = 0.0, []
+    for k in range(len(snaps)):
+        x = X[k].detach().clone().requires_grad_(True)
+        u = autodiff.energy(m, x, t2)
+        U2.append(u.detach())
+        (gx,) = torch.autograd.grad(u, x, create_graph=True)
+        loss2 = loss2 + ((gx + R[k]) ** 2).mean()
+    (loss2 / len(snaps)).backward()
+    m.check()
+    np.testing.assert_array_equal(U.detach().cpu().numpy(), torch.stack(U2).cpu().numpy())
+    np.testing.assert_allclose(th.grad.cpu().numpy(), t2.grad.cpu().numpy(), rtol=1e-12, atol=0)
