@@ -657,7 +657,9 @@ def run_batch(a):
                                       f"(total {int(n_total)}), density 0.2-0.6, lambda in {{0,0.5,1,2,5}}, "
                                       f"kT 0.03-0.2, BAOAB gamma=1 dt=0.001, skin 0.3",
                           "systems": len(wls), "particles": int(n_total), "md_steps_per_step": a.md_steps,
-                          "split": tune[1], "l2": "flushed (512 MB write) between timed launches",
+                          "split": tune[1], "block_threads": tune[2],
+                          "autotune_ms_per_200_steps": {f"{th}x{sp:g}": round(ms, 3) for th, sp, ms in tune[3]},
+                          "l2": "flushed (512 MB write) between timed launches",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps, "clocks": clk,
                "kernel_digest": _kernel_digest()}

@@ -51,7 +51,7 @@ extern "C" {
 #define SWP_API
 #endif
 
-#define SWP_ABI_VERSION 4
+#define SWP_ABI_VERSION 5
 
 /* Status codes. */
 #define SWP_OK 0
@@ -193,18 +193,28 @@ SWP_API int swp_step_nvt(swp_ctx* ctx, double dt, double kT, double gamma, int n
  * blocks of its own (its device-side barriers span only those blocks); the
  * others run on one block each, packed heaviest first onto the least-loaded
  * block, a block advancing its systems one after the other.  split > 0
- * (1.0 is a good default; tune it by timing).
+ * (1.0 is a good default; tune it by timing).  A group has at most
+ * min(threads, 304) blocks.
+ *
+ * Block shape: threads per block of the batched kernel, 1024 (0 selects it;
+ * 64 registers per thread, one block per SM), or in FP32 512 (128 registers),
+ * 384 or 256 (as many registers as the kernel uses: no spills), one block per
+ * SM each: smaller blocks give each thread more registers and a small system
+ * fewer idle threads, larger ones more warps per SM.  Tune it by timing with
+ * the split.
  *
  * ws: device scratch of at least swp_batch_workspace_size(n_systems) bytes,
  * owned by the caller and used until the launch completes.  Enqueued on the
  * shared stream; errors of system r (timeout, list overflow) are latched in
  * system r and reported by swp_sync(ctx[r]): on SWP_ERR_NLIST_OVERFLOW that
  * system completed thermo.steps_done steps (the others are unaffected).
- * Errors: SWP_ERR_INVALID (bad arguments, mixed precision/device/stream, ws
- * too small, more large systems than blocks), SWP_ERR_STATE, SWP_ERR_CUDA. */
+ * Errors: SWP_ERR_INVALID (bad arguments, mixed precision/device/stream, a
+ * block shape the precision does not have, ws too small, more large systems
+ * than blocks), SWP_ERR_STATE, SWP_ERR_CUDA. */
 SWP_API size_t swp_batch_workspace_size(int n_systems);
 SWP_API int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const double* kT,
-                           const double* gamma, int nsteps, double split, void* ws, size_t ws_bytes);
+                           const double* gamma, int nsteps, double split, int threads, void* ws,
+                           size_t ws_bytes);
 
 /* Wait for the stream and report latched device errors. */
 SWP_API int swp_sync(swp_ctx* ctx);

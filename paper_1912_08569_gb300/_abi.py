@@ -128,7 +128,7 @@ def load_library(path: str = LIB_PATH):
         "swp_set_bonds": ([c_void_p, c_int, c_void_p, c_double, c_double], c_int),
         "swp_batch_workspace_size": ([c_int], c_size_t),
         "swp_batch_step": ([P(c_void_p), c_int, P(c_double), P(c_double), P(c_double), c_int, c_double,
-                            c_void_p, c_size_t], c_int),
+                            c_int, c_void_p, c_size_t], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -331,12 +331,13 @@ def swp_batch_workspace_size(n_systems: int) -> int:
     return int(load_library().swp_batch_workspace_size(int(n_systems)))
 
 
-def swp_batch_step(ctxs, dt, kT, gamma, nsteps: int, split: float, ws_ptr: int, ws_bytes: int):
-    """One launch advancing every context in ctxs nsteps steps (per-system dt, kT, gamma)."""
+def swp_batch_step(ctxs, dt, kT, gamma, nsteps: int, split: float, ws_ptr: int, ws_bytes: int, threads: int = 0):
+    """One launch advancing every context in ctxs nsteps steps (per-system dt, kT, gamma);
+    threads: the batched kernel's block shape (0: 1024)."""
     m = len(ctxs)
     arr = (ctypes.c_void_p * m)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
     f = lambda v: (ctypes.c_double * m)(*[float(x) for x in v])
-    rc = load_library().swp_batch_step(arr, m, f(dt), f(kT), f(gamma), int(nsteps), float(split),
+    rc = load_library().swp_batch_step(arr, m, f(dt), f(kT), f(gamma), int(nsteps), float(split), int(threads),
                                        ctypes.c_void_p(ws_ptr), int(ws_bytes))
     return _check(ctxs[0] if m else None, rc, "swp_batch_step")
 

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <string>
 #include <utility>
+#include <type_traits>
 #include <vector>
 
 #include "swp_internal.h"
@@ -559,7 +560,8 @@ struct BatchPlan {
     std::vector<int4> items;    // (system, rank, group size, 0)
 };
 
-int plan_batch(const std::vector<long long>& w, int B, double split, BatchPlan& plan)
+// gmax: the largest group (blocks given to one system).
+int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, BatchPlan& plan)
 {
     const int m = (int)w.size();
     long long W = 0;
@@ -572,7 +574,7 @@ int plan_batch(const std::vector<long long>& w, int B, double split, BatchPlan& 
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
     for (int r : order)
         if ((double)w[r] > split * T) {
-            g[r] = std::max(1, (int)std::llround((double)w[r] / T));
+            g[r] = std::min(gmax, std::max(1, (int)std::llround((double)w[r] / T)));
             used += g[r];
         }
     bool small = false;
@@ -593,7 +595,7 @@ int plan_batch(const std::vector<long long>& w, int B, double split, BatchPlan& 
         while (used < B) {
             int best = -1;
             for (int r = 0; r < m; r++)
-                if (g[r] > 0 && g[r] < kMaxGrid && (best < 0 || (double)w[r] / g[r] > (double)w[best] / g[best]))
+                if (g[r] > 0 && g[r] < gmax && (best < 0 || (double)w[r] / g[r] > (double)w[best] / g[best]))
                     best = r;
             if (best < 0) break;
             g[best]++;
@@ -632,21 +634,55 @@ size_t batch_bytes(int m, size_t dev_size)
            align256(sizeof(int4) * (m + kMaxGrid));
 }
 
+// The block shapes of the batched kernel: 1024 threads in both precisions,
+// 512, 384 and 256 in FP32.
+bool batch_shape_ok(int precision, int threads)
+{
+    return threads == 1024 || (precision == SWP_FP32 && (threads == 512 || threads == 384 || threads == 256));
+}
+
+template <typename Real>
+cudaError_t batch_occupancy_shape(int threads, int* bps)
+{
+    if constexpr (std::is_same<Real, float>::value) {
+        if (threads == 512) return batch_occupancy_512(Prec<float>(), bps);
+        if (threads == 384) return batch_occupancy_384(Prec<float>(), bps);
+        if (threads == 256) return batch_occupancy_256(Prec<float>(), bps);
+    }
+    return batch_occupancy_1024(Prec<Real>(), bps);
+}
+
+template <typename Real>
+cudaError_t launch_batch_shape(int threads, const Dev<Real>* devs, const RunArgs* args, const int* ofs,
+                               const int4* items, int uni, int bonds, int grid, cudaStream_t s)
+{
+    if constexpr (std::is_same<Real, float>::value) {
+        if (threads == 512) return launch_batch_512(devs, args, ofs, items, uni, bonds, grid, s);
+        if (threads == 384) return launch_batch_384(devs, args, ofs, items, uni, bonds, grid, s);
+        if (threads == 256) return launch_batch_256(devs, args, ofs, items, uni, bonds, grid, s);
+    }
+    return launch_batch_1024(devs, args, ofs, items, uni, bonds, grid, s);
+}
+
 template <typename Real>
 int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunArgs>& args, double split,
-              void* ws, size_t ws_bytes)
+              int threads, void* ws, size_t ws_bytes)
 {
     swp_ctx* c0 = cs[idx[0]];
     const int m = (int)idx.size();
     int bps = 0;
-    SWP_CUDA(c0, batch_occupancy<Real>(&bps));
+    SWP_CUDA(c0, batch_occupancy_shape<Real>(threads, &bps));
     if (bps < 1) return fail(c0, SWP_ERR_CUDA, "batched step kernel does not fit on an SM");
-    const int B = std::min(kMaxGrid, c0->num_sms * std::min(bps, 2048 / kBlockBatch));
+    const int B = std::min(kMaxGrid, c0->num_sms * std::min(bps, 2048 / threads));
     if (ws_bytes < batch_bytes(m, sizeof(Dev<Real>))) return fail(c0, SWP_ERR_INVALID, "batch workspace too small");
     std::vector<long long> w(m);
-    for (int r = 0; r < m; r++) w[r] = cs[idx[r]]->n;
+    int gmax = threads;  // a group's thermo partials are reduced by one block's threads
+    for (int r = 0; r < m; r++) {
+        w[r] = cs[idx[r]]->n;
+        gmax = std::min(gmax, cs[idx[r]]->max_blocks);  // and fit each system's partials
+    }
     BatchPlan plan;
-    if (plan_batch(w, B, split, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
+    if (plan_batch(w, B, split, gmax, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
     std::vector<Dev<Real>> devs(m);
     int uni = 1, bonds = 0;
     for (int r = 0; r < m; r++) {
@@ -673,7 +709,7 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
                                  c0->stream));
     SWP_CUDA(c0, cudaMemcpyAsync(d_items, plan.items.data(), sizeof(int4) * plan.items.size(),
                                  cudaMemcpyHostToDevice, c0->stream));
-    SWP_CUDA(c0, launch_batch<Real>(d_dev, d_args, d_ofs, d_items, uni, bonds, B, c0->stream));
+    SWP_CUDA(c0, launch_batch_shape<Real>(threads, d_dev, d_args, d_ofs, d_items, uni, bonds, B, c0->stream));
     return SWP_OK;
 }
 
@@ -1026,10 +1062,11 @@ size_t swp_batch_workspace_size(int n_systems)
 }
 
 int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const double* kT,
-                   const double* gamma, int nsteps, double split, void* ws, size_t ws_bytes)
+                   const double* gamma, int nsteps, double split, int threads, void* ws, size_t ws_bytes)
 {
     if (!ctx || n_systems < 1 || !dt || !kT || !gamma || !ws || nsteps < 0 || !(split > 0.0))
         return SWP_ERR_INVALID;
+    if (threads == 0) threads = 1024;
     for (int r = 0; r < n_systems; r++)
         if (!ctx[r]) return SWP_ERR_INVALID;
     swp_ctx* c0 = ctx[0];
@@ -1041,6 +1078,8 @@ int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const d
         if (rc) return rc;
         if (c->precision != c0->precision || c->device != c0->device || c->stream != c0->stream)
             return fail(c0, SWP_ERR_INVALID, "batched systems need one precision, device and stream");
+        if (!batch_shape_ok(c->precision, threads))
+            return fail(c0, SWP_ERR_INVALID, "block shape: 1024 threads, or 512, 384 or 256 in FP32");
         if (!step_params_ok(dt[r], kT[r], gamma[r], nsteps))
             return fail(c, SWP_ERR_INVALID, "need dt > 0, nsteps >= 0, gamma >= 0, kT >= 0");
         for (int q = 0; q < r; q++)
@@ -1050,8 +1089,8 @@ int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const d
         args.push_back(step_args(dt[r], kT[r], gamma[r], nsteps));
     }
     if (idx.empty() || nsteps == 0) return SWP_OK;
-    return c0->precision == SWP_FP64 ? batch_run<double>(ctx, idx, args, split, ws, ws_bytes)
-                                     : batch_run<float>(ctx, idx, args, split, ws, ws_bytes);
+    return c0->precision == SWP_FP64 ? batch_run<double>(ctx, idx, args, split, threads, ws, ws_bytes)
+                                     : batch_run<float>(ctx, idx, args, split, threads, ws, ws_bytes);
 }
 
 int swp_sync(swp_ctx* c)

@@ -197,12 +197,20 @@ template <typename Real>
 cudaError_t run_occupancy(int block, int* blocks_per_sm);
 // Batched launch (k_batch): per-system device structures and run arguments in
 // device memory; block b runs items[item_ofs[b] .. item_ofs[b + 1]), each
-// (system, rank in its group, group size, unused).
+// (system, rank in its group, group size, unused).  One launcher per block
+// shape (threads per block): 1024 in both precisions, 512, 384 and 256 in FP32;
+// batch_occupancy_<T> gives the blocks per SM of that shape.
 template <typename Real>
-cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
-                         int uni, int bonds, int grid, cudaStream_t s);
-template <typename Real>
-cudaError_t batch_occupancy(int* blocks_per_sm);
+struct Prec {};
+#define SWP_DECLARE_BATCH(R, T)                                                                             \
+    cudaError_t launch_batch_##T(const Dev<R>* devs, const RunArgs* args, const int* item_ofs,              \
+                                 const int4* items, int uni, int bonds, int grid, cudaStream_t s);           \
+    cudaError_t batch_occupancy_##T(Prec<R>, int* blocks_per_sm);
+SWP_DECLARE_BATCH(float, 1024)
+SWP_DECLARE_BATCH(double, 1024)
+SWP_DECLARE_BATCH(float, 512)
+SWP_DECLARE_BATCH(float, 384)
+SWP_DECLARE_BATCH(float, 256)
 // Derivatives with respect to one reactive type pair's (lambda, eps, sigma).
 // theta: (lambda, eps, sigma) in device memory; pc < 0: the control block's
 // current snapshot set; dU (device, may be null): dU/dtheta from the sums.

@@ -15,10 +15,12 @@
 // r_min, vh' = -v'/eps_hat, so the total force of a reactive pair is the
 // two-body force times (1 - dU3/dvh_ij / eps_hat).
 //
-// This file is compiled twice (see swp_launch.cuh): with SWP_BATCHED 0 into
-// namespace swp::single (the single-system step kernel and the exchange
-// kernels) and with SWP_BATCHED 1 into swp::batched (the batched kernel), so
-// that the code a group of one block or a group of fewer blocks than
+// This file is compiled several times: with SWP_BATCHED 0 into namespace
+// swp::single (the single-system step kernel and the exchange kernels; see
+// swp_launch.cuh) and with SWP_BATCHED 1 into one namespace per block shape
+// of the batched kernel (SWP_BATCH_NS, SWP_BATCH_THREADS threads per block,
+// SWP_BATCH_MINB blocks per SM in its launch bounds; see swp_batch_impl.cuh),
+// so that the code a group of one block or a group of fewer blocks than
 // thermo quantities needs costs the single-system kernel nothing.
 
 #include "swp_internal.h"
@@ -29,7 +31,10 @@
 
 namespace swp {
 #if SWP_BATCHED
-namespace batched {
+#if !defined(SWP_BATCH_NS) || !defined(SWP_BATCH_THREADS) || !defined(SWP_BATCH_MINB)
+#error "define SWP_BATCH_NS, SWP_BATCH_THREADS and SWP_BATCH_MINB with SWP_BATCHED 1"
+#endif
+namespace SWP_BATCH_NS {
 #else
 namespace single {
 #endif
@@ -45,13 +50,18 @@ constexpr bool kBatched = SWP_BATCHED != 0;
 #define SWP_COLD
 #endif
 // Threads per block.  The batched kernel reads every system's descriptors from
-// shared memory rather than the constant bank, so at 64 registers per thread
-// it spills; 512-thread blocks at 128 registers run without spilling but were
-// measured slower on 256 systems (2.6e9 against 2.8e9 particle-steps/s), so it
-// keeps 1024.  The single-system kernel runs 768 threads (80 registers): its
-// resident step keeps a thread's row, the integrator's state and the pair
-// arithmetic in registers at once.
-constexpr int kThreads = kBatched ? kBlockBatch : kBlock;
+// shared memory rather than the constant bank; its block shapes trade
+// registers per thread (spills at 1024 threads, 64 registers) against warps
+// per SM, and SwapBatch.autotune times them on the batch at hand.  The
+// single-system kernel runs 768 threads (80 registers): its resident step
+// keeps a thread's row, the integrator's state and the pair arithmetic in
+// registers at once.
+#if SWP_BATCHED
+constexpr int kThreads = SWP_BATCH_THREADS;
+constexpr int kMinBlocks = SWP_BATCH_MINB;
+#else
+constexpr int kThreads = kBlock;
+#endif
 
 // ---------------------------------------------------------------------------
 // Group of blocks that advances one system: the whole grid for a single
@@ -482,26 +492,30 @@ __device__ __forceinline__ void warp_part(float x, int q)
 __device__ __forceinline__ void warp_sums_to(double* blk, double* out, double* out2)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (warp < kNQA) {
-        float hi = lane < nw ? s_wpart[warp][lane] : 0.0f, lo = 0.0f;
+    for (int q = warp; q < kNQ; q += nw) {  // quantity q by warp q mod nw (blocks of fewer warps)
+        if (q >= kNQA) {
+            if (out && lane == 0) {
+                out[q] = 0.0;
+                if (out2) out2[q] = 0.0;
+            }
+            continue;
+        }
+        float hi = lane < nw ? s_wpart[q][lane] : 0.0f, lo = 0.0f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
             df_add(hi, lo, h2, l2);
         }
         if (lane == 0) {
-            const double tot = blk[warp] + ((double)hi + (double)lo);
+            const double tot = blk[q] + ((double)hi + (double)lo);
             if (out) {
-                out[warp] = tot;
-                if (out2) out2[warp] = tot;
-                blk[warp] = 0.0;
+                out[q] = tot;
+                if (out2) out2[q] = tot;
+                blk[q] = 0.0;
             } else {
-                blk[warp] = tot;
+                blk[q] = tot;
             }
         }
-    } else if (out && warp == kNQA && lane < kNQ - kNQA) {
-        out[kNQA + lane] = 0.0;
-        if (out2) out2[kNQA + lane] = 0.0;
     }
 }
 
@@ -523,28 +537,32 @@ __device__ __forceinline__ void block_sums(const float* acc, float*, double* blk
 __device__ __forceinline__ void block_sums(const double* acc, double* stage, double* blk, double* out,
                                            double* out2 = nullptr)
 {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, B = blockDim.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, B = blockDim.x, nw = (B + 31) >> 5;
 #pragma unroll
     for (int q = 0; q < kNQA; q++) stage[q * B + t] = acc[q];
     __syncthreads();
-    if (warp < kNQA) {
+    for (int q = warp; q < kNQ; q += nw) {  // quantity q by warp q mod nw
+        if (q >= kNQA) {
+            if (out && lane == 0) {
+                out[q] = 0.0;
+                if (out2) out2[q] = 0.0;
+            }
+            continue;
+        }
         double x = 0.0;
-        for (int k = lane; k < B; k += 32) x += stage[warp * B + k];
+        for (int k = lane; k < B; k += 32) x += stage[q * B + k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) {
-            const double tot = blk[warp] + x;
+            const double tot = blk[q] + x;
             if (out) {
-                out[warp] = tot;
-                if (out2) out2[warp] = tot;
-                blk[warp] = 0.0;
+                out[q] = tot;
+                if (out2) out2[q] = tot;
+                blk[q] = 0.0;
             } else {
-                blk[warp] = tot;
+                blk[q] = tot;
             }
         }
-    } else if (out && warp == kNQA && lane < kNQ - kNQA) {
-        out[kNQA + lane] = 0.0;
-        if (out2) out2[kNQA + lane] = 0.0;
     }
     __syncthreads();
 }
@@ -928,7 +946,8 @@ template <typename Real>
 struct Stage {
     typedef typename Dev<Real>::R4 R4;
     typedef typename Dev<Real>::P4 P4;
-    static constexpr int kWave = sizeof(Real) == 4 ? 8192 : 3072;
+    // entries per wave: 8 (FP32) or 3 (FP64) per thread of a batched block shape
+    static constexpr int kWave = kBatched ? (sizeof(Real) == 4 ? 8 : 3) * kThreads : (sizeof(Real) == 4 ? 8192 : 3072);
     static constexpr size_t B = kThreads;
     static constexpr size_t O_POS = 0;                                  // [B] P4 positions
     static constexpr size_t O_VEL = O_POS + B * sizeof(P4);             // [B] R4 velocities
@@ -1580,12 +1599,12 @@ template <typename Real>
 __device__ __forceinline__ void reduce_small(const Dev<Real>& d)
 {
     if (g_rank() != 0) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < kNQA) {
-        double v = lane < g_size() ? d.partials[(size_t)lane * kNQ + w] : 0.0;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    for (int q = w; q < kNQA; q += nw) {
+        double v = lane < g_size() ? d.partials[(size_t)lane * kNQ + q] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) d.ctl->thermo[w] = v;
+        if (lane == 0) d.ctl->thermo[q] = v;
     }
 }
 
@@ -2491,7 +2510,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
 // item, so the group barriers only ever wait for blocks working on the same
 // system.
 template <typename Real, bool UNI, bool BONDS>
-__global__ void __launch_bounds__(kThreads, 1) k_batch(const Dev<Real>* devs, const RunArgs* args,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_batch(const Dev<Real>* devs, const RunArgs* args,
                                                      const int* item_ofs, const int4* items)
 {
     __shared__ Dev<Real> s_dev;
@@ -2857,5 +2876,5 @@ __global__ void k_eval_prep(Dev<Real> d, int ti, int tj, const double* theta, do
 
 #endif  // !SWP_BATCHED
 
-}  // namespace single / batched
+}  // namespace single / SWP_BATCH_NS
 }  // namespace swp

@@ -7,9 +7,11 @@
 #define SWP_BATCHED 0
 #include "swp_kernels.cuh"
 #undef SWP_BATCHED
-#define SWP_BATCHED 1
-#include "swp_kernels.cuh"
-#undef SWP_BATCHED
+// the batched kernel's 1024-thread shape (both precisions)
+#define SWP_BATCH_NS batched1024
+#define SWP_BATCH_THREADS 1024
+#define SWP_BATCH_MINB 1
+#include "swp_batch_impl.cuh"
 
 namespace swp {
 using single::Stage;
@@ -58,47 +60,6 @@ cudaError_t run_occupancy(int block, int* blocks_per_sm)
         int b = 0;
         e = prepare_fn<Real>(fn);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, run_smem_bytes<Real>());
-        best = b < best ? b : best;
-    }
-    *blocks_per_sm = best;
-    return e;
-}
-
-template <typename Real>
-static void* batch_fn(int uni, int bonds = 0)
-{
-    if (bonds) return uni ? (void*)batched::k_batch<Real, true, true> : (void*)batched::k_batch<Real, false, true>;
-    return uni ? (void*)batched::k_batch<Real, true, false> : (void*)batched::k_batch<Real, false, false>;
-}
-
-template <typename Real>
-static size_t batch_smem_bytes()
-{
-    return batched::Stage<Real>::kBytes;
-}
-
-template <typename Real>
-cudaError_t launch_batch(const Dev<Real>* devs, const RunArgs* args, const int* item_ofs, const int4* items,
-                         int uni, int bonds, int grid, cudaStream_t s)
-{
-    void* fn = batch_fn<Real>(uni, bonds);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<Real>());
-    if (e != cudaSuccess) return e;
-    void* kargs[] = {(void*)&devs, (void*)&args, (void*)&item_ofs, (void*)&items};
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlockBatch), kargs, batch_smem_bytes<Real>(), s);
-}
-
-template <typename Real>
-cudaError_t batch_occupancy(int* blocks_per_sm)
-{
-    const int sm = (int)batch_smem_bytes<Real>();
-    int best = 1 << 30;
-    cudaError_t e = cudaSuccess;
-    for (int v = 0; v < 4 && e == cudaSuccess; v++) {  // every (uniform, bonds) variant
-        void* fn = batch_fn<Real>(v & 1, v >> 1);
-        int b = 0;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBlockBatch, sm);
         best = b < best ? b : best;
     }
     *blocks_per_sm = best;
@@ -176,9 +137,7 @@ cudaError_t launch_eval_prep(const Dev<Real>& d, int ti, int tj, const double* t
     template cudaError_t launch_get_state<R>(const Dev<R>&, int, int, cudaStream_t);             \
     template cudaError_t launch_get_forces<R>(const Dev<R>&, int, cudaStream_t);                 \
     template cudaError_t launch_get_nlist<R>(const Dev<R>&, int, int*, int*, int, cudaStream_t); \
-    template cudaError_t launch_batch<R>(const Dev<R>*, const RunArgs*, const int*, const int4*, int, int, int, \
-                                         cudaStream_t);                                                   \
-    template cudaError_t batch_occupancy<R>(int*);                                               \
+    SWP_BATCH_DEFINE(R)                                                                          \
     template cudaError_t launch_param_grad<R>(const Dev<R>&, int, double*, double*, const double*, double*, \
                                               double*, double*, cudaStream_t);                            \
     template cudaError_t launch_eval_prep<R>(const Dev<R>&, int, int, const double*, double, double, double, \

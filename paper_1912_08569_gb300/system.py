@@ -234,10 +234,13 @@ class SwapBatch:
 
     The systems may differ in size, box, coefficients and temperature; they
     share precision, device and stream.  ``split`` sets which systems get
-    blocks of their own (see swp_batch_step); ``autotune`` picks it by timing.
+    blocks of their own and ``threads`` the batched kernel's block shape (see
+    swp_batch_step); ``autotune`` picks both by timing.
     """
 
-    def __init__(self, systems, split: float = 1.0):
+    SHAPES = {A.SWP_FP32: (1024, 512, 384, 256), A.SWP_FP64: (1024,)}  # threads per block
+
+    def __init__(self, systems, split: float = 1.0, threads: int = 1024):
         import torch
 
         self.systems = list(systems)
@@ -251,6 +254,7 @@ class SwapBatch:
                 raise ValueError("batched systems need one precision")
         self.torch = torch
         self.split = float(split)
+        self.threads = int(threads)
         nb = A.swp_batch_workspace_size(len(self.systems))
         self.ws = torch.empty(nb, dtype=torch.uint8, device=s0.device)
 
@@ -266,7 +270,7 @@ class SwapBatch:
         """Advance every system nsteps steps (per-system or common dt, kT, gamma)."""
         dt, kT, gamma = self._per(dt), self._per(kT), self._per(gamma)
         A.swp_batch_step([s.ctx for s in self.systems], dt, kT, gamma, int(nsteps), self.split,
-                         self.ws.data_ptr(), self.ws.numel())
+                         self.ws.data_ptr(), self.ws.numel(), self.threads)
         if not sync:
             return
         for k, s in enumerate(self.systems):
@@ -284,21 +288,26 @@ class SwapBatch:
         for s in self.systems:
             A.swp_sync(s.ctx)
 
-    def autotune(self, nsteps: int, dt, kT=0.0, gamma=0.0, splits=(0.5, 1.0, 2.0, 4.0, 1e9)):
-        """Times one nsteps run per candidate split (the systems advance) and keeps the fastest."""
+    def autotune(self, nsteps: int, dt, kT=0.0, gamma=0.0, splits=(0.5, 1.0, 2.0, 4.0, 1e9), shapes=None):
+        """Times one nsteps run per (block shape, split) candidate -- every
+        shape the precision has, by default -- with the systems advancing, and
+        keeps the fastest; returns (ms, split, threads, table of every timing)."""
         t = self.torch
-        best = None
-        for sp in splits:
-            self.split = float(sp)
-            self.run(1, dt, kT, gamma)  # warm-up (and list builds for the new grouping)
-            e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
-            stream = self.systems[0].stream
-            e0.record(stream)
-            self.run(nsteps, dt, kT, gamma, sync=False)
-            e1.record(stream)
-            self.sync()
-            ms = e0.elapsed_time(e1)
-            if best is None or ms < best[0]:
-                best = (ms, float(sp))
-        self.split = best[1]
-        return best
+        shapes = self.SHAPES[self.systems[0].precision] if shapes is None else shapes
+        best, table = None, []
+        for th in shapes:
+            for sp in splits:
+                self.threads, self.split = int(th), float(sp)
+                self.run(1, dt, kT, gamma)  # warm-up (and list builds for the new grouping)
+                e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+                stream = self.systems[0].stream
+                e0.record(stream)
+                self.run(nsteps, dt, kT, gamma, sync=False)
+                e1.record(stream)
+                self.sync()
+                ms = e0.elapsed_time(e1)
+                table.append((int(th), float(sp), ms))
+                if best is None or ms < best[0]:
+                    best = (ms, float(sp), int(th))
+        self.split, self.threads = best[1], best[2]
+        return best + (table,)

@@ -7,7 +7,9 @@ run of the same system from the same seeded inputs, with the tolerances of
 the single-system trajectory tests.  Both work splits are covered: every
 system on blocks of its own (groups of several blocks, group barriers) and
 every system packed onto single blocks (block-local barriers, several systems
-per block).
+per block), with every block shape of the batched kernel (1024, 512, 384 and
+256 threads per block in FP32, 1024 in FP64); a shape the precision lacks is
+refused.
 """
 import numpy as np
 import pytest
@@ -45,15 +47,17 @@ def _min_image(d, box):
     return d - box * np.round(d / box)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision,threads", [("fp32", 1024), ("fp32", 512), ("fp32", 384), ("fp32", 256),
+                                               ("fp64", 1024)])
 @pytest.mark.parametrize("split", [0.5, 1e9])
-def test_batch_matches_oracle_per_system(orc, precision, split):
+def test_batch_matches_oracle_per_system(orc, precision, threads, split):
+    """Every block shape of the batched kernel, both work splits."""
     from paper_1912_08569_gb300 import SwapBatch
 
     wls = [_wl(*p) for p in SYSTEMS]
     systems = [make_gpu(wl, precision) for wl in wls]
     kT = [p[3] for p in SYSTEMS]
-    batch = SwapBatch(systems, split=split)
+    batch = SwapBatch(systems, split=split, threads=threads)
     dt, nsteps = 0.001, 20
     batch.run(nsteps, dt, kT, 1.0)
     fp32 = precision == "fp32"
@@ -113,3 +117,14 @@ def test_batch_rejects_mixed_precision():
     wls = [_wl(*p) for p in SYSTEMS[:2]]
     with pytest.raises(ValueError):
         SwapBatch([make_gpu(wls[0], "fp32"), make_gpu(wls[1], "fp64")])
+
+
+def test_batch_rejects_missing_block_shape():
+    from paper_1912_08569_gb300 import SwapBatch
+    from paper_1912_08569_gb300 import _abi as A
+
+    systems = [make_gpu(_wl(*p), "fp64") for p in SYSTEMS[:2]]
+    for threads in (512, 300):
+        with pytest.raises(A.SwpError) as e:
+            SwapBatch(systems, threads=threads).run(1, 0.001, 0.1, 1.0)
+        assert e.value.code == A.SWP_ERR_INVALID

@@ -29,7 +29,7 @@ class FakeLib:
     def swp_compute_forces(self, ctx):
         self.calls.append(("forces", ctx))
 
-    def swp_batch_step(self, ctxs, dt, kT, gamma, nsteps, split, ws, nbytes):
+    def swp_batch_step(self, ctxs, dt, kT, gamma, nsteps, split, ws, nbytes, threads=0):
         self.calls.append(("batch", tuple(ctxs), int(nsteps)))
 
     def swp_sync(self, ctx):
@@ -106,7 +106,7 @@ def test_batch_overflowing_system_finishes_alone(fake):
                {"b": types.SimpleNamespace(steps_done=120, max_row=80)})
     systems = [_system(k) for k in ("a", "b", "c")]
     batch = object.__new__(S.SwapBatch)
-    batch.systems, batch.split = systems, 1.0
+    batch.systems, batch.split, batch.threads = systems, 1.0, 1024
     batch.ws = types.SimpleNamespace(data_ptr=lambda: 0, numel=lambda: 0)
     batch.run(500, 0.001, [0.1, 0.2, 0.3], 1.0)
     assert lib.calls[0] == ("batch", ("a", "b", "c"), 500)
