@@ -506,6 +506,20 @@ int run(swp_ctx* c, RunArgs a)
     if (c->bps_req > 0) bps = std::min(bps, c->bps_req);
     bps = std::min(bps, c->max_blocks / std::max(c->num_sms, 1));
     c->grid = step_grid(c, bps);
+    // a bonded network runs the 1024-thread kernel (two-barrier step: more
+    // warps hide its global gathers; 434 against 500 us per step on the 2M-bead
+    // network), everything else the 768-thread one (the resident step where it
+    // applies; at 1M-2M unbonded particles the two shapes are within 3 %, the
+    // 768-thread one ahead)
+    const bool wide = !c->bond_host.empty();
+    if (wide) {
+        int bw = 0;
+        SWP_CUDA(c, run_occupancy_wide<Real>(&bw));
+        if (bw < 1) return fail(c, SWP_ERR_CUDA, "step kernel does not fit on an SM");
+        if (c->bps_req > 0) bw = std::min(bw, c->bps_req);
+        bw = std::min(bw, c->max_blocks / std::max(c->num_sms, 1));
+        c->grid = step_grid(c, bw);
+    }
     if (!c->table_only && c->table_theta) {  // an ordinary run takes the host coefficients again
         c->table_dirty = true;
         c->table_theta = false;
@@ -518,7 +532,8 @@ int run(swp_ctx* c, RunArgs a)
     if (c->table_only) a.uni = 0;  // the device table holds coefficients the host copy does not
     c->withhold = 0;  // one launch consumes the request
     SWP_CUDA(c, cudaMemsetAsync(&d.ctl->barrier, 0, sizeof(unsigned long long), c->stream));
-    SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
+    if (wide) SWP_CUDA(c, launch_run_wide<Real>(d, a, c->grid, c->stream));
+    else SWP_CUDA(c, launch_run<Real>(d, a, c->grid, kBlock, c->stream));
     return SWP_OK;
 }
 

@@ -14,6 +14,7 @@ constexpr int kTypeBits = 4;       // packed word: (tag << kTypeBits) | type
 constexpr int kBlock = 768;        // threads per block of the step kernel (one block per SM, 80 registers)
 constexpr int kMaxGrid = 320;      // largest grid of the step kernel (blocks)
 constexpr int kBlockBatch = 1024;  // threads per block of the batched kernel
+constexpr int kBlockWide = 1024;   // threads per block of the step kernel of bonded networks
 constexpr int kMaxBonds = 4;       // harmonic bonds per particle (chains: 2)
 constexpr int kMaxTag = (1 << 27); // tags must fit in 27 bits (sign bit stays clear)
 
@@ -195,6 +196,11 @@ template <typename Real>
 cudaError_t launch_run(const Dev<Real>& d, const RunArgs& a, int grid, int block, cudaStream_t s);
 template <typename Real>
 cudaError_t run_occupancy(int block, int* blocks_per_sm);
+// The 1024-thread step kernel (two-barrier step only), run by bonded networks.
+template <typename Real>
+cudaError_t launch_run_wide(const Dev<Real>& d, const RunArgs& a, int grid, cudaStream_t s);
+template <typename Real>
+cudaError_t run_occupancy_wide(int* blocks_per_sm);
 // Batched launch (k_batch): per-system device structures and run arguments in
 // device memory; block b runs items[item_ofs[b] .. item_ofs[b + 1]), each
 // (system, rank in its group, group size, unused).  One launcher per block

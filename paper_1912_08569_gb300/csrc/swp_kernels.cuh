@@ -29,12 +29,26 @@
 #error "define SWP_BATCHED (0 or 1) before including swp_kernels.cuh"
 #endif
 
+// With SWP_BATCHED 0 and SWP_WIDE 1 it is compiled into namespace swp::wide:
+// the single-system step kernel with 1024-thread blocks (two-barrier step
+// only), which bonded networks run: their gathers' latency is hidden better
+// with more warps.  That copy leaves out the resident step and the exchange
+// kernels.
+#undef SWP_HAS_RESIDENT
+#if !SWP_BATCHED && !SWP_WIDE
+#define SWP_HAS_RESIDENT 1
+#else
+#define SWP_HAS_RESIDENT 0
+#endif
+
 namespace swp {
 #if SWP_BATCHED
 #if !defined(SWP_BATCH_NS) || !defined(SWP_BATCH_THREADS) || !defined(SWP_BATCH_MINB)
 #error "define SWP_BATCH_NS, SWP_BATCH_THREADS and SWP_BATCH_MINB with SWP_BATCHED 1"
 #endif
 namespace SWP_BATCH_NS {
+#elif SWP_WIDE
+namespace wide {
 #else
 namespace single {
 #endif
@@ -59,6 +73,8 @@ constexpr bool kBatched = SWP_BATCHED != 0;
 #if SWP_BATCHED
 constexpr int kThreads = SWP_BATCH_THREADS;
 constexpr int kMinBlocks = SWP_BATCH_MINB;
+#elif SWP_WIDE
+constexpr int kThreads = kBlockWide;
 #else
 constexpr int kThreads = kBlock;
 #endif
@@ -1011,6 +1027,11 @@ __device__ __forceinline__ Real s_term(const Dev<Real>& d, const PairP<Real>* ta
     return r2 < p.rc2 ? mul_rn(p.a, vh) : Real(0);
 }
 
+// Entries per thread whose gathers a two-barrier pass issues together (S
+// pass, force pass).
+constexpr int kGather = 4;
+constexpr int kGatherF = 2;
+
 // staged: the block has one sub-chunk and the shared copies of its positions
 // and list ranges are current (kept by the previous force pass), so they are
 // not loaded again.  With one sub-chunk the block's S values also stay in
@@ -1040,26 +1061,26 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
         Real s = Real(0);
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
-            // the thread's entries e, e + B, ...: the next entry's indices are in
-            // flight while the current entry is evaluated
+            // the thread's entries e, e + B, ... in groups of kGather: the group's
+            // index loads, then its partner gathers, are independent of one
+            // another, so that many are in flight when the partners come from DRAM
             const int B = blockDim.x;
-            int e = wb + t;
-            int j_c = 0, o_c = 0;
-            if (e < we) {
-                j_c = d.ent_j[e];
-                o_c = d.ent_o[e];
-            }
-            while (e < we) {
-                const P4 p_c = pos[j_c];
-                int j_n = 0, o_n = 0;
-                if (e + B < we) {
-                    j_n = d.ent_j[e + B];
-                    o_n = d.ent_o[e + B];
+            for (int e0 = wb + t; e0 < we; e0 += kGather * B) {
+                int jj[kGather], oo[kGather];
+#pragma unroll
+                for (int u = 0; u < kGather; u++) {
+                    const int e = e0 + u * B;
+                    jj[u] = e < we ? d.ent_j[e] : 0;
+                    oo[u] = e < we ? d.ent_o[e] : 0;
                 }
-                SM::w()[e - wb] = s_term<Real, UNI>(d, tab, ps, SM::pos()[o_c], p_c);
-                e += B;
-                j_c = j_n;
-                o_c = o_n;
+                P4 pp[kGather];
+#pragma unroll
+                for (int u = 0; u < kGather; u++) pp[u] = pos[jj[u]];  // slot 0 for a missing entry
+#pragma unroll
+                for (int u = 0; u < kGather; u++) {
+                    const int e = e0 + u * B;
+                    if (e < we) SM::w()[e - wb] = s_term<Real, UNI>(d, tab, ps, SM::pos()[oo[u]], pp[u]);
+                }
             }
             __syncthreads();
             if (t < P) {
@@ -1310,21 +1331,41 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         Real fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;  // reactive and other entries' sums
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
-            for (int e = wb + t; e < we; e += blockDim.x) {
-                const int j_c = d.ent_j[e], o_c = d.ent_o[e];
-                const P4 pj = pos[j_c];
-                const Real sj = e < e_rend ? d.S[j_c] : Real(0);
-                Real ex, ey, ez;
-                if (e < e_rend)
-                    entry_force<Real, UNI, true, TH>(d, tab, SM::pos()[o_c], pj, SM::S()[o_c], sj, ps, acc, ex, ey, ez);
-                else
-                    entry_force<Real, UNI, false, TH>(d, tab, SM::pos()[o_c], pj, Real(0), Real(0), pw, acc, ex, ey, ez);
-                R4 r;
-                r.x = ex;
-                r.y = ey;
-                r.z = ez;
-                r.w = Real(0);
-                SM::w4()[e - wb] = r;
+            // groups of kGatherF entries per thread, their gathers issued together
+            const int B = blockDim.x;
+            for (int e0 = wb + t; e0 < we; e0 += kGatherF * B) {
+                int jj[kGatherF], oo[kGatherF];
+#pragma unroll
+                for (int u = 0; u < kGatherF; u++) {
+                    const int e = e0 + u * B;
+                    jj[u] = e < we ? d.ent_j[e] : 0;
+                    oo[u] = e < we ? d.ent_o[e] : 0;
+                }
+                P4 pj[kGatherF];
+                Real sj[kGatherF];
+#pragma unroll
+                for (int u = 0; u < kGatherF; u++) {
+                    pj[u] = pos[jj[u]];  // slot 0 for a missing entry
+                    sj[u] = e0 + u * B < e_rend ? d.S[jj[u]] : Real(0);
+                }
+#pragma unroll
+                for (int u = 0; u < kGatherF; u++) {
+                    const int e = e0 + u * B;
+                    if (e >= we) continue;
+                    Real ex, ey, ez;
+                    if (e < e_rend)
+                        entry_force<Real, UNI, true, TH>(d, tab, SM::pos()[oo[u]], pj[u], SM::S()[oo[u]], sj[u], ps,
+                                                         acc, ex, ey, ez);
+                    else
+                        entry_force<Real, UNI, false, TH>(d, tab, SM::pos()[oo[u]], pj[u], Real(0), Real(0), pw, acc,
+                                                          ex, ey, ez);
+                    R4 r;
+                    r.x = ex;
+                    r.y = ey;
+                    r.z = ez;
+                    r.w = Real(0);
+                    SM::w4()[e - wb] = r;
+                }
             }
             __syncthreads();
             if (t < P) {
@@ -1635,7 +1676,7 @@ __device__ __forceinline__ void add_disp(Ctl* ctl, long long stp)
     __syncthreads();
 }
 
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
 // ---------------------------------------------------------------------------
 // Resident mode: one system, FP32, no bonds, every block's particles in one
 // sub-chunk (up to blockDim x grid particles).
@@ -2246,7 +2287,7 @@ static __device__ bool r_enter(const Dev<float>& d, const RunArgs& a)
     return true;
 }
 
-#endif  // !SWP_BATCHED
+#endif  // SWP_HAS_RESIDENT
 
 // One system advanced by the group of blocks this block belongs to (g_rank /
 // g_size set by the caller).  Returns false when a wait timed out (the status
@@ -2255,7 +2296,7 @@ template <typename Real, bool UNI, bool BONDS>
 __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 {
     // the resident mode exists for one FP32 system without bonds
-    constexpr bool kRes = !kBatched && sizeof(Real) == 4 && !BONDS;
+    constexpr bool kRes = SWP_HAS_RESIDENT && sizeof(Real) == 4 && !BONDS;
     Ctl* ctl = d.ctl;
     PairP<Real>* tab = (PairP<Real>*)s_tab_raw;
     const int ntt = d.ntypes * d.ntypes;
@@ -2349,7 +2390,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         while (s_ls.rc == 0 && s_ls.state == 2) {
             const long long stp = s_ls.step;
             if (threadIdx.x == 0 && g_rank() == 0) ctl->dmax2[(stp + 1) & 1] = 0u;
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
             if constexpr (kRes) {
                 if (s_ls.r_gathered) {
                     // the halo copies and the displacement read issued after the
@@ -2363,7 +2404,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             if (s_ls.need_rb || 2.0f * s_ls.disp > skin_eff) {
                 // a resident gather issued for this step lands in memory the rebuild reuses
                 cp_async_wait_all();
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
                 if constexpr (kRes)
                     if (s_ls.r_valid) r_flush(d, s_ls.ac);  // the build reorders the global state
 #endif
@@ -2387,7 +2428,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
             const int flags = F_CLOSING | (more ? F_OPENING : F_STORE);
             Acc<Real> acc;
             bool resident = false;
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
             if constexpr (kRes) {
                 if (s_ls.r_try)
                     if (!r_enter(d, a)) return false;
@@ -2441,7 +2482,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
                 if (threadIdx.x == 0) s_ls.pc ^= 1;
                 __syncthreads();
                 bool gathered = false;
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
                 if constexpr (kRes) {
                     if (s_ls.r_valid) {
                         // the displacement read and the next step's copies
@@ -2463,7 +2504,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
         }
     }
     cp_async_wait_all();  // copies issued for a step that did not come
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
     if constexpr (kRes)
         if (s_ls.r_valid) r_flush(d, s_ls.ac);
 #endif
@@ -2496,7 +2537,7 @@ __device__ __forceinline__ bool run_system(const Dev<Real>& d, const RunArgs& a)
 
 #if !SWP_BATCHED
 template <typename Real, bool UNI, bool BONDS>
-__global__ void __launch_bounds__(kBlock, 1) k_run(Dev<Real> d, RunArgs a)
+__global__ void __launch_bounds__(kThreads, 1) k_run(Dev<Real> d, RunArgs a)
 {
     run_system<Real, UNI, BONDS>(d, a);
 }
@@ -2533,7 +2574,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_batch(const Dev<Real>*
 }
 #endif  // SWP_BATCHED
 
-#if !SWP_BATCHED
+#if SWP_HAS_RESIDENT
 // ---------------------------------------------------------------------------
 // Host-exchange kernels (user order <-> slot order).
 
@@ -2874,7 +2915,7 @@ __global__ void k_eval_prep(Dev<Real> d, int ti, int tj, const double* theta, do
     }
 }
 
-#endif  // !SWP_BATCHED
+#endif  // SWP_HAS_RESIDENT
 
-}  // namespace single / SWP_BATCH_NS
+}  // namespace single / wide / SWP_BATCH_NS
 }  // namespace swp
