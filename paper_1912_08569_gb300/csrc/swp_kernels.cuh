@@ -479,7 +479,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
 // cleared.  Each thread holds the terms of one sub-chunk at most (multi-chunk
 // passes flush after every sub-chunk), so the error does not grow with the
 // system size; block partials are summed over blocks in FP64
-// (run_reduce_thermo / reduce_finish).
+// (run_reduce_thermo).
 //
 // FP32 runs: each warp folds its lanes' values by a shuffle tree (at most five
 // roundings of the warp's sum of magnitudes) into s_wpart[q][warp]; warp q
@@ -1070,8 +1070,8 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
 #pragma unroll
                 for (int u = 0; u < kGather; u++) {
                     const int e = e0 + u * B;
-                    jj[u] = e < we ? d.ent_j[e] : 0;
-                    oo[u] = e < we ? d.ent_o[e] : 0;
+                    jj[u] = e < we ? __ldcs(&d.ent_j[e]) : 0;  // streamed: keep L2 for the snapshots
+                    oo[u] = e < we ? __ldcs(&d.ent_o[e]) : 0;
                 }
                 P4 pp[kGather];
 #pragma unroll
@@ -1338,8 +1338,8 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
 #pragma unroll
                 for (int u = 0; u < kGatherF; u++) {
                     const int e = e0 + u * B;
-                    jj[u] = e < we ? d.ent_j[e] : 0;
-                    oo[u] = e < we ? d.ent_o[e] : 0;
+                    jj[u] = e < we ? __ldcs(&d.ent_j[e]) : 0;  // streamed: keep L2 for the snapshots
+                    oo[u] = e < we ? __ldcs(&d.ent_o[e]) : 0;
                 }
                 P4 pj[kGatherF];
                 Real sj[kGatherF];
@@ -1441,6 +1441,8 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         if (TH && !single) {
             // several sub-chunks: fold this one's terms into the block's FP64
             // running sums, so no thread accumulates more than one sub-chunk
+            // (per-warp running sums without the block barriers, tried in FP64
+            // and in double-float, measured slower)
             block_sums(acc.q, SM::w(), blk, (double*)nullptr);
 #pragma unroll
             for (int q = 0; q < kNQA; q++) acc.q[q] = Real(0);
