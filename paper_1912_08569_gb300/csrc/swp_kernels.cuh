@@ -1218,13 +1218,16 @@ __device__ __forceinline__ float integrate_one(const Dev<Real>& d, const RunArgs
         const int n = d.n;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            d.xq[ac][c * n + i] = st.q[c];
+            __stcs(&d.xq[ac][c * n + i], st.q[c]);  // read again only next step: evict first
             if (w[c]) d.img[ac][c * n + i] += w[c];
         }
         d.pos[pc ^ 1][i] = np;
         if (keep) *keep = np;
     }
-    d.vel[ac][i] = v;
+    if constexpr (sizeof(Real) == 4)
+        __stcs((float4*)&d.vel[ac][i], *(const float4*)&v);
+    else
+        d.vel[ac][i] = v;
     return disp2;
 }
 
