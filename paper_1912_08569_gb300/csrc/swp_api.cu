@@ -188,13 +188,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // blocks): partner slots, then owner indices (both int32).
 size_t list_entries(const swp_ctx* c) { return ((size_t)std::max(c->n, 1) + c->max_blocks) * c->max_nn; }
 
-size_t list_bytes(const swp_ctx* c) { return 2 * align256(list_entries(c) * 4); }
+size_t list_bytes(const swp_ctx* c) { return align256(list_entries(c) * 4) + align256(list_entries(c) * 2); }
 
 template <typename Real>
 void set_list(const swp_ctx* c, char* base, Dev<Real>* d)
 {
     d->ent_j = (int*)base;
-    d->ent_o = base ? (int*)(base + align256(list_entries(c) * 4)) : nullptr;
+    d->ent_o = base ? (unsigned short*)(base + align256(list_entries(c) * 4)) : nullptr;
 }
 
 // Carves the workspace; with base == nullptr only measures it.

@@ -138,7 +138,7 @@ struct Dev {
     R4* force;         // (fx, fy, fz, 0)
     Real* S;           // per-centre sum of a*vh over reactive partners
     int* ent_j;            // neighbour entries: partner slot (block-compact layout)
-    int* ent_o;            // neighbour entries: owner's index inside its sub-chunk
+    unsigned short* ent_o; // neighbour entries: owner's index inside its sub-chunk (< 1024)
     int4* pinfo;           // per particle: (first reactive entry, count, first other entry, count)
     const int* cell_rank;  // [2 * ncell]: cell linear index -> rank in the sorted cell order,
                            // then rank -> linear index

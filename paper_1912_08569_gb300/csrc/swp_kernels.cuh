@@ -916,12 +916,12 @@ __device__ int ph_build_cells(const Dev<Real>& d, const PairP<Real>* tab, int pc
                                 if (react) {
                                     const int e = run.x + __popc(br & lt);
                                     d.ent_j[e] = cq[k];
-                                    d.ent_o[e] = i - q0;
+                                    d.ent_o[e] = (unsigned short)(i - q0);
                                 }
                                 if (other) {
                                     const int e = run.y + __popc(bw & lt);
                                     d.ent_j[e] = cq[k];
-                                    d.ent_o[e] = i - q0;
+                                    d.ent_o[e] = (unsigned short)(i - q0);
                                 }
                             }
                             run.x += __popc(br);
