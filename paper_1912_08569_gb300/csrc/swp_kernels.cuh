@@ -2857,17 +2857,23 @@ __global__ void k_pgrad_forces(Dev<Real> d, int pc, const double* sd, const doub
     }
 }
 
-// Pass 3: one block adds the per-block sums in block order into total[4],
-// and forms dU/dtheta from them into dU[3] (when given).
+// Pass 3: one block of four warps adds the per-block sums into total[4] --
+// warp k sums quantity k, lane l the blocks l, l + 32, ... in order, then a
+// fixed shuffle tree -- and forms dU/dtheta from them into dU[3] (when given).
 static __global__ void k_pgrad_total(const double* part, int nblocks, double* total, const double* theta,
                                      double* dU)
 {
     __shared__ double t[4];
-    if (threadIdx.x < 4) {
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k < 4) {
         double v = 0.0;
-        for (int b = 0; b < nblocks; b++) v += part[4 * b + threadIdx.x];
-        total[threadIdx.x] = v;
-        t[threadIdx.x] = v;
+        for (int b = lane; b < nblocks; b += 32) v += part[4 * b + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            total[k] = v;
+            t[k] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0 && dU) {

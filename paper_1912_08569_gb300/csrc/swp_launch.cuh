@@ -118,7 +118,7 @@ cudaError_t launch_param_grad(const Dev<Real>& d, int pc, double* sd, double* pa
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    single::k_pgrad_total<<<1, 32, 0, s>>>(part, blocks, total, theta, dU);
+    single::k_pgrad_total<<<1, 128, 0, s>>>(part, blocks, total, theta, dU);
     return cudaGetLastError();
 }
 
