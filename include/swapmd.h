@@ -51,7 +51,7 @@ extern "C" {
 #define SWP_API
 #endif
 
-#define SWP_ABI_VERSION 5
+#define SWP_ABI_VERSION 6
 
 /* Status codes. */
 #define SWP_OK 0
@@ -188,13 +188,18 @@ SWP_API int swp_step_nvt(swp_ctx* ctx, double dt, double kT, double gamma, int n
  * list buffer and state, and none may appear twice; empty systems are
  * skipped.
  *
- * Work split: with w the particle count of a system and T the mean count per
- * block of the launch, a system with w > split * T gets max(1, round(w / T))
- * blocks of its own (its device-side barriers span only those blocks); the
- * others run on one block each, packed heaviest first onto the least-loaded
- * block, a block advancing its systems one after the other.  split > 0
- * (1.0 is a good default; tune it by timing).  A group has at most
- * min(threads, 304) blocks.
+ * Work split, with w the particle count of a system and a block's load the
+ * particles it advances (a group member: w / group size).  split = 0 (the
+ * balanced plan, the default): the smallest largest load C for which every
+ * system with w > C gets ceil(w / C) blocks (its device-side barriers span
+ * only those blocks; no member share below `threads` particles) and every
+ * other system, heaviest first, goes onto the least-loaded block, group
+ * members included, with no load above C; a block runs its group share
+ * first, then its single-block systems one after the other.  split > 0 (the
+ * threshold plan): with T the mean load, a system with w > split * T gets
+ * max(1, round(w / T)) blocks that run nothing else, the others are packed
+ * the same way onto the remaining blocks.  A group has at most
+ * min(threads, 304) blocks.  swp_batch_plan returns either plan.
  *
  * Block shape: threads per block of the batched kernel, 1024 (0 selects it;
  * 64 registers per thread, one block per SM), or in FP32 512 (128 registers),
@@ -215,6 +220,18 @@ SWP_API size_t swp_batch_workspace_size(int n_systems);
 SWP_API int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const double* kT,
                            const double* gamma, int nsteps, double split, int threads, void* ws,
                            size_t ws_bytes);
+
+/* The work split of swp_batch_step (host only; no device work): the plan
+ * for systems of w[r] >= 0 particles on n_blocks blocks.  swp_batch_step uses
+ * n_blocks = SMs x blocks per SM of the block shape, max_group =
+ * min(threads, 304) and min_part = threads.  Outputs: item_ofs[n_blocks + 1]
+ * (block k runs items item_ofs[k] .. item_ofs[k + 1] - 1, in that order) and
+ * items[4 * i ..] = (system, rank in its group, group size, 0), at most
+ * n_systems + n_blocks items (the caller's capacity), their count in
+ * *n_items.  Errors: SWP_ERR_INVALID (bad arguments, more large systems than
+ * blocks in the threshold plan). */
+SWP_API int swp_batch_plan(const long long* w, int n_systems, int n_blocks, double split, int max_group,
+                           int min_part, int* item_ofs, int* items, int* n_items);
 
 /* Wait for the stream and report latched device errors. */
 SWP_API int swp_sync(swp_ctx* ctx);

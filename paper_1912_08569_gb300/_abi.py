@@ -50,6 +50,7 @@ EXPORTS = (
     "swp_set_timeout", "swp_last_error", "swp_destroy", "swp_compute_forces_static",
     "swp_batch_workspace_size", "swp_batch_step", "swp_param_grad", "swp_set_bonds", "swp_set_resident",
     "swp_set_withhold_arrival", "swp_thermo_log_bytes", "swp_set_thermo_log", "swp_thermo_log", "swp_eval_grad",
+    "swp_batch_plan",
 )
 
 
@@ -129,6 +130,8 @@ def load_library(path: str = LIB_PATH):
         "swp_batch_workspace_size": ([c_int], c_size_t),
         "swp_batch_step": ([P(c_void_p), c_int, P(c_double), P(c_double), P(c_double), c_int, c_double,
                             c_int, c_void_p, c_size_t], c_int),
+        "swp_batch_plan": ([P(ctypes.c_longlong), c_int, c_int, c_double, c_int, c_int, P(c_int), P(c_int),
+                            P(c_int)], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -340,6 +343,21 @@ def swp_batch_step(ctxs, dt, kT, gamma, nsteps: int, split: float, ws_ptr: int, 
     rc = load_library().swp_batch_step(arr, m, f(dt), f(kT), f(gamma), int(nsteps), float(split), int(threads),
                                        ctypes.c_void_p(ws_ptr), int(ws_bytes))
     return _check(ctxs[0] if m else None, rc, "swp_batch_step")
+
+
+def swp_batch_plan(w, n_blocks: int, split: float, max_group: int, min_part: int):
+    """The batched work split for systems of w[r] particles on n_blocks blocks
+    (host only): returns (item_ofs [n_blocks + 1], items [n, 4] rows of
+    (system, rank in its group, group size, 0))."""
+    m = len(w)
+    wa = (ctypes.c_longlong * m)(*[int(x) for x in w])
+    ofs = (ctypes.c_int * (n_blocks + 1))()
+    items = (ctypes.c_int * (4 * (m + max(n_blocks, 0))))()
+    n = ctypes.c_int(0)
+    rc = load_library().swp_batch_plan(wa, m, int(n_blocks), float(split), int(max_group), int(min_part), ofs,
+                                       items, ctypes.byref(n))
+    _check(None, rc, "swp_batch_plan")
+    return np.array(list(ofs), dtype=np.int64), np.array(list(items)[: 4 * n.value], dtype=np.int64).reshape(-1, 4)
 
 
 def swp_destroy(ctx):

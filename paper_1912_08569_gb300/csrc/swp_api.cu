@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <utility>
 #include <type_traits>
@@ -563,21 +564,117 @@ cudaMemcpyKind kind_from_dev(int where)
 // ---------------------------------------------------------------------------
 // Batched runs: m systems advanced by one cooperative launch of B blocks.
 //
-// Plan: with the work of a system taken as its particle count w and the mean
-// per block T = sum(w) / B, a system heavier than split * T gets a group of
-// max(1, round(w / T)) blocks of its own; the others are packed, heaviest
-// first, onto the block with the least work so far (longest-processing-time
-// rule), each running on one block.  Blocks left over when there is nothing
-// to pack go to the groups with the most work per block.
+// The work of a system is taken as its particle count w; a block's load is
+// the work of its items (a group member: w / group size).
+//
+// Balanced plan (split = 0): the smallest largest load C (bisection) for which
+// every system heavier than C gets g = ceil(w / C) blocks (at most gmax, and
+// no member share below min_part particles) with w / g <= C, and the other
+// systems, heaviest first, each go onto the block with the least load so far
+// (longest-processing-time rule; group members included, after their share)
+// with no load above C.  A block runs its group share first, then its
+// single-block systems: the members of a group start it together (every block
+// of the cooperative launch is resident), so no group barrier waits for a
+// block that is busy with another system.
+//
+// Threshold plan (split > 0): with T = sum(w) / B the mean load, a system
+// heavier than split * T gets a group of max(1, round(w / T)) blocks of its
+// own; the others are packed by the same rule onto the remaining blocks.
+// Blocks left over when there is nothing to pack go to the groups with the
+// most work per block.
 
 struct BatchPlan {
     std::vector<int> item_ofs;  // [B + 1]
     std::vector<int4> items;    // (system, rank, group size, 0)
 };
 
-// gmax: the largest group (blocks given to one system).
-int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, BatchPlan& plan)
+void plan_flatten(const std::vector<std::vector<int4>>& per, BatchPlan& plan)
 {
+    const int B = (int)per.size();
+    plan.item_ofs.assign(B + 1, 0);
+    plan.items.clear();
+    for (int k = 0; k < B; k++) {
+        plan.item_ofs[k] = (int)plan.items.size();
+        for (const int4& it : per[k]) plan.items.push_back(it);
+    }
+    plan.item_ofs[B] = (int)plan.items.size();
+}
+
+// Whether the balanced plan fits under the largest load C; fills per if so.
+// order: the systems heaviest first (ties by index).
+bool plan_balanced_at(const std::vector<long long>& w, const std::vector<int>& order, int B, double C,
+                      int gmax, int min_part, std::vector<std::vector<int4>>* per)
+{
+    std::vector<int> g(w.size(), 0);
+    long long used = 0;
+    for (int r : order) {
+        const double x = (double)std::max(w[r], 1LL);
+        if (x <= C) break;
+        long long k = (long long)std::ceil(x / C);
+        k = std::min<long long>(k, gmax);
+        k = std::min<long long>(k, std::max<long long>(1, w[r] / std::max(min_part, 1)));
+        if (x / (double)k > C) return false;
+        g[r] = (int)k;
+        used += k;
+        if (used > B) return false;
+    }
+    if (per) per->assign(B, {});
+    std::vector<std::pair<double, int>> heap;  // (load, block), least first
+    heap.reserve(B);
+    int b = 0;
+    for (int r : order) {
+        if (g[r] == 0) break;
+        for (int k = 0; k < g[r]; k++, b++) {
+            heap.push_back({(double)w[r] / g[r], b});
+            if (per) (*per)[b].push_back(make_int4(r, k, g[r], 0));
+        }
+    }
+    for (; b < B; b++) heap.push_back({0.0, b});
+    std::make_heap(heap.begin(), heap.end(), std::greater<std::pair<double, int>>());
+    for (int r : order) {
+        if (g[r] > 0) continue;
+        std::pop_heap(heap.begin(), heap.end(), std::greater<std::pair<double, int>>());
+        std::pair<double, int>& top = heap.back();
+        top.first += (double)std::max(w[r], 1LL);
+        if (top.first > C) return false;
+        if (per) (*per)[top.second].push_back(make_int4(r, 0, 1, 0));
+        std::push_heap(heap.begin(), heap.end(), std::greater<std::pair<double, int>>());
+    }
+    return true;
+}
+
+int plan_balanced(const std::vector<long long>& w, int B, int gmax, int min_part, BatchPlan& plan)
+{
+    const int m = (int)w.size();
+    std::vector<int> order(m);
+    for (int r = 0; r < m; r++) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+    double W = 0.0;
+    for (long long x : w) W += (double)std::max(x, 1LL);
+    // hi always fits (no group, every load at most the total); lo is a bound
+    double lo = W / B, hi = std::max(W, 1.0);
+    std::vector<std::vector<int4>> per;
+    if (plan_balanced_at(w, order, B, lo, gmax, min_part, &per)) {
+        plan_flatten(per, plan);
+        return 0;
+    }
+    for (int it = 0; it < 100 && hi > lo * (1.0 + 1e-6); it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (plan_balanced_at(w, order, B, mid, gmax, min_part, nullptr))
+            hi = mid;
+        else
+            lo = mid;
+    }
+    if (!plan_balanced_at(w, order, B, hi, gmax, min_part, &per)) return -1;
+    plan_flatten(per, plan);
+    return 0;
+}
+
+// gmax: the largest group (blocks given to one system); min_part: the
+// smallest member share of a group in the balanced plan.
+int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, int min_part, BatchPlan& plan)
+{
+    if (split <= 0.0) return plan_balanced(w, B, gmax, min_part, plan);
     const int m = (int)w.size();
     long long W = 0;
     for (long long x : w) W += std::max(x, 1LL);
@@ -633,13 +730,7 @@ int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, B
             per[best].push_back(make_int4(r, 0, 1, 0));
             load[best] += (double)std::max(w[r], 1LL);
         }
-    plan.item_ofs.assign(B + 1, 0);
-    plan.items.clear();
-    for (int k = 0; k < B; k++) {
-        plan.item_ofs[k] = (int)plan.items.size();
-        for (const int4& it : per[k]) plan.items.push_back(it);
-    }
-    plan.item_ofs[B] = (int)plan.items.size();
+    plan_flatten(per, plan);
     return 0;
 }
 
@@ -697,7 +788,7 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
         gmax = std::min(gmax, cs[idx[r]]->max_blocks);  // and fit each system's partials
     }
     BatchPlan plan;
-    if (plan_batch(w, B, split, gmax, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
+    if (plan_batch(w, B, split, gmax, threads, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
     std::vector<Dev<Real>> devs(m);
     int uni = 1, bonds = 0;
     for (int r = 0; r < m; r++) {
@@ -1079,7 +1170,7 @@ size_t swp_batch_workspace_size(int n_systems)
 int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const double* kT,
                    const double* gamma, int nsteps, double split, int threads, void* ws, size_t ws_bytes)
 {
-    if (!ctx || n_systems < 1 || !dt || !kT || !gamma || !ws || nsteps < 0 || !(split > 0.0))
+    if (!ctx || n_systems < 1 || !dt || !kT || !gamma || !ws || nsteps < 0 || !(split >= 0.0))
         return SWP_ERR_INVALID;
     if (threads == 0) threads = 1024;
     for (int r = 0; r < n_systems; r++)
@@ -1106,6 +1197,29 @@ int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const d
     if (idx.empty() || nsteps == 0) return SWP_OK;
     return c0->precision == SWP_FP64 ? batch_run<double>(ctx, idx, args, split, threads, ws, ws_bytes)
                                      : batch_run<float>(ctx, idx, args, split, threads, ws, ws_bytes);
+}
+
+int swp_batch_plan(const long long* w, int n_systems, int n_blocks, double split, int max_group, int min_part,
+                   int* item_ofs, int* items, int* n_items)
+{
+    if (!w || n_systems < 1 || n_blocks < 1 || n_blocks > kMaxGrid || !(split >= 0.0) || max_group < 1 ||
+        min_part < 1 || !item_ofs || !items || !n_items)
+        return SWP_ERR_INVALID;
+    std::vector<long long> wv(w, w + n_systems);
+    for (long long x : wv)
+        if (x < 0) return SWP_ERR_INVALID;
+    BatchPlan plan;
+    if (plan_batch(wv, n_blocks, split, max_group, min_part, plan)) return SWP_ERR_INVALID;
+    if (plan.items.size() > (size_t)n_systems + n_blocks) return SWP_ERR_INVALID;
+    for (int k = 0; k <= n_blocks; k++) item_ofs[k] = plan.item_ofs[k];
+    for (size_t i = 0; i < plan.items.size(); i++) {
+        items[4 * i + 0] = plan.items[i].x;
+        items[4 * i + 1] = plan.items[i].y;
+        items[4 * i + 2] = plan.items[i].z;
+        items[4 * i + 3] = plan.items[i].w;
+    }
+    *n_items = (int)plan.items.size();
+    return SWP_OK;
 }
 
 int swp_sync(swp_ctx* c)

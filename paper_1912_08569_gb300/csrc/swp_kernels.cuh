@@ -1029,6 +1029,30 @@ __device__ __forceinline__ Real s_term(const Dev<Real>& d, const PairP<Real>* ta
     return r2 < p.rc2 ? mul_rn(p.a, vh) : Real(0);
 }
 
+// End of the block's region of the list (entries of its particles are
+// placed inside [rank * Pb * max_nn, (rank + 1) * Pb * max_nn)).
+template <typename Real>
+__device__ __forceinline__ long long block_list_end(const Dev<Real>& d)
+{
+    const long long Pb = (d.n + g_size() - 1) / g_size();
+    return (long long)(g_rank() + 1) * Pb * d.max_nn;
+}
+
+// Brings list entries [e0, e1) (partner slots and owner indices) into L2, one
+// 128-byte line per thread, while the block works on other entries.
+template <typename Real>
+__device__ __forceinline__ void prefetch_entries(const Dev<Real>& d, long long e0, long long e1)
+{
+    if (e1 <= e0) return;
+    const long long nj = ((e1 - 1) >> 5) - (e0 >> 5) + 1;  // 32 partner slots per line
+    const long long no = ((e1 - 1) >> 6) - (e0 >> 6) + 1;  // 64 owner indices per line
+    for (long long k = threadIdx.x; k < nj + no; k += blockDim.x) {
+        const void* p = k < nj ? (const void*)&d.ent_j[max(((e0 >> 5) + k) << 5, e0)]
+                               : (const void*)&d.ent_o[max(((e0 >> 6) + k - nj) << 6, e0)];
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+}
+
 // Entries per thread whose gathers a two-barrier pass issues together (S
 // pass, force pass).
 constexpr int kGather = 4;
@@ -1060,6 +1084,20 @@ __device__ void s_pass_block(const Dev<Real>& d, const PairP<Real>* tab, int pc,
         }
         const int e_beg = SM::info()[0].x;
         const int e_end = SM::info()[P - 1].x + SM::info()[P - 1].y;
+        {
+            // into L2 while this sub-chunk runs: the next sub-chunk's reactive
+            // entries (sized like this one's), or after the last one the
+            // block's first sub-chunk, which the force pass starts with
+            const int4 last = SM::info()[P - 1];
+            const long long full = (long long)last.z + last.w;
+            const long long cap = block_list_end(d);
+            if (q0 + P < b1)
+                prefetch_entries(d, full, min(full + (e_end - e_beg), cap));
+            else {
+                const long long f0 = cap - (long long)((d.n + g_size() - 1) / g_size()) * d.max_nn;
+                prefetch_entries(d, f0, min(f0 + (full - e_beg), cap));
+            }
+        }
         Real s = Real(0);
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
@@ -1333,6 +1371,19 @@ __device__ float f_pass_block(const Dev<Real>& d, const PairP<Real>* tab, const 
         const int e_beg = SM::info()[0].x;
         const int e_rend = SM::info()[P - 1].x + SM::info()[P - 1].y;
         const int e_end = SM::info()[P - 1].z + SM::info()[P - 1].w;
+        {
+            // into L2 while this sub-chunk runs: the next sub-chunk's entries
+            // (sized like this one's), or after the last one the reactive
+            // entries of the block's first sub-chunk, which the next S pass
+            // starts with
+            const long long cap = block_list_end(d);
+            if (q0 + P < b1)
+                prefetch_entries(d, e_end, min((long long)e_end + (e_end - e_beg), cap));
+            else {
+                const long long f0 = cap - (long long)((d.n + g_size() - 1) / g_size()) * d.max_nn;
+                prefetch_entries(d, f0, min(f0 + (e_rend - e_beg), cap));
+            }
+        }
         Real fx = 0, fy = 0, fz = 0, gx = 0, gy = 0, gz = 0;  // reactive and other entries' sums
         for (int wb = e_beg; wb < e_end; wb += SM::wave) {
             const int we = min(wb + SM::wave, e_end);
@@ -2576,7 +2627,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_batch(const Dev<Real>*
             s_grp[1] = w.z;
         }
         __syncthreads();
-        if (!run_system<Real, UNI, BONDS>(s_dev, s_args)) return;
+        if (!run_system<Real, UNI, BONDS>(s_dev, s_args)) {
+            // a wait of this system ran out (latched in its status word): its
+            // copies in flight land before the next system reuses the shared
+            // buffers, and the block goes on with its other systems
+            cp_async_wait_all();
+            __syncthreads();
+        }
     }
 }
 #endif  // SWP_BATCHED

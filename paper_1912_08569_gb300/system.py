@@ -233,14 +233,15 @@ class SwapBatch:
     """Independent SwapSystem objects advanced together, one launch per call.
 
     The systems may differ in size, box, coefficients and temperature; they
-    share precision, device and stream.  ``split`` sets which systems get
-    blocks of their own and ``threads`` the batched kernel's block shape (see
-    swp_batch_step); ``autotune`` picks both by timing.
+    share precision, device and stream.  ``split`` selects the work split
+    (0: the balanced plan; > 0: the threshold plan with that factor) and
+    ``threads`` the batched kernel's block shape (see swp_batch_step);
+    ``autotune`` picks both by timing.
     """
 
     SHAPES = {A.SWP_FP32: (1024, 512, 384, 256), A.SWP_FP64: (1024,)}  # threads per block
 
-    def __init__(self, systems, split: float = 1.0, threads: int = 1024):
+    def __init__(self, systems, split: float = 0.0, threads: int = 1024):
         import torch
 
         self.systems = list(systems)
@@ -288,7 +289,7 @@ class SwapBatch:
         for s in self.systems:
             A.swp_sync(s.ctx)
 
-    def autotune(self, nsteps: int, dt, kT=0.0, gamma=0.0, splits=(0.5, 1.0, 2.0, 4.0, 1e9), shapes=None):
+    def autotune(self, nsteps: int, dt, kT=0.0, gamma=0.0, splits=(0.0, 0.5, 1.0, 2.0, 1e9), shapes=None):
         """Times one nsteps run per (block shape, split) candidate -- every
         shape the precision has, by default -- with the systems advancing, and
         keeps the fastest; returns (ms, split, threads, table of every timing)."""

@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_abi_version_needs_no_device(lib):
     from paper_1912_08569_gb300 import _abi
 
-    assert _abi.swp_abi_version() == 5
+    assert _abi.swp_abi_version() == 6
 
 
 def test_header_compiles_as_plain_c(tmp_path):

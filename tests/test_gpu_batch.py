@@ -4,11 +4,12 @@ against the oracle, system by system.
 Each system of a small uneven batch (different sizes, densities, lambda and
 temperature) is advanced by the batched kernel and compared with the oracle's
 run of the same system from the same seeded inputs, with the tolerances of
-the single-system trajectory tests.  Both work splits are covered: every
-system on blocks of its own (groups of several blocks, group barriers) and
-every system packed onto single blocks (block-local barriers, several systems
-per block), with every block shape of the batched kernel (1024, 512, 384 and
-256 threads per block in FP32, 1024 in FP64); a shape the precision lacks is
+the single-system trajectory tests.  The work splits covered: every system
+on blocks of its own (groups of several blocks, group barriers), every system
+packed onto single blocks (block-local barriers, several systems per block),
+and the balanced plan, whose blocks may run a group share and then whole
+systems, with every block shape of the batched kernel (1024, 512, 384 and 256
+threads per block in FP32, 1024 in FP64); a shape the precision lacks is
 refused.
 """
 import numpy as np
@@ -47,11 +48,31 @@ def _min_image(d, box):
     return d - box * np.round(d / box)
 
 
+def _assert_matches_oracle(orc, wl, s, kT, dt, nsteps, precision):
+    fp32 = precision == "fp32"
+    x, v, img = s.state()
+    th = s.thermo()
+    xo, vo, imo, tho = orc.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], wl["n_types"],
+                               oracle_pairs(orc, wl), wl["box"], dt, nsteps, kT=kT, gamma=1.0,
+                               seed=wl["seed"], fp32=fp32)
+    assert th["step"] == nsteps
+    dx = np.abs(_min_image(x - xo, wl["box"]))
+    assert dx.max() <= TRAJ[precision]["x"], (wl["n"], dx.max())
+    assert np.abs(v - vo).max() <= TRAJ[precision]["v"], (wl["n"], np.abs(v - vo).max())
+    assert np.array_equal(img, imo)
+    ref = orc.forces(xo, wl["types"], 2, oracle_pairs(orc, wl), wl["box"], fp32=fp32)
+    tol = max(TOL[precision], 1e3 * TRAJ[precision]["x"])
+    assert abs(th["U2"] - tho[-1, 0]) <= tol * ref["scale_U2"], wl["n"]
+    assert abs(th["U3"] - tho[-1, 1]) <= tol * ref["scale_U3"], wl["n"]
+    assert th["n_bonds"] == ref["n_bonds"], wl["n"]
+
+
 @pytest.mark.parametrize("precision,threads", [("fp32", 1024), ("fp32", 512), ("fp32", 384), ("fp32", 256),
                                                ("fp64", 1024)])
-@pytest.mark.parametrize("split", [0.5, 1e9])
+@pytest.mark.parametrize("split", [0.0, 0.5, 1e9])
 def test_batch_matches_oracle_per_system(orc, precision, threads, split):
-    """Every block shape of the batched kernel, both work splits."""
+    """Every block shape of the batched kernel, the balanced plan and both
+    ends of the threshold plan."""
     from paper_1912_08569_gb300 import SwapBatch
 
     wls = [_wl(*p) for p in SYSTEMS]
@@ -60,23 +81,31 @@ def test_batch_matches_oracle_per_system(orc, precision, threads, split):
     batch = SwapBatch(systems, split=split, threads=threads)
     dt, nsteps = 0.001, 20
     batch.run(nsteps, dt, kT, 1.0)
-    fp32 = precision == "fp32"
     for wl, s, t in zip(wls, systems, kT):
-        x, v, img = s.state()
-        th = s.thermo()
-        xo, vo, imo, tho = orc.run(wl["x"], wl["v"], wl["types"], wl["mass"], wl["tags"], wl["n_types"],
-                                   oracle_pairs(orc, wl), wl["box"], dt, nsteps, kT=t, gamma=1.0,
-                                   seed=wl["seed"], fp32=fp32)
-        assert th["step"] == nsteps
-        dx = np.abs(_min_image(x - xo, wl["box"]))
-        assert dx.max() <= TRAJ[precision]["x"], (wl["n"], dx.max())
-        assert np.abs(v - vo).max() <= TRAJ[precision]["v"], (wl["n"], np.abs(v - vo).max())
-        assert np.array_equal(img, imo)
-        ref = orc.forces(xo, wl["types"], 2, oracle_pairs(orc, wl), wl["box"], fp32=fp32)
-        tol = max(TOL[precision], 1e3 * TRAJ[precision]["x"])
-        assert abs(th["U2"] - tho[-1, 0]) <= tol * ref["scale_U2"], wl["n"]
-        assert abs(th["U3"] - tho[-1, 1]) <= tol * ref["scale_U3"], wl["n"]
-        assert th["n_bonds"] == ref["n_bonds"], wl["n"]
+        _assert_matches_oracle(orc, wl, s, t, dt, nsteps, precision)
+
+
+def test_balanced_plan_blocks_run_a_group_share_then_other_systems(orc):
+    """80 systems of 150-3,000 particles on 256-thread blocks: the balanced
+    plan gives some blocks a share of a multi-block group first and then whole
+    systems; every system matches the oracle's run of it."""
+    import torch
+
+    from paper_1912_08569_gb300 import SwapBatch
+    from paper_1912_08569_gb300 import _abi as A
+
+    wls = inputs.batch_workload(80, seed=7, n_min=150, n_max=3000)
+    nb = torch.cuda.get_device_properties(0).multi_processor_count
+    ofs, items = A.swp_batch_plan([wl["n"] for wl in wls], nb, 0.0, 256, 256)
+    mixed = [b for b in range(nb) if ofs[b + 1] - ofs[b] > 1 and items[ofs[b]][2] > 1]
+    assert mixed, "the size mix should give some group member other systems"
+    systems = [make_gpu(wl, "fp32") for wl in wls]
+    batch = SwapBatch(systems, split=0.0, threads=256)
+    dt, nsteps = 0.001, 20
+    kT = [wl["kT"] for wl in wls]
+    batch.run(nsteps, dt, kT, 1.0)
+    for wl, s, t in zip(wls, systems, kT):
+        _assert_matches_oracle(orc, wl, s, t, dt, nsteps, "fp32")
 
 
 def test_batch_equals_single_runs_in_forces(orc):
