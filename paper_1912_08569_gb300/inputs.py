@@ -163,17 +163,26 @@ def batch_workload(n_systems: int = 256, seed: int = 7, n_min: int = 1000, n_max
     system is the binary A:B 1:1 mixture of ``workload`` (RSA positions,
     Maxwell velocities at its temperature), BAOAB gamma 1, dt 0.001, skin 0.3.
     """
+    out = []
+    for k, (n, rho, t, lam) in enumerate(batch_params(n_systems, seed, n_min, n_max, density, lambdas, kT)):
+        wl = workload("mix100k", lambda3=lam, seed=seed * 1000 + k, n=n, density=rho)
+        wl["kT"] = t
+        wl["v"] = maxwell_velocities(n, t, wl["mass"], seed=seed * 1000 + k + 500)
+        out.append(wl)
+    return out
+
+
+def batch_params(n_systems: int = 256, seed: int = 7, n_min: int = 1000, n_max: int = 32000,
+                 density=(0.2, 0.6), lambdas=(0.0, 0.5, 1.0, 2.0, 5.0), kT=(0.03, 0.2)):
+    """(n, density, kT, lambda) of each system of ``batch_workload`` with the
+    same arguments, without generating the systems."""
     rng = np.random.Generator(np.random.Philox(seed))
     out = []
     for k in range(n_systems):
         n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
         rho = float(rng.uniform(*density))
         t = float(rng.uniform(*kT))
-        lam = float(lambdas[k % len(lambdas)])
-        wl = workload("mix100k", lambda3=lam, seed=seed * 1000 + k, n=n, density=rho)
-        wl["kT"] = t
-        wl["v"] = maxwell_velocities(n, t, wl["mass"], seed=seed * 1000 + k + 500)
-        out.append(wl)
+        out.append((n, rho, t, float(lambdas[k % len(lambdas)])))
     return out
 
 
