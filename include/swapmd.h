@@ -188,19 +188,15 @@ SWP_API int swp_step_nvt(swp_ctx* ctx, double dt, double kT, double gamma, int n
  * list buffer and state, and none may appear twice; empty systems are
  * skipped.
  *
- * Work split, with w the particle count of a system.  split = 0 (the
- * balanced plan, the default): a share of s particles of a system on g
- * blocks costs s + chunk * ceil(s / threads) (+ group if g > 1), in units of
- * one particle's work, with chunk = 0.425 * threads (the fixed cost of a
- * sub-chunk's phases) and group = 0.14 * threads (a group barrier's), as
- * measured on GB300; the plan is the smallest largest block load C for which
- * every system costing more than C whole gets the fewest blocks whose largest
- * share costs at most C (its device-side barriers span only those blocks; no
- * share below `threads` particles) and every other system, heaviest first,
- * goes onto the least-loaded block, group members included, with no load
- * above C; a block runs its group share first, then its single-block systems
- * one after the other.  split > 0 (the threshold plan, on particle counts):
- * with T the mean count per block, a system with w > split * T gets
+ * Work split, with w the particle count of a system and a block's load the
+ * particles it advances (a group member: w / group size).  split = 0 (the
+ * balanced plan, the default): the smallest largest load C for which every
+ * system with w > C gets ceil(w / C) blocks (its device-side barriers span
+ * only those blocks; no member share below `threads` particles) and every
+ * other system, heaviest first, goes onto the least-loaded block, group
+ * members included, with no load above C; a block runs its group share
+ * first, then its single-block systems one after the other.  split > 0 (the
+ * threshold plan): with T the mean load, a system with w > split * T gets
  * max(1, round(w / T)) blocks that run nothing else, the others are packed
  * the same way onto the remaining blocks.  A group has at most
  * min(threads, 304) blocks.  swp_batch_plan returns either plan.
@@ -226,20 +222,16 @@ SWP_API int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt,
                            size_t ws_bytes);
 
 /* The work split of swp_batch_step (host only; no device work): the plan
- * for systems of w[r] >= 0 particles on n_blocks blocks, with `threads`
- * particles per sub-chunk (also the smallest share of a group member) and
- * the balanced plan's costs chunk_cost, group_cost >= 0 (particle units).
- * swp_batch_step uses n_blocks = SMs x blocks per SM of the block shape,
- * max_group = min(threads, 304), chunk_cost = 0.425 * threads and
- * group_cost = 0.14 * threads.  Outputs: item_ofs[n_blocks + 1] (block k runs
- * items item_ofs[k] .. item_ofs[k + 1] - 1, in that order) and
+ * for systems of w[r] >= 0 particles on n_blocks blocks.  swp_batch_step uses
+ * n_blocks = SMs x blocks per SM of the block shape, max_group =
+ * min(threads, 304) and min_part = threads.  Outputs: item_ofs[n_blocks + 1]
+ * (block k runs items item_ofs[k] .. item_ofs[k + 1] - 1, in that order) and
  * items[4 * i ..] = (system, rank in its group, group size, 0), at most
  * n_systems + n_blocks items (the caller's capacity), their count in
  * *n_items.  Errors: SWP_ERR_INVALID (bad arguments, more large systems than
  * blocks in the threshold plan). */
 SWP_API int swp_batch_plan(const long long* w, int n_systems, int n_blocks, double split, int max_group,
-                           int threads, double chunk_cost, double group_cost, int* item_ofs, int* items,
-                           int* n_items);
+                           int min_part, int* item_ofs, int* items, int* n_items);
 
 /* Wait for the stream and report latched device errors. */
 SWP_API int swp_sync(swp_ctx* ctx);

@@ -130,8 +130,8 @@ def load_library(path: str = LIB_PATH):
         "swp_batch_workspace_size": ([c_int], c_size_t),
         "swp_batch_step": ([P(c_void_p), c_int, P(c_double), P(c_double), P(c_double), c_int, c_double,
                             c_int, c_void_p, c_size_t], c_int),
-        "swp_batch_plan": ([P(ctypes.c_longlong), c_int, c_int, c_double, c_int, c_int, c_double, c_double,
-                            P(c_int), P(c_int), P(c_int)], c_int),
+        "swp_batch_plan": ([P(ctypes.c_longlong), c_int, c_int, c_double, c_int, c_int, P(c_int), P(c_int),
+                            P(c_int)], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -345,22 +345,17 @@ def swp_batch_step(ctxs, dt, kT, gamma, nsteps: int, split: float, ws_ptr: int, 
     return _check(ctxs[0] if m else None, rc, "swp_batch_step")
 
 
-def swp_batch_plan(w, n_blocks: int, split: float, max_group: int, threads: int, chunk_cost=None,
-                   group_cost=None):
+def swp_batch_plan(w, n_blocks: int, split: float, max_group: int, min_part: int):
     """The batched work split for systems of w[r] particles on n_blocks blocks
-    (host only); chunk_cost and group_cost default to the ones swp_batch_step
-    uses for this block shape (0.425 and 0.14 x threads).  Returns (item_ofs
-    [n_blocks + 1], items [n, 4] rows of (system, rank in its group, group
-    size, 0))."""
+    (host only): returns (item_ofs [n_blocks + 1], items [n, 4] rows of
+    (system, rank in its group, group size, 0))."""
     m = len(w)
-    chunk_cost = 0.425 * threads if chunk_cost is None else chunk_cost
-    group_cost = 0.14 * threads if group_cost is None else group_cost
     wa = (ctypes.c_longlong * m)(*[int(x) for x in w])
     ofs = (ctypes.c_int * (n_blocks + 1))()
     items = (ctypes.c_int * (4 * (m + max(n_blocks, 0))))()
     n = ctypes.c_int(0)
-    rc = load_library().swp_batch_plan(wa, m, int(n_blocks), float(split), int(max_group), int(threads),
-                                       float(chunk_cost), float(group_cost), ofs, items, ctypes.byref(n))
+    rc = load_library().swp_batch_plan(wa, m, int(n_blocks), float(split), int(max_group), int(min_part), ofs,
+                                       items, ctypes.byref(n))
     _check(None, rc, "swp_batch_plan")
     return np.array(list(ofs), dtype=np.int64), np.array(list(items)[: 4 * n.value], dtype=np.int64).reshape(-1, 4)
 

@@ -564,15 +564,12 @@ cudaMemcpyKind kind_from_dev(int where)
 // ---------------------------------------------------------------------------
 // Batched runs: m systems advanced by one cooperative launch of B blocks.
 //
-// Balanced plan (split = 0).  The cost of a share of s particles of a system
-// split over g blocks, in units of one particle's work:
-//   cost(s, g) = s + chunk * ceil(s / sub) + (g > 1 ? group : 0),
-// with sub the particles per sub-chunk (threads per block), chunk the fixed
-// cost of a sub-chunk's phases and group the extra cost of a group barrier;
-// a block's load is the cost of its items.  The plan is the smallest largest
-// load C (bisection) for which every system with cost(w, 1) > C gets the
-// fewest blocks g (at most gmax, no member share below min_part particles)
-// whose largest member share ceil(w / g) costs at most C, and the other
+// The work of a system is taken as its particle count w; a block's load is
+// the work of its items (a group member: w / group size).
+//
+// Balanced plan (split = 0): the smallest largest load C (bisection) for which
+// every system heavier than C gets g = ceil(w / C) blocks (at most gmax, and
+// no member share below min_part particles) with w / g <= C, and the other
 // systems, heaviest first, each go onto the block with the least load so far
 // (longest-processing-time rule; group members included, after their share)
 // with no load above C.  A block runs its group share first, then its
@@ -580,25 +577,15 @@ cudaMemcpyKind kind_from_dev(int where)
 // of the cooperative launch is resident), so no group barrier waits for a
 // block that is busy with another system.
 //
-// Threshold plan (split > 0), on particle counts: with T = sum(w) / B the
-// mean load, a system heavier than split * T gets a group of
-// max(1, round(w / T)) blocks of its own; the others are packed by the same
-// rule onto the remaining blocks.  Blocks left over when there is nothing to
-// pack go to the groups with the most work per block.
+// Threshold plan (split > 0): with T = sum(w) / B the mean load, a system
+// heavier than split * T gets a group of max(1, round(w / T)) blocks of its
+// own; the others are packed by the same rule onto the remaining blocks.
+// Blocks left over when there is nothing to pack go to the groups with the
+// most work per block.
 
 struct BatchPlan {
     std::vector<int> item_ofs;  // [B + 1]
     std::vector<int4> items;    // (system, rank, group size, 0)
-};
-
-struct PlanCost {
-    int sub = 1;
-    double chunk = 0.0;
-    double group = 0.0;
-    double of(long long s, int g) const
-    {
-        return (double)s + chunk * (double)((s + sub - 1) / sub) + (g > 1 ? group : 0.0);
-    }
 };
 
 void plan_flatten(const std::vector<std::vector<int4>>& per, BatchPlan& plan)
@@ -614,20 +601,19 @@ void plan_flatten(const std::vector<std::vector<int4>>& per, BatchPlan& plan)
 }
 
 // Whether the balanced plan fits under the largest load C; fills per if so.
-// order: the systems heaviest first (ties by index); w1: the whole-system
-// costs cost(max(w, 1), 1).
-bool plan_balanced_at(const std::vector<long long>& w, const std::vector<double>& w1,
-                      const std::vector<int>& order, int B, double C, int gmax, int min_part,
-                      const PlanCost& cost, std::vector<std::vector<int4>>* per)
+// order: the systems heaviest first (ties by index).
+bool plan_balanced_at(const std::vector<long long>& w, const std::vector<int>& order, int B, double C,
+                      int gmax, int min_part, std::vector<std::vector<int4>>* per)
 {
     std::vector<int> g(w.size(), 0);
     long long used = 0;
     for (int r : order) {
-        if (w1[r] <= C) break;
-        const long long kmax = std::min<long long>(gmax, std::max<long long>(1, w[r] / std::max(min_part, 1)));
-        long long k = std::max<long long>(2, (long long)((double)w[r] / C));
-        while (k <= kmax && cost.of((w[r] + k - 1) / k, (int)k) > C) k++;
-        if (k > kmax) return false;
+        const double x = (double)std::max(w[r], 1LL);
+        if (x <= C) break;
+        long long k = (long long)std::ceil(x / C);
+        k = std::min<long long>(k, gmax);
+        k = std::min<long long>(k, std::max<long long>(1, w[r] / std::max(min_part, 1)));
+        if (x / (double)k > C) return false;
         g[r] = (int)k;
         used += k;
         if (used > B) return false;
@@ -638,10 +624,8 @@ bool plan_balanced_at(const std::vector<long long>& w, const std::vector<double>
     int b = 0;
     for (int r : order) {
         if (g[r] == 0) break;
-        const long long Pb = (w[r] + g[r] - 1) / g[r];  // member shares as the kernel splits them
         for (int k = 0; k < g[r]; k++, b++) {
-            const long long sk = std::max(0LL, std::min(Pb, w[r] - k * Pb));
-            heap.push_back({cost.of(sk, g[r]), b});
+            heap.push_back({(double)w[r] / g[r], b});
             if (per) (*per)[b].push_back(make_int4(r, k, g[r], 0));
         }
     }
@@ -651,7 +635,7 @@ bool plan_balanced_at(const std::vector<long long>& w, const std::vector<double>
         if (g[r] > 0) continue;
         std::pop_heap(heap.begin(), heap.end(), std::greater<std::pair<double, int>>());
         std::pair<double, int>& top = heap.back();
-        top.first += w1[r];
+        top.first += (double)std::max(w[r], 1LL);
         if (top.first > C) return false;
         if (per) (*per)[top.second].push_back(make_int4(r, 0, 1, 0));
         std::push_heap(heap.begin(), heap.end(), std::greater<std::pair<double, int>>());
@@ -659,44 +643,38 @@ bool plan_balanced_at(const std::vector<long long>& w, const std::vector<double>
     return true;
 }
 
-int plan_balanced(const std::vector<long long>& w, int B, int gmax, int min_part, const PlanCost& cost,
-                  BatchPlan& plan)
+int plan_balanced(const std::vector<long long>& w, int B, int gmax, int min_part, BatchPlan& plan)
 {
     const int m = (int)w.size();
     std::vector<int> order(m);
     for (int r = 0; r < m; r++) order[r] = r;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
-    std::vector<double> w1(m);
     double W = 0.0;
-    for (int r = 0; r < m; r++) {
-        w1[r] = cost.of(std::max(w[r], 1LL), 1);
-        W += w1[r];
-    }
+    for (long long x : w) W += (double)std::max(x, 1LL);
     // hi always fits (no group, every load at most the total); lo is a bound
-    double lo = W / B, hi = W;
+    double lo = W / B, hi = std::max(W, 1.0);
     std::vector<std::vector<int4>> per;
-    if (plan_balanced_at(w, w1, order, B, lo, gmax, min_part, cost, &per)) {
+    if (plan_balanced_at(w, order, B, lo, gmax, min_part, &per)) {
         plan_flatten(per, plan);
         return 0;
     }
     for (int it = 0; it < 100 && hi > lo * (1.0 + 1e-6); it++) {
         const double mid = 0.5 * (lo + hi);
-        if (plan_balanced_at(w, w1, order, B, mid, gmax, min_part, cost, nullptr))
+        if (plan_balanced_at(w, order, B, mid, gmax, min_part, nullptr))
             hi = mid;
         else
             lo = mid;
     }
-    if (!plan_balanced_at(w, w1, order, B, hi, gmax, min_part, cost, &per)) return -1;
+    if (!plan_balanced_at(w, order, B, hi, gmax, min_part, &per)) return -1;
     plan_flatten(per, plan);
     return 0;
 }
 
 // gmax: the largest group (blocks given to one system); min_part: the
-// smallest member share of a group in the balanced plan; cost: its cost model.
-int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, int min_part,
-               const PlanCost& cost, BatchPlan& plan)
+// smallest member share of a group in the balanced plan.
+int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, int min_part, BatchPlan& plan)
 {
-    if (split <= 0.0) return plan_balanced(w, B, gmax, min_part, cost, plan);
+    if (split <= 0.0) return plan_balanced(w, B, gmax, min_part, plan);
     const int m = (int)w.size();
     long long W = 0;
     for (long long x : w) W += std::max(x, 1LL);
@@ -756,20 +734,6 @@ int plan_batch(const std::vector<long long>& w, int B, double split, int gmax, i
     return 0;
 }
 
-// The balanced plan's cost model for a block shape, measured on GB300 with
-// 1024-thread blocks (152 blocks, one to four equal systems per block, groups
-// of two and four blocks): a sub-chunk costs about 7.9 us plus 0.018 us per
-// particle, a group 2.6 us per step more; in particles, chunk = 0.425 threads
-// and group = 0.14 threads (the per-particle cost scales as 1 / threads).
-PlanCost batch_cost(int threads)
-{
-    PlanCost c;
-    c.sub = threads;
-    c.chunk = 0.425 * threads;
-    c.group = 0.14 * threads;
-    return c;
-}
-
 size_t batch_bytes(int m, size_t dev_size)
 {
     return align256(dev_size * m) + align256(sizeof(RunArgs) * m) + align256(sizeof(int) * (kMaxGrid + 1)) +
@@ -824,8 +788,7 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
         gmax = std::min(gmax, cs[idx[r]]->max_blocks);  // and fit each system's partials
     }
     BatchPlan plan;
-    if (plan_batch(w, B, split, gmax, threads, batch_cost(threads), plan))
-        return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
+    if (plan_batch(w, B, split, gmax, threads, plan)) return fail(c0, SWP_ERR_INVALID, "more large systems than blocks");
     std::vector<Dev<Real>> devs(m);
     int uni = 1, bonds = 0;
     for (int r = 0; r < m; r++) {
@@ -1236,21 +1199,17 @@ int swp_batch_step(swp_ctx* const* ctx, int n_systems, const double* dt, const d
                                      : batch_run<float>(ctx, idx, args, split, threads, ws, ws_bytes);
 }
 
-int swp_batch_plan(const long long* w, int n_systems, int n_blocks, double split, int max_group, int threads,
-                   double chunk_cost, double group_cost, int* item_ofs, int* items, int* n_items)
+int swp_batch_plan(const long long* w, int n_systems, int n_blocks, double split, int max_group, int min_part,
+                   int* item_ofs, int* items, int* n_items)
 {
     if (!w || n_systems < 1 || n_blocks < 1 || n_blocks > kMaxGrid || !(split >= 0.0) || max_group < 1 ||
-        threads < 1 || !(chunk_cost >= 0.0) || !(group_cost >= 0.0) || !item_ofs || !items || !n_items)
+        min_part < 1 || !item_ofs || !items || !n_items)
         return SWP_ERR_INVALID;
-    PlanCost cost;
-    cost.sub = threads;
-    cost.chunk = chunk_cost;
-    cost.group = group_cost;
     std::vector<long long> wv(w, w + n_systems);
     for (long long x : wv)
         if (x < 0) return SWP_ERR_INVALID;
     BatchPlan plan;
-    if (plan_batch(wv, n_blocks, split, max_group, threads, cost, plan)) return SWP_ERR_INVALID;
+    if (plan_batch(wv, n_blocks, split, max_group, min_part, plan)) return SWP_ERR_INVALID;
     if (plan.items.size() > (size_t)n_systems + n_blocks) return SWP_ERR_INVALID;
     for (int k = 0; k <= n_blocks; k++) item_ofs[k] = plan.item_ofs[k];
     for (size_t i = 0; i < plan.items.size(); i++) {
