@@ -366,7 +366,10 @@ SWP_API int swp_set_resident(swp_ctx* ctx, int enable);
  * grid barrier, so that every other block's bounded wait runs out after the
  * timeout of swp_set_timeout: the launch ends early with every block returned,
  * and the next swp_sync / swp_read_* reports SWP_ERR_TIMEOUT (the state is then
- * lost: set it again).  Nothing faults and no wait is unbounded; it exercises
+ * lost: set it again).  In a batched launch (swp_batch_step) the same happens
+ * to the group of blocks of ctx's system, whose blocks then go on with the
+ * other systems the plan gave them; a system on one block has no grid
+ * barrier, and there the request has no effect.  Nothing faults and no wait is unbounded; it exercises
  * the path a real stall (a block starved by other work, a lost arrival) takes.
  * The request is consumed by that one launch.  on not 0 or 1: SWP_ERR_INVALID. */
 SWP_API int swp_set_withhold_arrival(swp_ctx* ctx, int on);

@@ -795,6 +795,8 @@ int batch_run(swp_ctx* const* cs, const std::vector<int>& idx, std::vector<RunAr
         swp_ctx* c = cs[idx[r]];
         int rc = prepare_args<Real>(c, args[r]);
         if (rc) return rc;
+        args[r].withhold = c->withhold;
+        c->withhold = 0;  // one launch consumes the request
         uni &= args[r].uni;
         devs[r] = dev<Real>(c);
         bonds |= devs[r].has_bonds;

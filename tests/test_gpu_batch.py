@@ -108,6 +108,41 @@ def test_balanced_plan_blocks_run_a_group_share_then_other_systems(orc):
         _assert_matches_oracle(orc, wl, s, t, dt, nsteps, "fp32")
 
 
+def test_batch_group_timeout_leaves_the_other_systems_running(orc):
+    """Failure detection without a fault, batched: the first group barrier of a
+    system on several blocks is withheld, its blocks' waits run out after 1 ms,
+    and those blocks go on with the whole systems the balanced plan gave them.
+    That system alone reports SWP_ERR_TIMEOUT; every other system matches the
+    oracle's run of it."""
+    import torch
+
+    from paper_1912_08569_gb300 import SwapBatch
+    from paper_1912_08569_gb300 import _abi as A
+
+    wls = inputs.batch_workload(80, seed=7, n_min=150, n_max=3000)
+    nb = torch.cuda.get_device_properties(0).multi_processor_count
+    ofs, items = A.swp_batch_plan([wl["n"] for wl in wls], nb, 0.0, 256, 256)
+    mixed = [b for b in range(nb) if ofs[b + 1] - ofs[b] > 1 and items[ofs[b]][2] > 1]
+    assert mixed
+    bad = int(items[ofs[mixed[0]]][0])  # a group system whose member block has other systems
+    after = [int(it[0]) for it in items[ofs[mixed[0]] + 1:ofs[mixed[0] + 1]]]
+    systems = [make_gpu(wl, "fp32") for wl in wls]
+    systems[bad].set_timeout(1_000_000)
+    A.swp_set_withhold_arrival(systems[bad].ctx, 1)
+    batch = SwapBatch(systems, split=0.0, threads=256)
+    dt, nsteps = 0.001, 20
+    kT = [wl["kT"] for wl in wls]
+    batch.run(nsteps, dt, kT, 1.0, sync=False)
+    with pytest.raises(A.SwpError) as e:
+        A.swp_sync(systems[bad].ctx)
+    assert e.value.code == A.SWP_ERR_TIMEOUT, str(e.value)
+    torch.cuda.synchronize()  # nothing is left running
+    assert after, "the member block runs other systems after its group share"
+    for r, (wl, s, t) in enumerate(zip(wls, systems, kT)):
+        if r != bad:
+            _assert_matches_oracle(orc, wl, s, t, dt, nsteps, "fp32")
+
+
 def test_batch_equals_single_runs_in_forces(orc):
     """After a batched run, each system's forces at its new positions agree with
     a fresh single-system evaluation of the same positions."""
